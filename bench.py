@@ -1,0 +1,447 @@
+#!/usr/bin/env python3
+"""Training-step throughput of the Student-splatting rasterizer on GB300.
+
+One step = project + bin + sort + forward render of every view, L1 loss,
+backward render + projection backward, SGHMC/Adam update -- the whole hot
+path on a 1.5M-component scene (6 clusters + ground plane, SH degree 3,
+nu in [1, 32], 30% scooping) seen by 4 views at 1297x840, seeded and
+synthetic.  The step is captured once into a CUDA graph and replayed.
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs an
+independent replica of the workload (no collective on the data path: the
+path shards by scene/views without an exchange in this form), so scaling is
+weak and `value` sums the pixels of all ranks over the slowest rank's time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+project) on a bounded pixel sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Mpix/s at 1.5M comps; serve p50/p99 ms, batched vs plain on one GB300"
+UNIT = "Mpix/s"
+WORKLOAD = ("clusters_1p5m_4views: 1.5M 3D t-components (6 Gaussian clusters + ground plane, log-scale "
+            "N(-4,0.7), SH degree 3, nu log-uniform [1,32], 30% scooping), 4 views x 1297x840 per step, "
+            "train step = project+bin+sort+render_fwd+L1+render_bwd+project_bwd+sghmc_step")
+N_SMS = 152
+MUFU_PER_SM_CLK = 16
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+# algorithmic work per contributing (splat, pixel) pair, counted from the
+# method's formulas: FP32 flops (FMA = 2) and MUFU ops
+FWD_FLOPS, FWD_MUFU = 22, 2
+BWD_FLOPS, BWD_MUFU = 75, 4
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--tile", default=None, help="WxH tile, e.g. 16x16 (default: autotuned cache or 16x16)")
+    ap.add_argument("--batch", type=int, default=None)
+    ap.add_argument("--no-plain", action="store_true", help="skip the one-frame-per-view comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ ranks
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over all ranks (x itself with one rank)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+REASON_NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
+class ClockSampler:
+    """nvidia-smi sampling every 200 ms while the timed region runs."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        self.t0 = time.time()
+
+    def stop(self) -> dict | None:
+        self.t1 = time.time()
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        for r in rows:
+            for name, val in zip(REASON_NAMES, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------------ ours
+
+def _cfg(args):
+    from paper_2503_10148_gb300 import autotune, frame
+    if args.tile or args.batch:
+        tw, th = (int(v) for v in (args.tile or "16x16").split("x"))
+        return frame.make_cfg(tile_w=tw, tile_h=th, batch=args.batch or 128), "cli"
+    best = autotune.cached("clusters_1p5m_4views")
+    if best:
+        return frame.make_cfg(tile_w=best["tile_w"], tile_h=best["tile_h"], batch=best["batch"]), "autotuned"
+    return frame.make_cfg(), "default"
+
+
+def stage_breakdown(ts, reps, device):
+    """Eager steps with CUDA events between the stages (same stream)."""
+    import torch
+    from paper_2503_10148_gb300 import frame as F
+    fr = ts.frame
+    st = torch.cuda.current_stream(device)
+    names = ["project", "bin", "sort", "render_fwd", "loss", "render_bwd", "project_bwd", "sghmc_step"]
+    acc = {n: 0.0 for n in names}
+    for _ in range(reps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+        ts.loss.zero_()
+        ev[0].record(st)
+        fr.project(st); ev[1].record(st)
+        fr.bin(st); ev[2].record(st)
+        fr.sort(st); ev[3].record(st)
+        fr.render_fwd(st); ev[4].record(st)
+        F.loss_l1(fr.rgb, ts.targets, ts.dl, ts.loss, st); ev[5].record(st)
+        fr.render_bwd(ts.dl, st); ev[6].record(st)
+        fr.project_bwd([ts.grads], st); ev[7].record(st)
+        F.sghmc_step(ts.scene, ts.grads, ts.state, ts.sp, stream=st); ev[8].record(st)
+        torch.cuda.synchronize(device)
+        for i, n in enumerate(names):
+            acc[n] += ev[i].elapsed_time(ev[i + 1])
+    return {n: acc[n] / reps for n in names}
+
+
+def read_counters(fr):
+    import torch
+    ctrl = fr.ws_view(fr.plan.ws_off_ctrl, torch.int64, 8).cpu().numpy()
+    # ctrl uint32 words: [4..5] contributing pairs, [6..7] evaluated pairs
+    return int(ctrl[2]), int(ctrl[3])
+
+
+def roofline(stage: str, ms: float, ts, contrib: int, peaks: dict, peak_src: str):
+    """Achieved vs peak for the dominant stage; ALU stages against the
+    FP32/MUFU ceiling derived from unit counts at the maximum SM clock, memory
+    stages against the measured copy bandwidth."""
+    t = ms * 1e-3
+    if stage in ("render_fwd", "render_bwd"):
+        flops, mufu = (FWD_FLOPS, FWD_MUFU) if stage == "render_fwd" else (BWD_FLOPS, BWD_MUFU)
+        clk = SM_MAX_MHZ * 1e6
+        fp32_peak = N_SMS * FP32_LANES_PER_SM * 2 * clk  # FLOP/s
+        mufu_peak = N_SMS * MUFU_PER_SM_CLK * clk  # op/s
+        pair_peak = min(fp32_peak / flops, mufu_peak / mufu)
+        achieved = contrib * flops / t / 1e12
+        peak = pair_peak * flops / 1e12
+        return {"bound": "alu", "kernel": stage, "achieved": round(achieved, 3), "peak": round(peak, 3),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": f"unit counts x {SM_MAX_MHZ:.0f} MHz (FP32 and MUFU ceilings)",
+                "work": f"{contrib} contributing pairs x {flops} FP32 flops + {mufu} MUFU"}
+    nbytes = algorithmic_bytes(stage, ts)
+    achieved = nbytes / t / 1e9
+    peak = float(peaks["hbm_gbs"])
+    return {"bound": "hbm", "kernel": stage, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
+            "work": f"{nbytes} algorithmic bytes"}
+
+
+def algorithmic_bytes(stage: str, ts) -> int:
+    fr = ts.frame
+    P = fr.plan
+    n = ts.scene.n
+    K = (ts.scene.sh_degree + 1) ** 2
+    V = P.n_jobs
+    pairs = fr.status()[1]
+    if stage == "project":
+        return n * (12 + 3 * K) * 4 + V * n * 64
+    if stage == "project_bwd":
+        return n * (12 + 3 * K) * 4 * 2 + V * n * 48
+    if stage == "sghmc_step":
+        return n * 4 * (3 * 4 + 1 + (9 + 3 * K) * 7)
+    if stage == "sort":
+        passes = (P.tile_bits + 7) // 8
+        return pairs * (passes * 16 + 4)
+    if stage == "bin":
+        return V * n * 4 * (4 * 4 + 3) + pairs * 8
+    return 0
+
+
+def kernels_per_step(plan) -> int:
+    """Our kernel launches in one train step (memsets excluded)."""
+    pair_passes = (plan.tile_bits + 7) // 8
+    bin_k = 1 + 4 * 3 + 4  # init, 4 radix passes, count/scan/finish/emit
+    sort_k = pair_passes * 3 + 1
+    return 1 + bin_k + sort_k + 1 + 1 + 1 + 1 + 2
+
+
+def run_ours(args):
+    import torch
+    from paper_2503_10148_gb300 import build, frame as F, inputs, train
+    rank, world, local = dist_env()
+    assert torch.cuda.is_available(), "bench.py needs a GPU (no CPU fallback)"
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist_init(world, "nccl")
+    build.build()
+
+    scene_np, cams = inputs.clusters_1p5m_4views()
+    cams = [F.f32_camera(c) for c in cams]
+    targets_np = np.concatenate([t.reshape(-1) for t in inputs.target_images(cams, seed=3)])
+    scene = F.Scene.from_numpy(scene_np, device)
+    targets = torch.as_tensor(targets_np, device=device)
+    cfg, cfg_src = _cfg(args)
+    ts = train.TrainStep(scene, cams, targets, cfg=cfg, device=device)
+    ts.calibrate()
+    ts.capture()
+    for _ in range(max(args.warmup, 3)):
+        ts.replay()
+    torch.cuda.synchronize(device)
+
+    mpix = sum(c.width * c.height for c in cams) / 1e6
+    gpu_idx = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES") else local
+    clocks = ClockSampler(gpu_idx)
+    st = torch.cuda.current_stream(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize(device)
+    clocks.start()
+    e0.record(st)
+    for _ in range(args.steps):
+        ts.replay()
+    e1.record(st)
+    torch.cuda.synchronize(device)
+    barrier(world)
+    clock_info = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(ms, world, device)
+    ts.check()
+
+    # end to end: targets from pinned host memory, loss read back, every step
+    host_t = torch.empty(targets.numel(), dtype=torch.float32, pin_memory=True)
+    host_t.copy_(torch.as_tensor(targets_np))
+    host_loss = torch.empty(1, dtype=torch.float32, pin_memory=True)
+    barrier(world)
+    torch.cuda.synchronize(device)
+    w0 = time.perf_counter()
+    e0.record(st)
+    for _ in range(args.steps):
+        ts.targets.copy_(host_t, non_blocking=True)
+        ts.replay()
+        host_loss.copy_(ts.loss, non_blocking=True)
+    e1.record(st)
+    torch.cuda.synchronize(device)
+    wall = (time.perf_counter() - w0) * 1e3 / args.steps
+    barrier(world)
+    e2e_ms = max_over_ranks(max(e0.elapsed_time(e1) / args.steps, wall), world, device)
+    ts.check()
+
+    # per-stage breakdown and roofline of the dominant kernel
+    stages = stage_breakdown(ts, 3, device)
+    contrib, evaluated = read_counters(ts.frame)
+    dom = max(stages, key=stages.get)
+    peaks, peak_src = measured_peaks()
+    roof = roofline(dom, stages[dom], ts, contrib, peaks, peak_src)
+    _, pairs, _ = ts.frame.status()
+
+    plain = None
+    if not args.no_plain:
+        ps = train.PlainStep(scene, cams, targets, cfg=cfg, device=device)
+        ps.run()
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        e0.record(st)
+        reps = max(3, args.steps // 4)
+        for _ in range(reps):
+            ps.run()
+        e1.record(st)
+        torch.cuda.synchronize(device)
+        pms = max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3) / reps
+        plain = {"form": "one frame per view, eager launches", "ms_per_step": round(pms, 3),
+                 "value": round(world * mpix / (pms * 1e-3), 2)}
+
+    result = {
+        "metric": METRIC, "value": round(world * mpix / (ms_max * 1e-3), 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms_max, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded scene, cameras and target images)",
+        "config": {"workload": WORKLOAD, "views": len(cams), "width": cams[0].width, "height": cams[0].height,
+                   "components": scene.n, "tile": f"{cfg.tile_w}x{cfg.tile_h}", "batch": cfg.batch,
+                   "cfg_source": cfg_src, "form": "batched frame, whole step in one CUDA graph",
+                   "pairs_per_step": pairs, "pair_capacity": ts.frame.pair_capacity,
+                   "l2": "inputs larger than L2 (params 360 MB, pair lists > 1 GB, images 52 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": round(world * mpix / (e2e_ms * 1e-3), 2), "unit": UNIT,
+                "h2d_bytes_per_step": int(targets.numel() * 4), "d2h_bytes_per_step": 4},
+        "gpu_launches": kernels_per_step(ts.frame.plan) * args.steps,
+        "roofline": roof,
+        "stages_ms": {k: round(v, 3) for k, v in stages.items()},
+        "pairs": {"contributing": contrib, "evaluated": evaluated},
+        "clocks": clock_info,
+        "plain": plain,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+# ------------------------------------------------------------------ oracle
+
+def _oracle_sample(scene_np, cams, n_pix, seed):
+    """FP64 oracle forward + backward of n_pix seeded pixels per view (the
+    projection of every (view, component) pair included)."""
+    import oracle
+    from paper_2503_10148_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    pix = [rng.choice(c.width * c.height, n_pix, replace=False).astype(np.int64) for c in cams]
+    w = inputs.linear_loss_weights(cams, seed)
+    dl = [wv.reshape(3, -1)[:, p] for wv, p in zip(w, pix)]
+    cfgd = dict(oracle.DEFAULT_CFG)
+    t0 = time.perf_counter()
+    oracle.backward(scene_np, cams, cfgd, dl, pix)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(budget_s: float):
+    import oracle
+    from paper_2503_10148_gb300 import inputs
+    scene_np, cams = inputs.clusters_1p5m_4views()
+    pilot = 8
+    t_pilot = _oracle_sample(scene_np, cams, pilot, seed=100)
+    n_pix = int(max(pilot, min(2000, pilot * budget_s / max(t_pilot, 1e-3))))
+    t = _oracle_sample(scene_np, cams, n_pix, seed=101)
+    px = n_pix * len(cams)
+    return {"value": round(px / t / 1e6, 8), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle fwd+bwd of {n_pix} seeded pixels per view x {len(cams)} views of the "
+                      f"1.5M-component workload, projection of all 6M (view, component) pairs included; "
+                      f"{t:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2503_10148_gb300 import inputs
+    oracle.build.build()
+    scene_np, cams = inputs.clusters_1p5m_4views()
+    n_pix = 32
+    for w in range(max(args.warmup, 3)):
+        _oracle_sample(scene_np, cams, n_pix, seed=1000 + w)
+    times = [_oracle_sample(scene_np, cams, n_pix, seed=2000 + k) for k in range(args.steps)]
+    total = sum(times)
+    px = n_pix * len(cams) * args.steps
+    value = px / total / 1e6
+    sample = (f"each step: FP64 oracle fwd+bwd of {n_pix} seeded pixels per view x {len(cams)} views of the "
+              f"1.5M-component workload, projection of all (view, component) pairs included")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 8), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(total / args.steps * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded scene and cameras)",
+        "config": {"workload": WORKLOAD, "views": len(cams), "width": cams[0].width, "height": cams[0].height,
+                   "components": scene_np["n"]},
+        "cpu_baseline": {"value": round(value, 8), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 8), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,82 @@
+"""Autotuner for the rasterizer's launch shape: tile size and staging batch.
+
+For a workload it times the whole captured train step (``train.TrainStep``)
+for every (tile_w, tile_h, batch) candidate and keeps the fastest.  Tile size
+trades pair count (bigger tiles: fewer pairs to sort, fewer splat records
+gathered) against per-warp culling efficiency; the staging batch trades
+shared memory and barrier count against wasted staging past termination.
+
+Results are stored per workload name in ``tuned.json`` next to this file;
+``cached(name)`` returns the stored choice or None.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CACHE = os.path.join(HERE, "tuned.json")
+
+TILES = ((16, 16), (32, 16), (16, 32), (32, 32))
+BATCHES = (32, 64, 128, 256)
+
+
+def cached(name: str) -> dict | None:
+    try:
+        with open(CACHE) as f:
+            return json.load(f).get(name)
+    except (OSError, ValueError):
+        return None
+
+
+def store(name: str, choice: dict, path: str = CACHE):
+    data = {}
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        pass
+    data[name] = choice
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+
+
+def tune(name: str, scene, cams, targets, candidates=None, steps: int = 5, device="cuda", log=print,
+         path: str = CACHE) -> dict:
+    """Times each candidate's captured step and stores the fastest."""
+    import torch
+
+    from . import frame as F
+    from . import train
+
+    candidates = candidates or [(tw, th, b) for (tw, th) in TILES for b in BATCHES]
+    snapshot = {f: scene.t[f].clone() for f in F.FIELDS}
+    results = []
+    for tw, th, b in candidates:
+        for f in F.FIELDS:  # every candidate starts from the same parameters
+            scene.t[f].copy_(snapshot[f])
+        cfg = F.make_cfg(tile_w=tw, tile_h=th, batch=b)
+        ts = train.TrainStep(scene, cams, targets, cfg=cfg, device=device)
+        ts.calibrate()
+        ts.capture()
+        ts.replay()
+        torch.cuda.synchronize(device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            ts.replay()
+        e1.record()
+        torch.cuda.synchronize(device)
+        ms = e0.elapsed_time(e1) / steps
+        ts.check()
+        results.append((ms, tw, th, b))
+        log(f"autotune {name}: tile {tw}x{th} batch {b}: {ms:.3f} ms/step")
+        del ts
+        torch.cuda.empty_cache()
+    for f in F.FIELDS:
+        scene.t[f].copy_(snapshot[f])
+    ms, tw, th, b = min(results)
+    choice = {"tile_w": tw, "tile_h": th, "batch": b, "ms_per_step": round(ms, 3),
+              "candidates": {f"{a}x{c}/{d}": round(m, 3) for m, a, c, d in results}}
+    store(name, choice, path)
+    return choice

@@ -1,0 +1,162 @@
+// Internal helpers shared by the libsss kernels (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sss.h"
+
+namespace sss {
+
+constexpr int kNumSMs = 152;          // GB300: 2 dies x 76 SMs
+constexpr float kFastNuMax = 64.0f;   // above this nu the log/exp pair runs on
+                                      // the accurate path (see eval_pair)
+
+// ------------------------------------------------------------ workspace
+template <typename T>
+__host__ __device__ inline T* ws_ptr(void* ws, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
+}
+template <typename T>
+__host__ __device__ inline const T* ws_ptr(const void* ws, size_t off) {
+  return reinterpret_cast<const T*>(static_cast<const char*>(ws) + off);
+}
+
+enum CtrlWord : int { kCtrlPairsNeeded = 0, kCtrlPairsSorted = 1, kCtrlStatus = 2, kCtrlEntries = 3 };
+
+// ------------------------------------------------------------ job lookup
+// Largest j in [0, n) with base(j) <= x; bases are non-decreasing.
+__device__ inline int job_of_entry(const sss_frame_plan& P, uint32_t e) {
+  int lo = 0, hi = P.n_jobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (P.jobs[mid].entry_base <= e) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ inline int job_of_tile(const sss_frame_plan& P, uint32_t t) {
+  int lo = 0, hi = P.n_jobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (P.jobs[mid].tile_base <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ inline int scene_of_comp(const sss_frame_plan& P, uint32_t g) {
+  int s = 0;
+  while (s + 1 < P.n_scenes && P.scene_comp_base[s + 1] <= g) ++s;
+  return s;
+}
+
+// ------------------------------------------------------------ launches
+#define SSS_LAUNCH_CHECK()                                  \
+  do {                                                      \
+    if (cudaPeekAtLastError() != cudaSuccess) {             \
+      (void)cudaGetLastError();                             \
+      return SSS_ERR_CUDA;                                  \
+    }                                                       \
+  } while (0)
+
+inline unsigned ceil_div(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ------------------------------------------------------------ splat record
+// Render record of one entry, three float4 (48 bytes):
+//   a = {mean2D x, mean2D y, conic a, conic b}
+//   b = {conic c, o, h_max, nu}
+//   c = {r, g, b, 1/nu}
+// h = a dx^2 + 2 b dx dy + c dy^2 with (dx, dy) = pixel centre - mean2D.
+struct SplatRec {
+  float4 a, b, c;
+};
+
+// MUFU base-2 logarithm and exponential (PTX lg2.approx / ex2.approx; the
+// PTX ISA documents their accuracy: about 2^-22 absolute for lg2 and 2^-22
+// relative for ex2).  The argument of lg2 here is >= 1, and an ex2 result that
+// would be subnormal flushes to 0, which the alpha threshold rejects anyway.
+__device__ __forceinline__ float mufu_lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float mufu_ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// One (splat, pixel) evaluation shared by the forward and backward kernels so
+// that both take identical FP32 decisions.  Returns false when the pair does
+// not contribute (outside the extent or |alpha| < tau).  Fast path: two MUFU
+// ops (lg2, ex2).  For nu > kFastNuMax the exponent -(nu+2)/2 is large enough
+// that the absolute error of lg2.approx would show, so log1pf/expf are used
+// (the branch is uniform across a warp: all lanes evaluate the same splat).
+struct PairEval {
+  float h, t2d, alpha, log_base;  // log_base = ln(1 + h/nu)
+  bool clamped;
+};
+
+__device__ __forceinline__ bool eval_pair(float dx, float dy, float ca, float cb2, float cc, float hmax_pre,
+                                          float o, float nu, float inv_nu, float tau, float amax, PairEval& r) {
+  float t = ca * dx;
+  t = fmaf(cb2, dy, t);
+  float h = fmaf(dx, t, cc * dy * dy);
+  if (!(h <= hmax_pre)) return false;
+  float e = fmaf(nu, -0.5f, -1.0f);  // -(nu + 2) / 2
+  float t2d, lb;
+  if (nu <= kFastNuMax) {
+    float base = fmaf(h, inv_nu, 1.0f);
+    float l2 = mufu_lg2(base);
+    t2d = mufu_ex2(e * l2);
+    lb = l2 * 0.69314718055994531f;
+  } else {
+    lb = log1pf(h * inv_nu);
+    t2d = expf(e * lb);
+  }
+  float alpha = o * t2d;
+  if (!(fabsf(alpha) >= tau)) return false;
+  bool cl = false;
+  if (alpha > amax) { alpha = amax; cl = true; }
+  if (alpha < -amax) { alpha = -amax; cl = true; }
+  r.h = h;
+  r.t2d = t2d;
+  r.alpha = alpha;
+  r.log_base = lb;
+  r.clamped = cl;
+  return true;
+}
+
+// Conservative test: can the ellipse h <= hmax_test reach the axis-aligned box
+// [x0, x1] x [y0, y1] of pixel centres?  The minimum of the convex quadratic
+// over the box is 0 if the centre is inside, else it lies on an edge facing
+// the centre, where it is a clamped 1D minimum.
+__device__ __forceinline__ bool ellipse_hits_box(float mx, float my, float ca, float cb, float cc,
+                                                 float hmax_test, float x0, float x1, float y0, float y1) {
+  bool inx = (mx >= x0) && (mx <= x1);
+  bool iny = (my >= y0) && (my <= y1);
+  if (inx && iny) return true;
+  float hmin = 3.0e38f;
+  if (!inx) {
+    float dx = (mx < x0 ? x0 : x1) - mx;
+    float dy = fminf(fmaxf(-cb * dx / cc, y0 - my), y1 - my);
+    float h = ca * dx * dx + 2.0f * cb * dx * dy + cc * dy * dy;
+    hmin = fminf(hmin, h);
+  }
+  if (!iny) {
+    float dy = (my < y0 ? y0 : y1) - my;
+    float dx = fminf(fmaxf(-cb * dy / ca, x0 - mx), x1 - mx);
+    float h = ca * dx * dx + 2.0f * cb * dx * dy + cc * dy * dy;
+    hmin = fminf(hmin, h);
+  }
+  return hmin <= hmax_test;
+}
+
+// Margin of the per-pixel prefilter over h_max (relative).  Pairs with
+// h <= h_max (1 + kHPad) are evaluated exactly; the |alpha| >= tau test then
+// decides.  Pairs beyond it have |alpha| below tau by far more than the FP32
+// error of alpha.
+constexpr float kHPad = 1e-3f;
+
+// ------------------------------------------------------------ warp helpers
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+}  // namespace sss

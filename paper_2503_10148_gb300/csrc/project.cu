@@ -1,0 +1,102 @@
+// a1: projection of 3D t-components to 2D t-splats (Sec. 3.2 Eq. t_2D).
+//
+// One thread per (scene, component): the component's parameters (60 floats
+// at SH degree 3) are read once, coalesced from the planar arrays, and every
+// job (view) of that scene is projected from registers.  Per (job, component)
+// entry the kernel writes the 48-byte render record, the FP32 depth key, the
+// tile count and the tile rectangle.  HBM traffic per component: 240 B read
+// (degree 3) + 64 B written per view.
+#include "proj_geom.cuh"
+
+namespace sss {
+
+template <int DEG>
+__device__ __forceinline__ void project_component(const sss_frame_plan& P, int s, uint32_t i, void* ws) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  const sss_params& S = P.scenes[s];
+  const sss_raster_cfg& cfg = P.cfg;
+  const CompParams c = load_comp(S, i);
+  const CompShape g = comp_shape(c);
+  float sh[3 * K];
+#pragma unroll
+  for (int k = 0; k < 3 * K; ++k) sh[k] = __ldg(S.sh + (size_t)k * S.n + i);
+
+  SplatRec* rec = ws_ptr<SplatRec>(ws, P.ws_off_rec);
+  uint32_t* dkey = ws_ptr<uint32_t>(ws, P.ws_off_dkey);
+  uint32_t* ntiles = ws_ptr<uint32_t>(ws, P.ws_off_ntiles);
+  uint2* rect = ws_ptr<uint2>(ws, P.ws_off_rect);
+
+  for (int q = P.scene_job_begin[s]; q < P.scene_job_begin[s + 1]; ++q) {
+    const sss_job_desc& J = P.jobs[P.scene_jobs[q]];
+    const uint32_t e = J.entry_base + i;
+    const ViewGeom v = view_geom(c, g, J.cam, cfg);
+    if (!v.valid) {
+      dkey[e] = 0xffffffffu;
+      ntiles[e] = 0u;
+      rect[e] = make_uint2(0u, 0u);
+      continue;
+    }
+    // extent: |o| T2D(h) >= tau  <=>  h <= h_max (reading of the SM's truncation)
+    const float hmax = v.nu * expm1f(2.0f / (v.nu + 2.0f) * logf(fabsf(v.o) / cfg.tau));
+    const float ex = sqrtf(v.A * hmax), ey = sqrtf(v.C * hmax);
+    float fx0 = fmaxf(ceilf(v.m2[0] - ex - 0.5f), 0.0f);
+    float fx1 = fminf(floorf(v.m2[0] + ex - 0.5f), (float)(J.cam.width - 1));
+    float fy0 = fmaxf(ceilf(v.m2[1] - ey - 0.5f), 0.0f);
+    float fy1 = fminf(floorf(v.m2[1] + ey - 0.5f), (float)(J.cam.height - 1));
+    uint32_t nt = 0;
+    uint2 rc = make_uint2(0u, 0u);
+    if (fx0 <= fx1 && fy0 <= fy1) {
+      const uint32_t tx0 = (uint32_t)fx0 / (uint32_t)cfg.tile_w, tx1 = (uint32_t)fx1 / (uint32_t)cfg.tile_w;
+      const uint32_t ty0 = (uint32_t)fy0 / (uint32_t)cfg.tile_h, ty1 = (uint32_t)fy1 / (uint32_t)cfg.tile_h;
+      nt = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+      rc = make_uint2(tx0 | (tx1 << 16), ty0 | (ty1 << 16));
+    }
+    // view-dependent colour: max(SH . Y(dir) + 0.5, 0)
+    float cc[3];
+    cam_centre(J.cam, cc);
+    float d0 = c.mu[0] - cc[0], d1 = c.mu[1] - cc[1], d2 = c.mu[2] - cc[2];
+    const float il = 1.0f / sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    float Y[K];
+    sh_basis<DEG>(d0 * il, d1 * il, d2 * il, Y);
+    float rgb[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float acc = 0.5f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc = fmaf(sh[3 * k + ch], Y[k], acc);
+      rgb[ch] = fmaxf(acc, 0.0f);
+    }
+    SplatRec r;
+    r.a = make_float4(v.m2[0], v.m2[1], v.con[0], v.con[1]);
+    r.b = make_float4(v.con[2], v.o, hmax, v.nu);
+    r.c = make_float4(rgb[0], rgb[1], rgb[2], 1.0f / v.nu);
+    rec[e] = r;
+    dkey[e] = __float_as_uint(v.p[2]);
+    ntiles[e] = nt;
+    rect[e] = rc;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_project(const sss_frame_plan P, void* ws) {
+  const uint32_t gidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gidx >= P.scene_comp_base[P.n_scenes]) return;
+  const int s = scene_of_comp(P, gidx);
+  const uint32_t i = gidx - P.scene_comp_base[s];
+  switch (P.scenes[s].sh_degree) {
+    case 0: project_component<0>(P, s, i, ws); break;
+    case 1: project_component<1>(P, s, i, ws); break;
+    case 2: project_component<2>(P, s, i, ws); break;
+    default: project_component<3>(P, s, i, ws); break;
+  }
+}
+
+}  // namespace sss
+
+extern "C" int sss_project(const sss_frame_plan* plan, void* ws, sss_stream_t stream) {
+  if (!plan || !ws) return SSS_ERR_INVALID_ARG;
+  const uint32_t total = plan->scene_comp_base[plan->n_scenes];
+  if (total == 0) return SSS_OK;
+  sss::k_project<<<sss::ceil_div(total, 256), 256, 0, (cudaStream_t)stream>>>(*plan, ws);
+  SSS_LAUNCH_CHECK();
+  return SSS_OK;
+}

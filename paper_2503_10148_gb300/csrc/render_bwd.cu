@@ -1,0 +1,226 @@
+// a5: closed-form backward of the compositing (SM "Backward Pass").
+//
+// Same CTA/warp/lane layout as the forward.  Each pixel walks its tile's list
+// from its last contributor back to the front, recomputing the transmittance
+// before every contributor as T_k = T_{k+1} / (1 - alpha_k) (no per-pixel
+// lists are stored), and keeps S = colour composited behind the current
+// splat + T_final bg.  For a contributor k:
+//   dL/drgb   = alpha T_k g                               (g = dL/dC)
+//   dL/dalpha = g . (T_k rgb - S / (1 - alpha))
+//   dL/do     = dL/dalpha T2D,  dL/dT2D = dL/dalpha o   (unless alpha was clamped)
+//   dL/dh     = dL/dT2D dT2D/dh,  dT2D/dh = -(nu+2)/(2 nu) T2D / (1 + h/nu)
+//   dL/dnu    = dL/dT2D T2D [-1/2 ln(1 + h/nu) + (nu+2) h / (2 nu^2 (1 + h/nu))]
+//               (mode 1 drops the logarithm, as printed in the SM)
+//   dh/dmean2D = -2 conic d,  dh/d(a, b, c) = (dx^2, 2 dx dy, dy^2).
+// A lane first sums its pixels; the warp then reduces the 10 sums with a
+// 16-slot reduce-scatter (16 shuffles instead of 10 x 5) and 10 lanes add the
+// totals to the splat's record with one vectorless RED each.
+#include "common.cuh"
+
+namespace sss {
+namespace {
+
+// v[0..15] summed over the warp; lane l ends with the total of slot
+// (l >> 1) & 15 in v[0].
+__device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], unsigned lane) {
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int h = 8 >> r;
+    const unsigned m = 16u >> r;
+    const bool upper = (lane & m) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float send = upper ? v[i] : v[i + h];
+      const float keep = upper ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+    }
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  return v[0];
+}
+
+template <int PW, int PH, int B>
+__global__ void __launch_bounds__(256) k_render_bwd(const sss_frame_plan P, void* ws,
+                                                    const float* __restrict__ dl_drgb) {
+  constexpr int NPIX = PW * PH;
+  constexpr int TW = 16 * PW, TH = 16 * PH;
+  constexpr int NW = B / 32;
+  __shared__ float4 s_a[B], s_b[B], s_c[B];
+  __shared__ uint32_t s_e[B];
+  __shared__ uint32_t s_top;
+
+  const uint32_t tile = blockIdx.x;
+  const int j = job_of_tile(P, tile);
+  const sss_job_desc& J = P.jobs[j];
+  const sss_raster_cfg& cfg = P.cfg;
+  const uint32_t lt = tile - J.tile_base;
+  const int tx = (int)(lt % (uint32_t)J.tiles_x), ty = (int)(lt / (uint32_t)J.tiles_x);
+  const int warp = threadIdx.x >> 5;
+  const unsigned lane = threadIdx.x & 31;
+  const int bx = tx * TW + (warp & 1) * 8 * PW, by = ty * TH + (warp >> 1) * 4 * PH;
+  const int lx = bx + (lane & 7) * PW, ly = by + (lane >> 3) * PH;
+  const int W = J.cam.width, H = J.cam.height;
+  const float box_x0 = bx + 0.5f, box_x1 = bx + 8 * PW - 0.5f;
+  const float box_y0 = by + 0.5f, box_y1 = by + 4 * PH - 0.5f;
+  const size_t hw = (size_t)W * H;
+
+  const float* Tf = ws_ptr<float>(ws, P.ws_off_T);
+  const uint32_t* Lf = ws_ptr<uint32_t>(ws, P.ws_off_last);
+  const float* gimg = dl_drgb + 3 * (size_t)J.pix_base;
+  float T[NPIX], S[NPIX][3], g[NPIX][3];
+  uint32_t last[NPIX];
+  uint32_t lane_max = 0;
+#pragma unroll
+  for (int p = 0; p < NPIX; ++p) {
+    const int x = lx + p % PW, y = ly + p / PW;
+    if (x < W && y < H) {
+      const size_t o = (size_t)y * W + x;
+      T[p] = Tf[J.pix_base + o];
+      last[p] = Lf[J.pix_base + o];
+      g[p][0] = gimg[o];
+      g[p][1] = gimg[hw + o];
+      g[p][2] = gimg[2 * hw + o];
+    } else {
+      T[p] = 1.0f;
+      last[p] = 0u;
+      g[p][0] = g[p][1] = g[p][2] = 0.0f;
+    }
+    S[p][0] = T[p] * cfg.bg[0];
+    S[p][1] = T[p] * cfg.bg[1];
+    S[p][2] = T[p] * cfg.bg[2];
+    lane_max = max(lane_max, last[p]);
+  }
+  const uint32_t warp_max = __reduce_max_sync(0xffffffffu, lane_max);
+  if (threadIdx.x == 0) s_top = 0;
+  __syncthreads();
+  if (lane == 0) atomicMax(&s_top, warp_max);
+  __syncthreads();
+  const uint32_t top = s_top;
+
+  const uint2 range = ws_ptr<uint2>(ws, P.ws_off_ranges)[tile];
+  const uint32_t* vals = ws_ptr<uint32_t>(ws, P.ws_off_pval) + (size_t)P.pair_slot * P.pair_capacity;
+  const SplatRec* rec = ws_ptr<SplatRec>(ws, P.ws_off_rec);
+  float* g2d = ws_ptr<float>(ws, P.ws_off_grad2d);
+  const float tau = cfg.tau, amax = cfg.alpha_max;
+  const bool paper_nu = cfg.nu_grad_mode == 1;
+
+  // list positions are relative to range.x; pixel p has contributors in [0, last[p])
+  for (uint32_t hi = top; hi > 0;) {
+    const uint32_t lo = hi > (uint32_t)B ? hi - B : 0u;
+    const uint32_t cnt = hi - lo;
+    __syncthreads();
+    if (threadIdx.x < B) {
+      if (threadIdx.x < cnt) {
+        const uint32_t e = vals[range.x + lo + threadIdx.x];
+        const SplatRec r = rec[e];
+        s_a[threadIdx.x] = r.a;
+        s_b[threadIdx.x] = r.b;
+        s_c[threadIdx.x] = r.c;
+        s_e[threadIdx.x] = e;
+      } else {
+        s_b[threadIdx.x] = make_float4(1.0f, 0.0f, -1.0f, 1.0f);
+      }
+    }
+    __syncthreads();
+    if (lo < warp_max) {
+      unsigned mask[NW];
+#pragma unroll
+      for (int k = 0; k < NW; ++k) {
+        const float4 a = s_a[k * 32 + lane], b = s_b[k * 32 + lane];
+        const bool hit = b.z >= 0.0f && (lo + k * 32 + lane) < warp_max &&
+                         ellipse_hits_box(a.x, a.y, a.z, a.w, b.x, fmaf(b.z, 2.0f * kHPad, b.z) + 1e-3f, box_x0,
+                                          box_x1, box_y0, box_y1);
+        mask[k] = __ballot_sync(0xffffffffu, hit);
+      }
+#pragma unroll
+      for (int k = NW - 1; k >= 0; --k) {
+        unsigned m = mask[k];
+        while (m) {
+          const int bit = 31 - __clz(m);
+          m &= ~(1u << bit);
+          const int si = k * 32 + bit;
+          const uint32_t pos = lo + si;
+          const float4 a = s_a[si], b = s_b[si], c = s_c[si];
+          const float cb2 = 2.0f * a.w, hpre = fmaf(b.z, kHPad, b.z);
+          const float nu = b.w, inv_nu = c.w, o = b.y;
+          const float e_exp = fmaf(nu, -0.5f, -1.0f);  // -(nu+2)/2
+          float v[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+          bool any = false;
+#pragma unroll
+          for (int p = 0; p < NPIX; ++p) {
+            if (pos >= last[p]) continue;
+            const float dx = (float)(lx + p % PW) + 0.5f - a.x;
+            const float dy = (float)(ly + p / PW) + 0.5f - a.y;
+            PairEval r;
+            if (!eval_pair(dx, dy, a.z, cb2, b.x, hpre, o, nu, inv_nu, tau, amax, r)) continue;
+            any = true;
+            const float inv_1ma = __fdividef(1.0f, 1.0f - r.alpha);
+            const float Tk = T[p] * inv_1ma;
+            T[p] = Tk;
+            const float w = r.alpha * Tk;
+            float dl_da = 0.0f;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+              const float cch = ch == 0 ? c.x : (ch == 1 ? c.y : c.z);
+              v[7 + ch] = fmaf(w, g[p][ch], v[7 + ch]);
+              dl_da = fmaf(g[p][ch], fmaf(Tk, cch, -S[p][ch] * inv_1ma), dl_da);
+              S[p][ch] = fmaf(w, cch, S[p][ch]);
+            }
+            if (r.clamped) continue;
+            v[5] = fmaf(dl_da, r.t2d, v[5]);
+            const float dl_dt = dl_da * o;
+            const float inv_base = __fdividef(1.0f, fmaf(r.h, inv_nu, 1.0f));
+            const float dl_dh = dl_dt * e_exp * inv_nu * r.t2d * inv_base;
+            const float second = -e_exp * r.h * inv_nu * inv_nu * inv_base;
+            const float dnu = paper_nu ? second : fmaf(-0.5f, r.log_base, second);
+            v[6] = fmaf(dl_dt * r.t2d, dnu, v[6]);
+            v[0] = fmaf(dl_dh, -2.0f * fmaf(a.z, dx, a.w * dy), v[0]);
+            v[1] = fmaf(dl_dh, -2.0f * fmaf(a.w, dx, b.x * dy), v[1]);
+            v[2] = fmaf(dl_dh, dx * dx, v[2]);
+            v[3] = fmaf(dl_dh, 2.0f * dx * dy, v[3]);
+            v[4] = fmaf(dl_dh, dy * dy, v[4]);
+          }
+          if (__any_sync(0xffffffffu, any)) {
+            const float tot = warp_reduce_scatter16(v, lane);
+            const unsigned slot = (lane >> 1) & 15u;
+            if ((lane & 1u) == 0u && slot < 10u) atomicAdd(g2d + (size_t)s_e[si] * 12 + slot, tot);
+          }
+        }
+      }
+    }
+    hi = lo;
+  }
+}
+
+template <int PW, int PH>
+int launch_batch(const sss_frame_plan& P, void* ws, const float* g, cudaStream_t st) {
+  const unsigned grid = P.n_tiles;
+  switch (P.cfg.batch) {
+    case 32: k_render_bwd<PW, PH, 32><<<grid, 256, 0, st>>>(P, ws, g); break;
+    case 64: k_render_bwd<PW, PH, 64><<<grid, 256, 0, st>>>(P, ws, g); break;
+    case 128: k_render_bwd<PW, PH, 128><<<grid, 256, 0, st>>>(P, ws, g); break;
+    case 256: k_render_bwd<PW, PH, 256><<<grid, 256, 0, st>>>(P, ws, g); break;
+    default: return SSS_ERR_UNSUPPORTED;
+  }
+  SSS_LAUNCH_CHECK();
+  return SSS_OK;
+}
+
+}  // namespace
+}  // namespace sss
+
+extern "C" int sss_render_bwd(const sss_frame_plan* plan, void* ws, const float* dL_drgb, sss_stream_t stream) {
+  if (!plan || !ws || !dL_drgb) return SSS_ERR_INVALID_ARG;
+  const sss_frame_plan& P = *plan;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(sss::ws_ptr<float>(ws, P.ws_off_grad2d), 0, 48 * (size_t)P.n_entries, st) != cudaSuccess)
+    return SSS_ERR_CUDA;
+  const int pw = P.cfg.tile_w / 16, ph = P.cfg.tile_h / 16;
+  if (pw == 1 && ph == 1) return sss::launch_batch<1, 1>(P, ws, dL_drgb, st);
+  if (pw == 2 && ph == 1) return sss::launch_batch<2, 1>(P, ws, dL_drgb, st);
+  if (pw == 1 && ph == 2) return sss::launch_batch<1, 2>(P, ws, dL_drgb, st);
+  if (pw == 2 && ph == 2) return sss::launch_batch<2, 2>(P, ws, dL_drgb, st);
+  return SSS_ERR_UNSUPPORTED;
+}

@@ -1,0 +1,176 @@
+// a4: per-pixel front-to-back compositing with signed alpha
+// (Sec. 3.4 Eq. SSS_color; signed opacity Sec. 3.3).
+//
+// One CTA of 256 threads per image tile of (16 PW) x (16 PH) pixels.  Warps
+// are laid out 2 x 4 over the tile; warp w owns an (8 PW) x (4 PH) box and
+// lane l a PW x PH block of pixels inside it.  The tile's splat list is
+// staged in shared memory B splats at a time (48-byte records gathered by
+// entry index).  Each warp then tests the B staged splats against its own
+// box in parallel (one splat per lane, exact ellipse/box test) and walks
+// only the survivors, in list (= depth) order, so pairs whose ellipse misses
+// the warp's 32 PW PH pixels cost nothing.  A warp stops evaluating when all
+// its pixels are done; the CTA stops staging when all warps are done.
+#include "common.cuh"
+
+namespace sss {
+namespace {
+
+template <int PW, int PH, int B>
+__global__ void __launch_bounds__(256) k_render_fwd(const sss_frame_plan P, void* ws, float* __restrict__ out_rgb) {
+  constexpr int NPIX = PW * PH;
+  constexpr int TW = 16 * PW, TH = 16 * PH;
+  constexpr int NW = B / 32;
+  __shared__ float4 s_a[B], s_b[B], s_c[B];
+
+  const uint32_t tile = blockIdx.x;
+  const int j = job_of_tile(P, tile);
+  const sss_job_desc& J = P.jobs[j];
+  const sss_raster_cfg& cfg = P.cfg;
+  const uint32_t lt = tile - J.tile_base;
+  const int tx = (int)(lt % (uint32_t)J.tiles_x), ty = (int)(lt / (uint32_t)J.tiles_x);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bx = tx * TW + (warp & 1) * 8 * PW, by = ty * TH + (warp >> 1) * 4 * PH;
+  const int lx = bx + (lane & 7) * PW, ly = by + (lane >> 3) * PH;
+  const int W = J.cam.width, H = J.cam.height;
+  const float box_x0 = bx + 0.5f, box_x1 = bx + 8 * PW - 0.5f;
+  const float box_y0 = by + 0.5f, box_y1 = by + 4 * PH - 0.5f;
+
+  float T[NPIX], C[NPIX][3];
+  uint32_t last[NPIX];
+  bool done[NPIX];
+#pragma unroll
+  for (int p = 0; p < NPIX; ++p) {
+    const int x = lx + p % PW, y = ly + p / PW;
+    done[p] = !(x < W && y < H);
+    T[p] = 1.0f;
+    C[p][0] = C[p][1] = C[p][2] = 0.0f;
+    last[p] = 0u;
+  }
+  bool lane_done = true;
+#pragma unroll
+  for (int p = 0; p < NPIX; ++p) lane_done = lane_done && done[p];
+  bool warp_done = __all_sync(0xffffffffu, lane_done);
+
+  const uint2 range = ws_ptr<uint2>(ws, P.ws_off_ranges)[tile];
+  const uint32_t* vals = ws_ptr<uint32_t>(ws, P.ws_off_pval) + (size_t)P.pair_slot * P.pair_capacity;
+  const SplatRec* rec = ws_ptr<SplatRec>(ws, P.ws_off_rec);
+  const float tau = cfg.tau, amax = cfg.alpha_max, tmin = cfg.t_min;
+  uint32_t n_eval = 0, n_contrib = 0;  // pair counters for the roofline
+
+  for (uint32_t b0 = range.x; b0 < range.y; b0 += B) {
+    if (__syncthreads_count(!warp_done) == 0) break;
+    const uint32_t cnt = min((uint32_t)B, range.y - b0);
+    if (threadIdx.x < B) {
+      if (threadIdx.x < cnt) {
+        const SplatRec r = rec[vals[b0 + threadIdx.x]];
+        s_a[threadIdx.x] = r.a;
+        s_b[threadIdx.x] = r.b;
+        s_c[threadIdx.x] = r.c;
+      } else {
+        s_b[threadIdx.x] = make_float4(1.0f, 0.0f, -1.0f, 1.0f);  // h_max < 0: never hits
+      }
+    }
+    __syncthreads();
+    if (warp_done) continue;
+    unsigned mask[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      const float4 a = s_a[k * 32 + lane], b = s_b[k * 32 + lane];
+      const bool hit = b.z >= 0.0f &&
+                       ellipse_hits_box(a.x, a.y, a.z, a.w, b.x, fmaf(b.z, 2.0f * kHPad, b.z) + 1e-3f, box_x0,
+                                        box_x1, box_y0, box_y1);
+      mask[k] = __ballot_sync(0xffffffffu, hit);
+    }
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      unsigned m = mask[k];
+      while (m && !warp_done) {
+        const int bit = __ffs(m) - 1;
+        m &= m - 1;
+        const int si = k * 32 + bit;
+        const float4 a = s_a[si], b = s_b[si], c = s_c[si];
+        const float cb2 = 2.0f * a.w, hpre = fmaf(b.z, kHPad, b.z);
+        const uint32_t pos1 = b0 + si - range.x + 1;
+#pragma unroll
+        for (int p = 0; p < NPIX; ++p) {
+          if (done[p]) continue;
+          const float dx = (float)(lx + p % PW) + 0.5f - a.x;
+          const float dy = (float)(ly + p / PW) + 0.5f - a.y;
+          PairEval r;
+          ++n_eval;
+          if (!eval_pair(dx, dy, a.z, cb2, b.x, hpre, b.y, b.w, c.w, tau, amax, r)) continue;
+          const float Tn = T[p] * (1.0f - r.alpha);
+          if (Tn < tmin) {
+            done[p] = true;
+            continue;
+          }
+          const float w = r.alpha * T[p];
+          C[p][0] = fmaf(w, c.x, C[p][0]);
+          C[p][1] = fmaf(w, c.y, C[p][1]);
+          C[p][2] = fmaf(w, c.z, C[p][2]);
+          T[p] = Tn;
+          last[p] = pos1;
+          ++n_contrib;
+        }
+        bool ld = true;
+#pragma unroll
+        for (int p = 0; p < NPIX; ++p) ld = ld && done[p];
+        warp_done = __all_sync(0xffffffffu, ld);
+      }
+    }
+  }
+
+  {
+    const uint32_t ne = __reduce_add_sync(0xffffffffu, n_eval), nc = __reduce_add_sync(0xffffffffu, n_contrib);
+    if ((threadIdx.x & 31) == 0 && ne) {
+      unsigned long long* ctr = reinterpret_cast<unsigned long long*>(ws_ptr<uint32_t>(ws, P.ws_off_ctrl) + 4);
+      atomicAdd(ctr, (unsigned long long)nc);
+      atomicAdd(ctr + 1, (unsigned long long)ne);
+    }
+  }
+  float* Tout = ws_ptr<float>(ws, P.ws_off_T);
+  uint32_t* Lout = ws_ptr<uint32_t>(ws, P.ws_off_last);
+  const size_t hw = (size_t)W * H;
+  float* img = out_rgb + 3 * (size_t)J.pix_base;
+#pragma unroll
+  for (int p = 0; p < NPIX; ++p) {
+    const int x = lx + p % PW, y = ly + p / PW;
+    if (x < W && y < H) {
+      const size_t o = (size_t)y * W + x;
+      img[o] = fmaf(T[p], cfg.bg[0], C[p][0]);
+      img[hw + o] = fmaf(T[p], cfg.bg[1], C[p][1]);
+      img[2 * hw + o] = fmaf(T[p], cfg.bg[2], C[p][2]);
+      Tout[J.pix_base + o] = T[p];
+      Lout[J.pix_base + o] = last[p];
+    }
+  }
+}
+
+template <int PW, int PH>
+int launch_batch(const sss_frame_plan& P, void* ws, float* out, cudaStream_t st) {
+  const unsigned grid = P.n_tiles;
+  switch (P.cfg.batch) {
+    case 32: k_render_fwd<PW, PH, 32><<<grid, 256, 0, st>>>(P, ws, out); break;
+    case 64: k_render_fwd<PW, PH, 64><<<grid, 256, 0, st>>>(P, ws, out); break;
+    case 128: k_render_fwd<PW, PH, 128><<<grid, 256, 0, st>>>(P, ws, out); break;
+    case 256: k_render_fwd<PW, PH, 256><<<grid, 256, 0, st>>>(P, ws, out); break;
+    default: return SSS_ERR_UNSUPPORTED;
+  }
+  SSS_LAUNCH_CHECK();
+  return SSS_OK;
+}
+
+}  // namespace
+}  // namespace sss
+
+extern "C" int sss_render_fwd(const sss_frame_plan* plan, void* ws, float* out_rgb, sss_stream_t stream) {
+  if (!plan || !ws || !out_rgb) return SSS_ERR_INVALID_ARG;
+  const sss_frame_plan& P = *plan;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int pw = P.cfg.tile_w / 16, ph = P.cfg.tile_h / 16;
+  if (pw == 1 && ph == 1) return sss::launch_batch<1, 1>(P, ws, out_rgb, st);
+  if (pw == 2 && ph == 1) return sss::launch_batch<2, 1>(P, ws, out_rgb, st);
+  if (pw == 1 && ph == 2) return sss::launch_batch<1, 2>(P, ws, out_rgb, st);
+  if (pw == 2 && ph == 2) return sss::launch_batch<2, 2>(P, ws, out_rgb, st);
+  return SSS_ERR_UNSUPPORTED;
+}

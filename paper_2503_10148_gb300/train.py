@@ -1,0 +1,119 @@
+"""One training step of the method, plain or captured into a CUDA graph.
+
+A step on one scene with V views is: project, bin, sort and forward-render
+all V views as one frame; L1 loss against the V target images (value and
+dL/dC); backward render and projection backward (gradients summed over the
+views); SGHMC on the means and Adam on the rest.  Every step is a libsss
+entry point; nothing is computed in Python.
+
+``TrainStep.capture()`` records the whole step (about 40 kernels) into one
+CUDA graph.  The number of (tile, splat) pairs is data dependent, so the
+frame is planned with a pair capacity measured on an eager step plus
+headroom; the device status word (checked with ``check()``) reports an
+overflow instead of a host sync inside the step.
+
+``PlainStep`` is the reference form the batched one is compared with: one
+frame per view, launched eagerly one after the other.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import frame as F
+
+
+class TrainStep:
+    def __init__(self, scene: F.Scene, cams, targets: torch.Tensor, cfg=None, sampler: dict | None = None,
+                 headroom: float = 1.5, device="cuda"):
+        self.scene = scene
+        self.cams = list(cams)
+        self.device = torch.device(device)
+        self.cfg = cfg if cfg is not None else F.make_cfg()
+        self.frame = F.Frame([scene], self.cams, cfg=self.cfg, device=self.device)
+        assert targets.numel() == self.frame.rgb.numel() and targets.dtype == torch.float32
+        self.targets = targets
+        self.grads = scene.zeros_like()
+        self.state = F.SamplerState(scene)
+        self.dl = torch.zeros_like(self.frame.rgb)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        self.step_counter = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self.sp = F.step_params(step_counter=self.step_counter, **(sampler or {}))
+        self.headroom = headroom
+        self.graph = None
+
+    def calibrate(self):
+        """Eager forward with capacity growth, then re-plan with headroom."""
+        self.frame.forward(grow=True)
+        _, need, _ = self.frame.status()
+        cap = max(int(need * self.headroom) + 4096, 1 << 16)
+        if cap != self.frame.pair_capacity:
+            self.frame.pair_capacity = cap
+            self.frame._replan()
+        return need
+
+    def run(self):
+        """Enqueue one step on the current stream (no host synchronisation)."""
+        st = torch.cuda.current_stream(self.device)
+        fr = self.frame
+        self.loss.zero_()
+        fr.project(st)
+        fr.bin(st)
+        fr.sort(st)
+        fr.render_fwd(st)
+        F.loss_l1(fr.rgb, self.targets, self.dl, self.loss, st)
+        fr.render_bwd(self.dl, st)
+        fr.project_bwd([self.grads], st)
+        F.sghmc_step(self.scene, self.grads, self.state, self.sp, stream=st)
+
+    def capture(self):
+        self.run()  # warm-up on the capture-free path (lazy module loading)
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run()
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def check(self):
+        """(status bits, pairs needed, pairs sorted); raises on overflow."""
+        st, need, done = self.frame.status()
+        if st:
+            raise RuntimeError(f"pair capacity {self.frame.pair_capacity} exceeded: {need} pairs needed")
+        return st, need, done
+
+
+class PlainStep:
+    """Same step with one frame per view, launched eagerly view after view."""
+
+    def __init__(self, scene: F.Scene, cams, targets: torch.Tensor, cfg=None, sampler: dict | None = None,
+                 device="cuda"):
+        self.scene = scene
+        self.device = torch.device(device)
+        self.cfg = cfg if cfg is not None else F.make_cfg()
+        self.frames = [F.Frame([scene], [c], cfg=self.cfg, device=self.device) for c in cams]
+        self.targets = []
+        off = 0
+        for fr in self.frames:
+            n = fr.rgb.numel()
+            self.targets.append(targets[off:off + n])
+            off += n
+        self.grads = [scene.zeros_like() for _ in self.frames]
+        self.total = scene.zeros_like()
+        self.state = F.SamplerState(scene)
+        self.dl = [torch.zeros_like(fr.rgb) for fr in self.frames]
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        self.step_counter = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self.sp = F.step_params(step_counter=self.step_counter, **(sampler or {}))
+
+    def run(self):
+        self.loss.zero_()
+        for fr, tgt, dl, g in zip(self.frames, self.targets, self.dl, self.grads):
+            fr.forward(grow=True)
+            F.loss_l1(fr.rgb, tgt, dl, self.loss)
+            fr.backward(dl, [g])
+        for f in F.FIELDS:
+            torch.stack([g.t[f] for g in self.grads]).sum(0, out=self.total.t[f])
+        F.sghmc_step(self.scene, self.total, self.state, self.sp)

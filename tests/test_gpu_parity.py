@@ -1,0 +1,457 @@
+"""GPU parity of every hot-path step against the FP64 oracle, through the C ABI.
+
+Bars: tile lists and sorted keys bit-exact; forward <= 1e-4 max-abs per pixel
+channel (pixels the oracle flags as within rounding distance of a discrete
+decision are excluded and counted); gradients <= 1e-3 relative per element
+(against max(|g_ref|, 1e-2 x the group maximum)) and <= 1e-4 relative L2 per
+group; sampler noise and updates within FP32 rounding.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2503_10148_gb300 import _abi, frame, inputs
+
+from gpu_util import (DEV, GRAD_FLOOR, GRAD_REL, GRAD_NORM, assert_groups_close, f32_scene, gpu_forward,
+                      masked_weights, oracle_views, require_gpu, scene_grads_flat)
+
+pytestmark = pytest.mark.gpu
+
+FWD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+# ---------------------------------------------------------------- a1 project
+
+def _check_projection(fr, scene, cams, cfgd):
+    recs = fr.records().cpu().numpy().astype(np.float64)
+    dkey = _u32(fr.depth_keys())
+    nt = fr.ntiles().cpu().numpy()
+    rect = _u32(fr.rects())
+    n = scene["n"]
+    for j, cam in enumerate(cams):
+        ref = oracle.project(scene, cam, cfgd)
+        eb = fr.plan.jobs[j].entry_base
+        sl = slice(eb, eb + n)
+        valid_ref = ref[:, oracle.P["valid"]] != 0
+        valid_gpu = dkey[sl] != 0xFFFFFFFF
+        assert np.array_equal(valid_ref, valid_gpu), int((valid_ref != valid_gpu).sum())
+        # FP32 depth keys: same FMA chain on both sides -> bit-exact
+        ref_bits = ref[valid_ref, oracle.P["depth"]].astype(np.float32).view(np.uint32)
+        assert np.array_equal(ref_bits, dkey[sl][valid_ref])
+        r = recs[sl][valid_ref]
+        rf = ref[valid_ref]
+        assert np.allclose(r[:, 0], rf[:, oracle.P["mx"]], rtol=0, atol=2e-3)
+        assert np.allclose(r[:, 1], rf[:, oracle.P["my"]], rtol=0, atol=2e-3)
+        scale = np.maximum(np.abs(rf[:, oracle.P["con_a"]]), np.abs(rf[:, oracle.P["con_c"]]))
+        for col, key in ((2, "con_a"), (3, "con_b"), (4, "con_c")):
+            assert np.all(np.abs(r[:, col] - rf[:, oracle.P[key]]) <= 2e-4 * scale), key
+        assert np.allclose(r[:, 5], rf[:, oracle.P["o"]], rtol=0, atol=2e-6)
+        assert np.allclose(r[:, 6], rf[:, oracle.P["hmax"]], rtol=2e-5, atol=1e-5)
+        assert np.allclose(r[:, 7], rf[:, oracle.P["nu"]], rtol=1e-6)
+        for col, key in ((8, "r"), (9, "g"), (10, "b")):
+            assert np.allclose(r[:, col], rf[:, oracle.P[key]], rtol=0, atol=2e-5), key
+        # tile rectangles: equal except where a box edge sits within 1e-3 px of
+        # a pixel-centre boundary (FP32 ceil/floor there is a coin toss)
+        ex = np.sqrt(rf[:, oracle.P["cov_a"]] * rf[:, oracle.P["hmax"]])
+        ey = np.sqrt(rf[:, oracle.P["cov_c"]] * rf[:, oracle.P["hmax"]])
+        edges = np.stack([rf[:, oracle.P["mx"]] - ex - 0.5, rf[:, oracle.P["mx"]] + ex - 0.5,
+                          rf[:, oracle.P["my"]] - ey - 0.5, rf[:, oracle.P["my"]] + ey - 0.5], 1)
+        fragile = np.any(np.abs(edges - np.round(edges)) < 1e-3, axis=1)
+        rg = rect[sl][valid_ref]
+        tx0, tx1 = rg[:, 0] & 0xFFFF, rg[:, 0] >> 16
+        ty0, ty1 = rg[:, 1] & 0xFFFF, rg[:, 1] >> 16
+        ntr = rf[:, oracle.P["ntiles"]]
+        has = ntr > 0
+        same = (nt[sl][valid_ref] == ntr) & (~has | ((tx0 == rf[:, oracle.P["tx0"]]) & (tx1 == rf[:, oracle.P["tx1"]])
+                                                      & (ty0 == rf[:, oracle.P["ty0"]]) & (ty1 == rf[:, oracle.P["ty1"]])))
+        assert np.all(same | fragile), int((~same & ~fragile).sum())
+        assert fragile.mean() < 0.03, fragile.mean()
+
+
+def test_project_tiny():
+    scene, cams = inputs.tiny_cube_2k()
+    fr, _, cams = gpu_forward(scene, cams)
+    _check_projection(fr, f32_scene(scene), cams, frame.cfg_dict(fr.cfg))
+
+
+def test_project_shell_sh3_multiview():
+    scene, cams = inputs.shell_100k_8views()
+    scene = inputs.subset_scene(scene, np.arange(0, 100_000, 5))
+    fr, _, cams = gpu_forward(scene, cams)
+    _check_projection(fr, f32_scene(scene), cams, frame.cfg_dict(fr.cfg))
+
+
+# ---------------------------------------------------------------- a2 + a3
+
+def _check_bin_sort(fr):
+    st, need, done = fr.status()
+    assert st == 0 and need == done
+    P = fr.plan
+    nt = fr.ntiles().cpu().numpy().astype(np.int64)
+    rect = _u32(fr.rects())
+    dkey = _u32(fr.depth_keys())
+    assert int(nt.sum()) == need
+    tiles_x = np.zeros(P.n_entries, np.int64)
+    tile_base = np.zeros(P.n_entries, np.int64)
+    for j in range(P.n_jobs):
+        J = P.jobs[j]
+        n = P.scenes[J.scene].n
+        tiles_x[J.entry_base:J.entry_base + n] = J.tiles_x
+        tile_base[J.entry_base:J.entry_base + n] = J.tile_base
+    r = np.stack([rect[:, 0] & 0xFFFF, rect[:, 0] >> 16, rect[:, 1] & 0xFFFF, rect[:, 1] >> 16], 1).astype(np.int64)
+    r[nt == 0] = (0, -1, 0, -1)
+    # reference fed the GPU's own rectangles and depth-key bits
+    ref_tiles, ref_ents = oracle.bin_sort_reference(r, dkey, tiles_x, tile_base)
+    k, v = fr.sorted_pairs(need)
+    assert np.array_equal(k.cpu().numpy().astype(np.int64), ref_tiles)
+    assert np.array_equal(v.cpu().numpy().astype(np.int64), ref_ents)
+    rng = fr.ranges().cpu().numpy().astype(np.int64)
+    t = np.arange(P.n_tiles)
+    lo = np.searchsorted(ref_tiles, t, "left")
+    hi = np.searchsorted(ref_tiles, t, "right")
+    empty = lo == hi
+    assert np.array_equal(rng[~empty, 0], lo[~empty]) and np.array_equal(rng[~empty, 1], hi[~empty])
+    assert np.all(rng[empty, 0] == rng[empty, 1])
+
+
+def test_bin_sort_bit_exact_tiny():
+    scene, cams = inputs.tiny_cube_2k()
+    fr, _, _ = gpu_forward(scene, cams)
+    _check_bin_sort(fr)
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 16), (16, 32), (32, 32)])
+def test_bin_sort_bit_exact_multiview(tile):
+    scene, cams = inputs.shell_100k_8views()
+    scene = inputs.subset_scene(scene, np.arange(0, 100_000, 3))
+    cams = [inputs.look_at(c.position, width=300 + 7 * i, height=211 + 3 * i) for i, c in enumerate(cams[:5])]
+    fr, _, _ = gpu_forward(scene, cams, frame.make_cfg(tile_w=tile[0], tile_h=tile[1]))
+    _check_bin_sort(fr)
+
+
+def test_depth_ties_break_by_component_index():
+    """Identical components (same depth key) must keep index order."""
+    base = inputs.scene_uniform_cube(64, seed=7)
+    idx = np.repeat(np.arange(64), 3)  # each component three times
+    scene = inputs.subset_scene(base, idx)
+    fr, _, _ = gpu_forward(scene, [inputs.look_at((0, 0, 3), width=64, height=64)])
+    _check_bin_sort(fr)
+
+
+# ---------------------------------------------------------------- a4 forward
+
+def _check_forward(fr, scene, cams, cfgd, pix=None):
+    refs = oracle_views(scene, cams, cfgd, pix)
+    worst = 0.0
+    flagged = 0
+    total = 0
+    kinds = np.zeros(4, np.int64)
+    for j, (cam, (_, ref)) in enumerate(zip(cams, refs)):
+        img = fr.image(j).reshape(3, -1).cpu().numpy().astype(np.float64)
+        Tg = fr.final_T()[fr.plan.jobs[j].pix_base:fr.plan.jobs[j].pix_base + cam.width * cam.height]
+        Tg = Tg.cpu().numpy().astype(np.float64)
+        if pix is not None:
+            img = img[:, pix[j]]
+            Tg = Tg[pix[j]]
+        ok = ref["flags"] == 0
+        flagged += int((~ok).sum())
+        kinds += np.bincount(ref["flags"], minlength=4)[:4]
+        total += ok.size
+        err = np.abs(img[:, ok] - ref["rgb"][:, ok])
+        worst = max(worst, float(err.max()) if err.size else 0.0)
+        assert np.abs(Tg[ok] - ref["T"][ok]).max() <= FWD_TOL
+    assert worst <= FWD_TOL, worst
+    # flagged: pixels with an |alpha| within 1e-4 relative of tau (bit 1) or a
+    # transmittance within 1e-3 relative of t_min at the termination test (bit 2)
+    print(f"forward max-abs {worst:.3e}; flagged {flagged}/{total} (near tau {kinds[1] + kinds[3]}, "
+          f"near t_min {kinds[2] + kinds[3]})")
+    assert flagged <= 0.05 * total, (flagged, total, kinds)
+    return worst, flagged
+
+
+@pytest.mark.parametrize("tile,batch", [((16, 16), 128), ((16, 16), 32), ((32, 16), 64), ((16, 32), 256),
+                                        ((32, 32), 128)])
+def test_forward_tiny_all_tile_configs(tile, batch):
+    scene, cams = inputs.tiny_cube_2k()
+    cfg = frame.make_cfg(tile_w=tile[0], tile_h=tile[1], batch=batch)
+    fr, _, cams = gpu_forward(scene, cams, cfg)
+    _check_forward(fr, f32_scene(scene), cams, frame.cfg_dict(cfg))
+
+
+def test_forward_last_contributor_matches_oracle():
+    scene, cams = inputs.tiny_cube_2k()
+    fr, _, cams = gpu_forward(scene, cams)
+    cfgd = frame.cfg_dict(fr.cfg)
+    ref = oracle.render(oracle.project(f32_scene(scene), cams[0], cfgd), cams[0], cfgd)
+    last = fr.last_contrib().cpu().numpy().astype(np.int64)
+    rng = fr.ranges().cpu().numpy().astype(np.int64)
+    k, v = fr.sorted_pairs(fr.status()[1])
+    v = v.cpu().numpy().astype(np.int64)
+    W = cams[0].width
+    ys, xs = np.divmod(np.arange(W * cams[0].height), W)
+    tile = (ys // 16) * fr.plan.jobs[0].tiles_x + xs // 16
+    comp = np.where(last > 0, v[np.maximum(rng[tile, 0] + last - 1, 0)], -1)
+    ok = ref["flags"] == 0
+    assert np.array_equal(comp[ok], ref["last"][ok])
+
+
+def test_forward_shell_8views_800_sampled():
+    """Shell workload at full size (100k components, 8 x 800x800, SH degree 3),
+    2,000 sampled pixels per view computed one by one by the oracle."""
+    scene, cams = inputs.shell_100k_8views()
+    fr, _, cams = gpu_forward(scene, cams)
+    rng = np.random.default_rng(0)
+    pix = [rng.choice(c.width * c.height, 2000, replace=False) for c in cams]
+    _check_forward(fr, f32_scene(scene), cams, frame.cfg_dict(fr.cfg), pix)
+
+
+@pytest.mark.parametrize("case", ["ragged", "no_termination", "lowpass", "background", "large_nu", "clamped_alpha",
+                                  "sh1", "sh2"])
+def test_forward_edge_cases(case):
+    scene = inputs.scene_uniform_cube(1500, seed=11)
+    cam = inputs.look_at((0.3, -0.2, 3.0), width=100, height=60)
+    kw = {}
+    if case == "no_termination":
+        kw["t_min"] = 0.0
+    elif case == "lowpass":
+        kw["lowpass"] = 0.3
+    elif case == "background":
+        kw["bg"] = (0.2, 0.5, 1.0)
+    elif case == "large_nu":
+        scene["nu"] = np.exp(np.random.default_rng(1).uniform(math.log(40), math.log(1e4), 1500)).astype(np.float32)
+    elif case == "clamped_alpha":
+        scene["opacity_raw"] = np.sign(scene["opacity_raw"]) * np.float32(4.0)
+    elif case in ("sh1", "sh2"):
+        deg = 1 if case == "sh1" else 2
+        K = (deg + 1) ** 2
+        sh = np.random.default_rng(2).normal(0, 0.3, (3 * K, 1500)).astype(np.float32)
+        sh[:3] = scene["sh"]
+        scene["sh"], scene["sh_degree"] = sh, deg
+    cfg = frame.make_cfg(**kw)
+    fr, _, cams = gpu_forward(scene, [cam], cfg)
+    _check_forward(fr, f32_scene(scene), cams, frame.cfg_dict(cfg))
+
+
+def test_forward_empty_and_culled_scenes():
+    cam = inputs.look_at((0, 0, 3), width=48, height=40)
+    cfg = frame.make_cfg(bg=(0.1, 0.2, 0.3))
+    behind = inputs.scene_uniform_cube(50, seed=1)
+    behind["mean"] = behind["mean"] + np.array([[0], [0], [5.0]], np.float32)  # all behind the camera
+    for sc in (inputs.subset_scene(inputs.scene_uniform_cube(10, seed=1), np.arange(0)), behind):
+        fr, _, _ = gpu_forward(sc, [cam], cfg)
+        img = fr.image(0).cpu().numpy()
+        assert np.allclose(img, np.array([0.1, 0.2, 0.3], np.float32)[:, None, None])
+        assert fr.status()[1] == 0
+
+
+# ---------------------------------------------------------------- a5 + a6 backward
+
+def _gpu_backward(fr, sc, ws):
+    dl = torch.as_tensor(np.concatenate([w.reshape(-1) for w in ws]).astype(np.float32), device=DEV)
+    g = sc.zeros_like()
+    fr.backward(dl, [g])
+    torch.cuda.synchronize()
+    return g
+
+
+def _grad2d_report(fr, g2d_ref, cams, scene):
+    g2 = fr.grad2d().cpu().numpy().astype(np.float64)[:, :10]
+    n = scene["n"]
+    for j in range(len(cams)):
+        eb = fr.plan.jobs[j].entry_base
+        got = g2[eb:eb + n]
+        ref = g2d_ref[j]
+        for c, name in enumerate(oracle.G_FIELDS):
+            scale = np.abs(ref[:, c]).max()
+            if scale == 0:
+                continue
+            tol = GRAD_REL * np.maximum(np.abs(ref[:, c]), GRAD_FLOOR * scale)
+            bad = np.abs(got[:, c] - ref[:, c]) > tol
+            assert not bad.any(), (j, name, int(bad.sum()), got[bad, c][:4], ref[bad, c][:4])
+            assert np.linalg.norm(got[:, c] - ref[:, c]) <= GRAD_NORM * np.linalg.norm(ref[:, c]), (j, name)
+
+
+@pytest.mark.parametrize("nu_mode", [0, 1])
+def test_backward_tiny_against_oracle_analytic(nu_mode):
+    scene, cams = inputs.tiny_cube_2k()
+    cfg = frame.make_cfg(nu_grad_mode=nu_mode)
+    fr, sc, cams = gpu_forward(scene, cams, cfg)
+    cfgd = frame.cfg_dict(cfg)
+    s32 = f32_scene(scene)
+    refs = oracle_views(s32, cams, cfgd)
+    ws = masked_weights(cams, refs, seed=5)
+    g = _gpu_backward(fr, sc, ws)
+    gref, g2d = oracle.backward(s32, cams, cfgd, ws, want_grad2d=True)
+    _grad2d_report(fr, g2d, cams, scene)
+    assert_groups_close(scene_grads_flat(g), gref, scene["n"], 0, label="tiny")
+
+
+def test_backward_shell_sh3_multiview_against_oracle_analytic():
+    scene, cams = inputs.shell_100k_8views()
+    scene = inputs.subset_scene(scene, np.arange(0, 100_000, 10))
+    cams = [inputs.look_at(c.position, width=160, height=128) for c in cams[:3]]
+    fr, sc, cams = gpu_forward(scene, cams)
+    cfgd = frame.cfg_dict(fr.cfg)
+    s32 = f32_scene(scene)
+    refs = oracle_views(s32, cams, cfgd)
+    ws = masked_weights(cams, refs, seed=6)
+    g = _gpu_backward(fr, sc, ws)
+    gref, g2d = oracle.backward(s32, cams, cfgd, ws, want_grad2d=True)
+    _grad2d_report(fr, g2d, cams, scene)
+    assert_groups_close(scene_grads_flat(g), gref, scene["n"], 3, label="shell")
+
+
+def test_backward_gradcheck_50k_against_oracle_fd_and_analytic():
+    """Gradient check: 50k components, 256x256; GPU gradient against the
+    oracle's FP64 central differences (h = 1e-6) on 200 parameters spread
+    over all six groups, and against the full analytic FP64 gradient."""
+    scene, cams = inputs.gradcheck_cube_50k()
+    fr, sc, cams = gpu_forward(scene, cams)
+    cfgd = frame.cfg_dict(fr.cfg)
+    s32 = f32_scene(scene)
+    refs = oracle_views(s32, cams, cfgd)
+    ws = masked_weights(cams, refs, seed=7)
+    g = scene_grads_flat(_gpu_backward(fr, sc, ws))
+    gref = oracle.backward(s32, cams, cfgd, ws)
+    assert_groups_close(g, gref, scene["n"], 0, label="gradcheck")
+    # finite differences on parameters that influence the loss
+    n = scene["n"]
+    sl = oracle.theta_slices(n, 0)
+    rng = np.random.default_rng(3)
+    theta = oracle.theta_from_scene(s32)
+    picks = []
+    per = {"mean": 34, "log_scale": 34, "quat": 34, "nu": 33, "opacity_raw": 33, "sh": 32}
+    for name, k in per.items():
+        cand = np.arange(sl[name].start, sl[name].stop)
+        cand = cand[np.abs(gref[cand]) > 1e-4 * np.abs(gref[sl[name]]).max()]
+        picks += list(rng.choice(cand, k, replace=False))
+    fd, smooth = oracle.fd_gradient(theta, n, 0, cams, cfgd, ws, picks)
+    checked = 0
+    for j, f, ok in zip(picks, fd, smooth):
+        if not ok:
+            continue
+        group = next(k for k, s in sl.items() if s.start <= j < s.stop)
+        scale = np.abs(gref[sl[group]]).max()
+        assert abs(g[j] - f) <= GRAD_REL * max(abs(f), GRAD_FLOOR * scale), (group, j, g[j], f)
+        checked += 1
+    assert checked >= 180
+
+
+def test_backward_edge_cases_large_nu_and_clamp():
+    scene = inputs.scene_uniform_cube(1200, seed=13)
+    rng = np.random.default_rng(4)
+    scene["nu"] = np.exp(rng.uniform(0, math.log(2e4), 1200)).astype(np.float32)  # some beyond the 1e4 limit
+    scene["opacity_raw"][:100] = np.float32(3.5)  # |o| > alpha_max: clamped alpha
+    cam = inputs.look_at((0.1, 0.2, 3.0), width=96, height=72)
+    cfg = frame.make_cfg(bg=(0.3, 0.1, 0.6), lowpass=0.3)
+    fr, sc, cams = gpu_forward(scene, [cam], cfg)
+    cfgd = frame.cfg_dict(cfg)
+    s32 = f32_scene(scene)
+    refs = oracle_views(s32, cams, cfgd)
+    ws = masked_weights(cams, refs, seed=8)
+    g = _gpu_backward(fr, sc, ws)
+    gref = oracle.backward(s32, cams, cfgd, ws)
+    assert_groups_close(scene_grads_flat(g), gref, 1200, 0, label="edge")
+
+
+# ---------------------------------------------------------------- a7 step
+
+@pytest.mark.parametrize("burn_in,step", [(False, 0), (True, 3), (False, (1 << 32) + 5)])
+def test_sghmc_step_against_oracle(burn_in, step):
+    scene = inputs.scene_sphere_shell(3000, seed=9)
+    n = scene["n"]
+    rng = np.random.default_rng(10)
+    sc = frame.Scene.from_numpy(scene, DEV)
+    grads = sc.zeros_like()
+    for f in frame.FIELDS:
+        grads.t[f].copy_(torch.as_tensor(rng.normal(size=tuple(grads.t[f].shape)).astype(np.float32)))
+    grads.t["opacity_raw"][0, :200] = 0.0
+    sc.t["opacity_raw"][0, :300] = torch.as_tensor(rng.uniform(-0.01, 0.01, 300).astype(np.float32))
+    st = frame.SamplerState(sc)
+    st.r.copy_(torch.as_tensor(rng.normal(size=(3, n)).astype(np.float32) * 0.1))
+    st.m.copy_(torch.as_tensor(rng.normal(size=tuple(st.m.shape)).astype(np.float32) * 0.01))
+    st.v.copy_(torch.as_tensor(np.abs(rng.normal(size=tuple(st.v.shape))).astype(np.float32) * 0.01))
+    theta0 = oracle.theta_from_scene(sc.to_numpy())
+    g0 = scene_grads_flat(grads)
+    r0 = st.r.cpu().numpy().astype(np.float64).reshape(-1)
+    K = 16
+    m0 = st.m.cpu().numpy().astype(np.float64)
+    v0 = st.v.cpu().numpy().astype(np.float64)
+    # oracle moments use theta's layout: mean rows unused
+    mo = np.concatenate([np.zeros(3 * n), m0.reshape(-1)])
+    vo = np.concatenate([np.zeros(3 * n), v0.reshape(-1)])
+    params = dict(eps=2e-2, C=0.6, k=100.0, t0=0.005, lr=(5e-3, 1e-3, 1e-2, 5e-2, 2.5e-3), beta1=0.9, beta2=0.999,
+                  adam_eps=1e-8)
+    sp = frame.step_params(eps=params["eps"], C=params["C"], burn_in=burn_in, seed=77, step=step,
+                           lr=params["lr"], adam_eps=params["adam_eps"])
+    xi = torch.zeros(3, n, dtype=torch.float32, device=DEV)
+    frame.sghmc_step(sc, grads, st, sp, xi_out=xi)
+    torch.cuda.synchronize()
+    th, rr, mm, vv, xir = oracle.sghmc_step(theta0, g0, r0, mo, vo, n=n, sh_degree=3, params=params,
+                                             burn_in=burn_in, seed=77, step=step)
+    assert np.abs(xi.cpu().numpy() - xir).max() < 2e-5
+    got = oracle.theta_from_scene(sc.to_numpy())
+    assert np.all(np.abs(got - th) <= 2e-6 * np.maximum(np.abs(th), 1.0)), np.abs(got - th).max()
+    assert np.allclose(st.r.cpu().numpy().reshape(-1), rr, rtol=1e-5, atol=2e-6)
+    assert np.allclose(st.m.cpu().numpy().reshape(-1), mm[3 * n:], rtol=1e-5, atol=1e-7)
+    assert np.allclose(st.v.cpu().numpy().reshape(-1), vv[3 * n:], rtol=1e-5, atol=1e-7)
+
+
+def test_sghmc_noise_moments_on_gpu():
+    n = 1_000_000
+    scene = inputs.scene_uniform_cube(n, seed=2)
+    sc = frame.Scene.from_numpy(scene, DEV)
+    st = frame.SamplerState(sc)
+    xi = torch.zeros(3, n, dtype=torch.float32, device=DEV)
+    frame.sghmc_step(sc, sc.zeros_like(), st, frame.step_params(seed=5, step=1), xi_out=xi)
+    z = xi.double()
+    assert float(z.mean(1).abs().max()) < 5e-3
+    assert float((z.var(1) - 1).abs().max()) < 6e-3
+    # spot-check individual normals against the oracle's Philox + Box-Muller
+    for i in (0, 1, 12345, n - 1):
+        assert np.allclose(xi[:, i].cpu().numpy(), oracle.normals3(5, 1, i), atol=2e-5)
+
+
+# ---------------------------------------------------------------- loss, capacity
+
+def test_loss_l1():
+    rng = np.random.default_rng(0)
+    a = rng.uniform(size=100_003).astype(np.float32)
+    b = rng.uniform(size=100_003).astype(np.float32)
+    b[:10] = a[:10]
+    pa, pb = torch.as_tensor(a, device=DEV), torch.as_tensor(b, device=DEV)
+    g = torch.empty_like(pa)
+    loss = torch.zeros(1, device=DEV)
+    frame.loss_l1(pa, pb, g, loss)
+    torch.cuda.synchronize()
+    assert float(loss) == pytest.approx(np.abs(a.astype(np.float64) - b).mean(), rel=1e-5)
+    assert np.array_equal(g.cpu().numpy(), (np.sign(a - b) / a.size).astype(np.float32))
+
+
+def test_pair_capacity_overflow_is_reported_and_recovered():
+    scene, cams = inputs.tiny_cube_2k()
+    cams = [frame.f32_camera(c) for c in cams]
+    sc = frame.Scene.from_numpy(scene, DEV)
+    fr = frame.Frame([sc], cams, pair_capacity=1000, device=DEV)
+    fr.project()
+    fr.bin()
+    fr.sort()
+    fr.render_fwd()
+    st, need, done = fr.status()
+    assert st & _abi.SSS_STATUS_PAIR_OVERFLOW and need > 1000 and done == 1000
+    fr2 = frame.Frame([sc], cams, pair_capacity=1000, device=DEV)
+    fr2.forward(grow=True)
+    st2, need2, done2 = fr2.status()
+    assert st2 == 0 and need2 == need == done2
