@@ -61,7 +61,8 @@ def lib():
                                  _nullable(_ip)]
         L.orc_render.restype = None
         L.orc_backward.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp, _ip, _dp, _ip,
-                                   _nullable(_lp), _nullable(_lp), _dp, _nullable(_dp), _dp]
+                                   _nullable(_lp), _nullable(_lp), _dp, _nullable(_dp), _dp, _nullable(_dp),
+                                   _nullable(_dp)]
         L.orc_backward.restype = None
         L.orc_sghmc_step.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int,
                                      ctypes.c_uint64, ctypes.c_uint64, _nullable(_dp)]
@@ -166,12 +167,16 @@ def render(proj: np.ndarray, cam, cfg=None, pix=None) -> dict:
     return dict(rgb=rgb, T=T, n_contrib=nc, last=last, flags=flags)
 
 
-def backward(scene_or_theta, cams, cfg, dl_dc, pix=None, *, n=None, sh_degree=None, want_grad2d=False):
+def backward(scene_or_theta, cams, cfg, dl_dc, pix=None, *, n=None, sh_degree=None, want_grad2d=False,
+             want_abs=False):
     """Analytic FP64 gradient of L = sum(dl_dc * C) w.r.t. theta.
 
     dl_dc: list (one per view) of [3][npix_v] (or [3][H][W]) arrays.
     pix:   None (all pixels) or a list of linear-index arrays per view.
-    Returns grad theta (planar) and, if asked, grad2d [views][n][G_STRIDE]."""
+    Returns grad theta (planar) and, if asked, grad2d [views][n][G_STRIDE];
+    with want_abs also the sums of |summand| for both (grad_abs, grad2d_abs),
+    the scale against which a floating-point evaluation of the same sums
+    rounds."""
     if isinstance(scene_or_theta, dict):
         theta = theta_from_scene(scene_or_theta)
         n, sh_degree = scene_or_theta["n"], scene_or_theta["sh_degree"]
@@ -192,8 +197,15 @@ def backward(scene_or_theta, cams, cfg, dl_dc, pix=None, *, n=None, sh_degree=No
     dl = np.ascontiguousarray(dl)
     grad = np.zeros_like(theta)
     g2d = np.zeros((V, n, G_STRIDE), np.float64) if want_grad2d else None
-    lib().orc_backward(n, sh_degree, theta, V, cds, whs, fd, fi, npix, pix_cat, dl, g2d, grad)
-    return (grad, g2d) if want_grad2d else grad
+    gabs = np.zeros_like(theta) if want_abs else None
+    g2abs = np.zeros((V, n, G_STRIDE), np.float64) if (want_abs and want_grad2d) else None
+    lib().orc_backward(n, sh_degree, theta, V, cds, whs, fd, fi, npix, pix_cat, dl, g2d, grad, g2abs, gabs)
+    out = (grad,)
+    if want_grad2d:
+        out += (g2d,)
+    if want_abs:
+        out += (gabs,) + ((g2abs,) if want_grad2d else ())
+    return out if len(out) > 1 else grad
 
 
 SGHMC_DEFAULTS = dict(eps=1e-3, C=0.5, k=100.0, t0=0.005, lr=(5e-3, 1e-3, 1e-2, 5e-2, 2.5e-3),

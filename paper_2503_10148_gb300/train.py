@@ -115,5 +115,5 @@ class PlainStep:
             F.loss_l1(fr.rgb, tgt, dl, self.loss)
             fr.backward(dl, [g])
         for f in F.FIELDS:
-            torch.stack([g.t[f] for g in self.grads]).sum(0, out=self.total.t[f])
+            self.total.t[f].copy_(torch.stack([g.t[f] for g in self.grads]).sum(0))
         F.sghmc_step(self.scene, self.total, self.state, self.sp)

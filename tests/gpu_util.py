@@ -66,16 +66,23 @@ def scene_grads_flat(g: frame.Scene) -> np.ndarray:
     return np.concatenate([g.t[f].detach().cpu().numpy().reshape(-1).astype(np.float64) for f in frame.FIELDS])
 
 
-GRAD_REL = 1e-3     # per-element relative bar
-GRAD_FLOOR = 1e-2   # ... measured against max(|g_ref|, GRAD_FLOOR * group max)
+GRAD_REL = 1e-3     # per-element relative bar ...
+GRAD_FLOOR = 1e-2   # ... against max(|g_ref|, GRAD_FLOOR * sum of |summands|)
 GRAD_NORM = 1e-4    # and ||g - g_ref|| / ||g_ref|| per group
 
 
-def assert_groups_close(got, ref, n, sh_degree, rel=GRAD_REL, floor=GRAD_FLOOR, norm=GRAD_NORM, label=""):
-    """Per parameter group: every element within rel of max(|g_ref|, floor x
-    the group's largest |g_ref|) -- elements far below the group scale are sums
-    dominated by cancellation, where FP32 keeps an absolute, not a relative,
-    accuracy -- and the group's relative L2 error within ``norm``."""
+def grad_den(ref, absref, floor=GRAD_FLOOR):
+    """Denominator of the relative error: |g_ref|, but at least GRAD_FLOOR of
+    the magnitude summed into it (a sum of terms of both signs -- the gradient
+    of a splat's position sums pixels on either side of it -- is only as
+    accurate in FP32 as its summands, not as its result)."""
+    scale = max(float(np.abs(ref).max()), 1e-30)
+    return np.maximum(np.maximum(np.abs(ref), floor * absref), 1e-7 * scale)
+
+
+def assert_groups_close(got, ref, n, sh_degree, absref, rel=GRAD_REL, norm=GRAD_NORM, label=""):
+    """Per parameter group: every element within ``rel`` of grad_den and the
+    group's relative L2 error within ``norm``."""
     sl = oracle.theta_slices(n, sh_degree)
     report = {}
     for name, s in sl.items():
@@ -84,7 +91,7 @@ def assert_groups_close(got, ref, n, sh_degree, rel=GRAD_REL, floor=GRAD_FLOOR, 
         if scale == 0:
             assert np.abs(a).max() == 0, (label, name)
             continue
-        den = np.maximum(np.abs(b), floor * scale)
+        den = grad_den(b, absref[s])
         relerr = np.abs(a - b) / den
         l2 = float(np.linalg.norm(a - b) / np.linalg.norm(b))
         report[name] = (float(relerr.max()), l2)

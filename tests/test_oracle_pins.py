@@ -457,6 +457,22 @@ def test_analytic_gradient_matches_central_differences():
     assert checked >= 50
 
 
+def test_summand_magnitudes_bound_the_gradient():
+    """grad_abs sums |summand|: it bounds |grad| (triangle inequality) and
+    equals it when a parameter receives a single summand."""
+    sc = _grad_scene(n=60, seed=4)
+    cam = inputs.look_at((0.2, 0.1, 3.0), width=40, height=32)
+    w = inputs.linear_loss_weights([cam], seed=2)
+    g, g2, ga, g2a = oracle.backward(sc, [cam], None, w, want_grad2d=True, want_abs=True)
+    assert np.all(ga >= np.abs(g) * (1 - 1e-12)) and np.all(g2a >= np.abs(g2) * (1 - 1e-12))
+    assert np.any(ga > np.abs(g) * 1.5)  # cancellation does occur
+    one = _one_component([0.05, -0.04, 0.1], [-2.2, -2.6, -2.4], [0.8, 0.1, 0.3, -0.2], 3.0, 0.7, rgb=[0.2, 0.5, 0.7])
+    pix = [np.array([40 * 16 + 20], np.int64)]
+    dl = [np.array([[0.3], [-0.2], [0.5]])]
+    g, g2, ga, g2a = oracle.backward(one, [cam], None, dl, pix, want_grad2d=True, want_abs=True)
+    assert np.allclose(g2a, np.abs(g2), rtol=1e-14, atol=0)
+
+
 def test_paper_printed_nu_gradient_disagrees_with_differences():
     """The printed SM dT/dnu holds the exponent fixed; it misses the
     -1/2 ln(1 + h/nu) T2D term, so it fails against finite differences where
