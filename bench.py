@@ -38,6 +38,8 @@ UNIT = "Mpix/s"
 WORKLOAD = ("clusters_1p5m_4views: 1.5M 3D t-components (6 Gaussian clusters + ground plane, log-scale "
             "N(-4,0.7), SH degree 3, nu log-uniform [1,32], 30% scooping), 4 views x 1297x840 per step, "
             "train step = project+bin+sort+render_fwd+L1+render_bwd+project_bwd+sghmc_step")
+WORKLOADS = {"clusters_1p5m_4views": "clusters_1p5m_4views", "shell_100k_8views": "shell_100k_8views",
+             "gradcheck_cube_50k": "gradcheck_cube_50k"}
 N_SMS = 152
 MUFU_PER_SM_CLK = 16
 FP32_LANES_PER_SM = 128
@@ -59,6 +61,8 @@ def parse_args():
     ap.add_argument("--no-plain", action="store_true", help="skip the one-frame-per-view comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="clusters_1p5m_4views", choices=sorted(WORKLOADS),
+                    help="smaller seeded workloads exist for profiling; the benchmark line uses the default")
     return ap.parse_args()
 
 
@@ -168,7 +172,7 @@ def _cfg(args):
     if args.tile or args.batch:
         tw, th = (int(v) for v in (args.tile or "16x16").split("x"))
         return frame.make_cfg(tile_w=tw, tile_h=th, batch=args.batch or 128), "cli"
-    best = autotune.cached("clusters_1p5m_4views")
+    best = autotune.cached(getattr(args, "workload", "clusters_1p5m_4views"))
     if best:
         return frame.make_cfg(tile_w=best["tile_w"], tile_h=best["tile_h"], batch=best["batch"]), "autotuned"
     return frame.make_cfg(), "default"
@@ -271,7 +275,7 @@ def run_ours(args):
     dist_init(world, "nccl")
     build.build()
 
-    scene_np, cams = inputs.clusters_1p5m_4views()
+    scene_np, cams = getattr(inputs, WORKLOADS[args.workload])()
     cams = [F.f32_camera(c) for c in cams]
     targets_np = np.concatenate([t.reshape(-1) for t in inputs.target_images(cams, seed=3)])
     scene = F.Scene.from_numpy(scene_np, device)
@@ -352,7 +356,8 @@ def run_ours(args):
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms_max, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded scene, cameras and target images)",
-        "config": {"workload": WORKLOAD, "views": len(cams), "width": cams[0].width, "height": cams[0].height,
+        "config": {"workload": WORKLOAD if args.workload == "clusters_1p5m_4views" else args.workload,
+                   "views": len(cams), "width": cams[0].width, "height": cams[0].height,
                    "components": scene.n, "tile": f"{cfg.tile_w}x{cfg.tile_h}", "batch": cfg.batch,
                    "cfg_source": cfg_src, "form": "batched frame, whole step in one CUDA graph",
                    "pairs_per_step": pairs, "pair_capacity": ts.frame.pair_capacity,
@@ -394,9 +399,12 @@ def cpu_baseline(budget_s: float):
     import oracle
     from paper_2503_10148_gb300 import inputs
     scene_np, cams = inputs.clusters_1p5m_4views()
-    pilot = 8
-    t_pilot = _oracle_sample(scene_np, cams, pilot, seed=100)
-    n_pix = int(max(pilot, min(2000, pilot * budget_s / max(t_pilot, 1e-3))))
+    # two pilots fit t(n) = fixed (projection of all entries) + n x per-pixel
+    t8 = _oracle_sample(scene_np, cams, 8, seed=100)
+    t40 = _oracle_sample(scene_np, cams, 40, seed=99)
+    per_px = max((t40 - t8) / 32.0, 1e-4)
+    fixed = max(t8 - 8 * per_px, 0.0)
+    n_pix = int(max(40, min(4000, (budget_s - fixed) / per_px)))
     t = _oracle_sample(scene_np, cams, n_pix, seed=101)
     px = n_pix * len(cams)
     return {"value": round(px / t / 1e6, 8), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
@@ -427,7 +435,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(total / args.steps * 1e3, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded scene and cameras)",
-        "config": {"workload": WORKLOAD, "views": len(cams), "width": cams[0].width, "height": cams[0].height,
+        "config": {"workload": WORKLOAD if args.workload == "clusters_1p5m_4views" else args.workload,
+                   "views": len(cams), "width": cams[0].width, "height": cams[0].height,
                    "components": scene_np["n"]},
         "cpu_baseline": {"value": round(value, 8), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
                          "sample": sample},

@@ -165,7 +165,11 @@ typedef struct sss_frame_plan {
   int32_t tile_bits; /* ceil(log2(n_tiles)) */
   /* workspace regions (byte offsets) */
   size_t ws_bytes;
-  size_t ws_off_rec;     /* float4[3][n_entries]: 2D splat records          */
+  size_t ws_off_rec;     /* float4[3][n_entries]: 2D splat records:
+                            {mean2D - origin, conic a, conic b},
+                            {conic c, o, h_max, nu}, {rgb, origin bits}
+                            with origin = the entry's first tile corner
+                            (x | y << 16)                                   */
   size_t ws_off_dkey;    /* uint32[n_entries]: FP32 depth-key bits          */
   size_t ws_off_ntiles;  /* uint32[n_entries]: tiles touched                */
   size_t ws_off_rect;    /* uint2[n_entries]: tile rect (x0|x1<<16, y0|y1<<16) */

@@ -62,7 +62,7 @@ def lib():
         L.orc_render.restype = None
         L.orc_backward.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp, _ip, _dp, _ip,
                                    _nullable(_lp), _nullable(_lp), _dp, _nullable(_dp), _dp, _nullable(_dp),
-                                   _nullable(_dp)]
+                                   _nullable(_dp), _nullable(_dp), _nullable(_dp)]
         L.orc_backward.restype = None
         L.orc_sghmc_step.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int,
                                      ctypes.c_uint64, ctypes.c_uint64, _nullable(_dp)]
@@ -198,14 +198,30 @@ def backward(scene_or_theta, cams, cfg, dl_dc, pix=None, *, n=None, sh_degree=No
     grad = np.zeros_like(theta)
     g2d = np.zeros((V, n, G_STRIDE), np.float64) if want_grad2d else None
     gabs = np.zeros_like(theta) if want_abs else None
+    gabsn = np.zeros_like(theta) if want_abs else None
     g2abs = np.zeros((V, n, G_STRIDE), np.float64) if (want_abs and want_grad2d) else None
-    lib().orc_backward(n, sh_degree, theta, V, cds, whs, fd, fi, npix, pix_cat, dl, g2d, grad, g2abs, gabs)
+    g2absn = np.zeros((V, n, G_STRIDE), np.float64) if (want_abs and want_grad2d) else None
+    lib().orc_backward(n, sh_degree, theta, V, cds, whs, fd, fi, npix, pix_cat, dl, g2d, grad, g2abs, gabs, gabsn,
+                       g2absn)
     out = (grad,)
     if want_grad2d:
         out += (g2d,)
     if want_abs:
-        out += (gabs,) + ((g2abs,) if want_grad2d else ())
+        out += (Magnitudes(gabs, gabsn),) + ((Magnitudes(g2abs, g2absn),) if want_grad2d else ())
     return out if len(out) > 1 else grad
+
+
+class Magnitudes:
+    """Per-element magnitude sums of a gradient: ``abs`` = sum of |summand|
+    (taken on the operands of every subtraction inside a summand), ``absn`` =
+    the same with each pixel's terms weighted by its contributor count."""
+
+    def __init__(self, abs_, absn):
+        self.abs = abs_
+        self.absn = absn
+
+    def __getitem__(self, sl):
+        return Magnitudes(self.abs[sl], self.absn[sl])
 
 
 SGHMC_DEFAULTS = dict(eps=1e-3, C=0.5, k=100.0, t0=0.005, lr=(5e-3, 1e-3, 1e-2, 5e-2, 2.5e-3),

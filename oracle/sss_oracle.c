@@ -523,23 +523,29 @@ static double dT_dnu(double h, double nu, int mode) {
  *   dC/drgb_k   = alpha_k T_k
  *   dC/dalpha_k = T_k rgb_k - (S_k + T_f bg) / (1 - alpha_k). */
 static void pixel_backward(const double* proj, const cvec* cs, double T_final, const double g[3], const ocfg* cfg,
-                           double* g2d, double* g2abs) {
+                           double* g2d, double* g2abs, double* g2absn) {
+  const double ncon = (double)cs->n; /* contributors of this pixel */
   double S[3] = {0, 0, 0};
   for (long k = cs->n - 1; k >= 0; --k) {
     const contrib* c = &cs->v[k];
     const double* r = proj + (size_t)c->idx * P_STRIDE;
     double* gr = g2d + (size_t)c->idx * G_STRIDE;
     double* ga = g2abs ? g2abs + (size_t)c->idx * G_STRIDE : NULL;
-    double dL_dalpha = 0.0;
+    double* gan = g2absn ? g2absn + (size_t)c->idx * G_STRIDE : NULL;
+    double dL_dalpha = 0.0, dL_dalpha_mag = 0.0;
     for (int ch = 0; ch < 3; ++ch) {
       double dC_dalpha = c->T * r[P_R + ch] - (S[ch] + T_final * cfg->bg[ch]) / (1.0 - c->alpha);
       dL_dalpha += g[ch] * dC_dalpha;
+      dL_dalpha_mag += fabs(g[ch]) * (c->T * fabs(r[P_R + ch]) +
+                                      fabs(S[ch] + T_final * cfg->bg[ch]) / (1.0 - c->alpha));
       double d_rgb = g[ch] * c->alpha * c->T;
 #pragma omp atomic
       gr[G_R + ch] += d_rgb;
       if (ga) {
 #pragma omp atomic
         ga[G_R + ch] += fabs(d_rgb);
+#pragma omp atomic
+        gan[G_R + ch] += fabs(d_rgb) * ncon;
       }
     }
     for (int ch = 0; ch < 3; ++ch) S[ch] += r[P_R + ch] * c->alpha * c->T;
@@ -570,11 +576,27 @@ static void pixel_backward(const double* proj, const cvec* cs, double T_final, c
     /* dL/d(limited nu); the limit's own derivative is applied in the chain */
 #pragma omp atomic
     gr[G_NU] += d_nu;
-    if (ga) { /* magnitudes of the summands (scale of the rounding of a sum) */
-      const double t[7] = {d_mx, d_my, d_ca, d_cb, d_cc, d_o, d_nu};
+    if (ga) {
+      /* Magnitudes of the summands, each taken on the operands of the
+       * subtractions inside it (T rgb and S / (1 - alpha) in dC/dalpha; the two
+       * terms of dT/dnu): the scale a floating-point evaluation rounds
+       * against. */
+      double dT_mag = fabs(r[P_O]) * dL_dalpha_mag;
+      double dh_mag = dT_mag * fabs(dT_dh(c->h, nu));
+      double nu_mag = 0.5 * log1p(c->h / nu) + (nu + 2.0) / 2.0 * c->h / (nu * nu) / (1.0 + c->h / nu);
+      const double t[7] = {
+          dh_mag * 2.0 * (fabs(r[P_CON_A] * c->dx) + fabs(r[P_CON_B] * c->dy)),
+          dh_mag * 2.0 * (fabs(r[P_CON_B] * c->dx) + fabs(r[P_CON_C] * c->dy)),
+          dh_mag * c->dx * c->dx,
+          dh_mag * 2.0 * fabs(c->dx * c->dy),
+          dh_mag * c->dy * c->dy,
+          dL_dalpha_mag * c->t2d,
+          dT_mag * c->t2d * nu_mag};
       for (int o = 0; o < 7; ++o) {
 #pragma omp atomic
-        ga[o] += fabs(t[o]);
+        ga[o] += t[o];
+#pragma omp atomic
+        gan[o] += t[o] * ncon;
       }
     }
   }
@@ -588,23 +610,31 @@ static void pixel_backward(const double* proj, const cvec* cs, double T_final, c
  *   dL_dC    concatenated per view [3][npix_v]
  *   grad2d   optional [n_views][n][G_STRIDE] output (dL/d 2D record)
  *   grad     [(12 + 3K) n] output, dL/dtheta summed over views
- *   grad2d_abs, grad_abs  optional: the same sums taken over the absolute
- *            values of the summands (per-pixel terms, then |Jacobian| times
- *            those), i.e. the magnitude a floating-point sum of the terms
+ *   grad2d_abs, grad_abs  optional: the same sums taken over magnitudes --
+ *            per pixel the absolute values of the operands of every
+ *            subtraction inside a term (T rgb and S / (1 - alpha) in
+ *            dC/dalpha, the two terms of dT/dnu), then |Jacobian| times those
+ *            -- i.e. the scale a floating-point evaluation of the same sums
  *            rounds against
+ *   grad_absn optional: as grad_abs with every pixel's magnitudes weighted by
+ *            its number of contributors (a transmittance recovered through
+ *            the whole list carries a rounding proportional to that count)
  * The 2D -> 3D chain uses the complex-step derivative of project_cx. */
 void orc_backward(int n, int sh_deg, const double* theta, int n_views, const double* cams, const int* whs,
                   const double* cfgd, const int* cfgi, const int64_t* npix, const int64_t* pix,
-                  const double* dL_dC, double* grad2d, double* grad, double* grad2d_abs, double* grad_abs) {
+                  const double* dL_dC, double* grad2d, double* grad, double* grad2d_abs, double* grad_abs,
+                  double* grad_absn, double* grad2d_absn) {
   ocfg cfg = read_cfg(cfgd, cfgi);
   int K = (sh_deg + 1) * (sh_deg + 1);
   size_t P = (size_t)(12 + 3 * K);
   memset(grad, 0, sizeof(double) * P * (size_t)n);
   if (grad_abs) memset(grad_abs, 0, sizeof(double) * P * (size_t)n);
+  if (grad_absn) memset(grad_absn, 0, sizeof(double) * P * (size_t)n);
   double* proj = (double*)malloc(sizeof(double) * P_STRIDE * (size_t)(n > 0 ? n : 1));
   double* g2 = (double*)malloc(sizeof(double) * G_STRIDE * (size_t)(n > 0 ? n : 1));
   double* g2a = (grad2d_abs || grad_abs) ? (double*)malloc(sizeof(double) * G_STRIDE * (size_t)(n > 0 ? n : 1))
                                          : NULL;
+  double* g2an = g2a ? (double*)malloc(sizeof(double) * G_STRIDE * (size_t)(n > 0 ? n : 1)) : NULL;
   size_t pix_off = 0, dl_off = 0;
   for (int v = 0; v < n_views; ++v) {
     ocam cam = read_cam(cams + 16 * v, whs + 2 * v);
@@ -613,6 +643,7 @@ void orc_backward(int n, int sh_deg, const double* theta, int n_views, const dou
     orc_project(n, sh_deg, theta, cams + 16 * v, whs + 2 * v, cfgd, cfgi, proj);
     memset(g2, 0, sizeof(double) * G_STRIDE * (size_t)n);
     if (g2a) memset(g2a, 0, sizeof(double) * G_STRIDE * (size_t)n);
+    if (g2an) memset(g2an, 0, sizeof(double) * G_STRIDE * (size_t)n);
     long m;
     long* order = sorted_valid(n, proj, &m);
     double* hpre = prefilter_bounds(n, proj, &cfg);
@@ -630,7 +661,7 @@ void orc_backward(int n, int sh_deg, const double* theta, int n_views, const dou
         cs.n = 0;
         composite_pixel(proj, order, m, hpre, &cfg, px, py, rgb, &T, &nc, &lst, &fl, &cs);
         double g[3] = {dl[k], dl[(size_t)np + k], dl[2 * (size_t)np + k]};
-        pixel_backward(proj, &cs, T, g, &cfg, g2, g2a);
+        pixel_backward(proj, &cs, T, g, &cfg, g2, g2a, g2an);
       }
       free(cs.v);
     }
@@ -638,6 +669,7 @@ void orc_backward(int n, int sh_deg, const double* theta, int n_views, const dou
     free(hpre);
     if (grad2d) memcpy(grad2d + (size_t)v * G_STRIDE * n, g2, sizeof(double) * G_STRIDE * (size_t)n);
     if (grad2d_abs) memcpy(grad2d_abs + (size_t)v * G_STRIDE * n, g2a, sizeof(double) * G_STRIDE * (size_t)n);
+    if (grad2d_absn) memcpy(grad2d_absn + (size_t)v * G_STRIDE * n, g2an, sizeof(double) * G_STRIDE * (size_t)n);
 
     /* chain to the 3D parameters, complex step of step size hc */
     const double hc = 1e-20;
@@ -645,6 +677,7 @@ void orc_backward(int n, int sh_deg, const double* theta, int n_views, const dou
     for (long i = 0; i < n; ++i) {
       const double* gi = g2 + (size_t)i * G_STRIDE;
       const double* gai = g2a ? g2a + (size_t)i * G_STRIDE : NULL;
+      const double* gani = g2an ? g2an + (size_t)i * G_STRIDE : NULL;
       int any = 0;
       for (int j = 0; j < G_STRIDE; ++j) any |= (gi[j] != 0.0) || (gai && gai[j] != 0.0);
       if (!any) continue;
@@ -658,10 +691,13 @@ void orc_backward(int n, int sh_deg, const double* theta, int n_views, const dou
         int ok = project_buf(buf, sh_deg, &cam, &cfg, out, &depth, cov, cm);
         buf[j] = save;
         if (!ok) continue;
-        double acc = 0.0, acc_abs = 0.0;
+        double acc = 0.0, acc_abs = 0.0, acc_absn = 0.0;
         for (int o = 0; o < G_STRIDE; ++o) {
           acc += gi[o] * (cimag(out[o]) / hc);
-          if (gai) acc_abs += gai[o] * fabs(cimag(out[o]) / hc);
+          if (gai) {
+            acc_abs += gai[o] * fabs(cimag(out[o]) / hc);
+            acc_absn += gani[o] * fabs(cimag(out[o]) / hc);
+          }
         }
         /* theta index of parameter j of component i */
         size_t row;
@@ -673,6 +709,7 @@ void orc_backward(int n, int sh_deg, const double* theta, int n_views, const dou
         else row = TH_SH(n) + (j - 12) * (size_t)n;
         grad[row + (size_t)i] += acc;
         if (grad_abs) grad_abs[row + (size_t)i] += acc_abs;
+        if (grad_absn) grad_absn[row + (size_t)i] += acc_absn;
       }
     }
     pix_off += pv ? (size_t)np : 0;
@@ -681,6 +718,7 @@ void orc_backward(int n, int sh_deg, const double* theta, int n_views, const dou
   free(proj);
   free(g2);
   free(g2a);
+  free(g2an);
 }
 
 /* ======================================================================== */

@@ -206,3 +206,4 @@ def sss_read_status(plan, ws_ptr: int, stream=None):
     _check("sss_read_status", lib().sss_read_status(ctypes.byref(plan), c_void_p(ws_ptr), ctypes.byref(st),
                                                     ctypes.byref(need), ctypes.byref(done), _stream(stream)))
     return int(st.value), int(need.value), int(done.value)
+

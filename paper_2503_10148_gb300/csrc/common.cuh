@@ -61,9 +61,13 @@ inline unsigned ceil_div(size_t a, size_t b) { return (unsigned)((a + b - 1) / b
 
 // ------------------------------------------------------------ splat record
 // Render record of one entry, three float4 (48 bytes):
-//   a = {mean2D x, mean2D y, conic a, conic b}
+//   a = {mean2D x - ox, mean2D y - oy, conic a, conic b}
 //   b = {conic c, o, h_max, nu}
-//   c = {r, g, b, 1/nu}
+//   c = {r, g, b, origin}   origin = bits of (ox | oy << 16)
+// (ox, oy) is the pixel corner of the entry's first tile: every pixel that
+// can see the splat has x >= ox, y >= oy, so (x - ox) is an exact small
+// integer and the stored, tile-relative mean keeps FP32's fine spacing near 0
+// instead of its ~1e-4 px spacing at 1000 px.
 // h = a dx^2 + 2 b dx dy + c dy^2 with (dx, dy) = pixel centre - mean2D.
 struct SplatRec {
   float4 a, b, c;
@@ -155,6 +159,12 @@ __device__ __forceinline__ bool ellipse_hits_box(float mx, float my, float ca, f
 // decides.  Pairs beyond it have |alpha| below tau by far more than the FP32
 // error of alpha.
 constexpr float kHPad = 1e-3f;
+
+__device__ __forceinline__ void rec_origin(float w, int& ox, int& oy) {
+  const uint32_t o = __float_as_uint(w);
+  ox = (int)(o & 0xffffu);
+  oy = (int)(o >> 16);
+}
 
 // ------------------------------------------------------------ warp helpers
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }

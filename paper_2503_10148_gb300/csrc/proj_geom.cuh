@@ -27,13 +27,13 @@ __device__ __forceinline__ CompParams load_comp(const sss_params& S, uint32_t i)
   return c;
 }
 
-// View-independent part: normalised quaternion, rotation, scales and
-// Sigma = R S S^T R^T (Sec. 3.1).
+// View-independent part: normalised quaternion, rotation, scales and the
+// factor M = R S of Sigma = R S S^T R^T = M M^T (Sec. 3.1).
 struct CompShape {
   float qn[4], qinv_norm;  // normalised quaternion (w, x, y, z), 1 / |q|
   float R[9];              // row-major rotation
   float s[3];              // exp(log_scale)
-  float Sig[6];            // xx, xy, xz, yy, yz, zz
+  float M[9];              // R diag(s), row-major
 };
 
 __device__ __forceinline__ CompShape comp_shape(const CompParams& c) {
@@ -54,18 +54,10 @@ __device__ __forceinline__ CompShape comp_shape(const CompParams& c) {
   g.R[8] = 1.0f - 2.0f * (x * x + y * y);
 #pragma unroll
   for (int k = 0; k < 3; ++k) g.s[k] = expf(c.ls[k]);
-  float M[9];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) M[r * 3 + k] = g.R[r * 3 + k] * g.s[k];
-  auto dot3 = [&](int a, int b) { return M[a * 3] * M[b * 3] + M[a * 3 + 1] * M[b * 3 + 1] + M[a * 3 + 2] * M[b * 3 + 2]; };
-  g.Sig[0] = dot3(0, 0);
-  g.Sig[1] = dot3(0, 1);
-  g.Sig[2] = dot3(0, 2);
-  g.Sig[3] = dot3(1, 1);
-  g.Sig[4] = dot3(1, 2);
-  g.Sig[5] = dot3(2, 2);
+    for (int k = 0; k < 3; ++k) g.M[r * 3 + k] = g.R[r * 3 + k] * g.s[k];
   return g;
 }
 
@@ -78,6 +70,7 @@ struct ViewGeom {
   float limx, limy;
   float j00, j02, j11, j12;
   float T[6];             // J W, rows 0 and 1
+  float N[6];             // T M (2x3): Sigma2D = N N^T (+ lowpass I)
   float A, B, C, det;     // Sigma2D (+ lowpass on the diagonal)
   float con[3];           // conic a, b, c
   float m2[2];            // mean2D
@@ -113,19 +106,22 @@ __device__ __forceinline__ ViewGeom view_geom(const CompParams& c, const CompSha
     v.T[k] = v.j00 * V[0 * 4 + k] + v.j02 * V[2 * 4 + k];
     v.T[3 + k] = v.j11 * V[1 * 4 + k] + v.j12 * V[2 * 4 + k];
   }
-  // Sigma T^T, columns for rows 0 and 1 of T
-  const float* S = g.Sig;
-  float u0[3], u1[3];
-  u0[0] = S[0] * v.T[0] + S[1] * v.T[1] + S[2] * v.T[2];
-  u0[1] = S[1] * v.T[0] + S[3] * v.T[1] + S[4] * v.T[2];
-  u0[2] = S[2] * v.T[0] + S[4] * v.T[1] + S[5] * v.T[2];
-  u1[0] = S[0] * v.T[3] + S[1] * v.T[4] + S[2] * v.T[5];
-  u1[1] = S[1] * v.T[3] + S[3] * v.T[4] + S[4] * v.T[5];
-  u1[2] = S[2] * v.T[3] + S[4] * v.T[4] + S[5] * v.T[5];
-  v.A = v.T[0] * u0[0] + v.T[1] * u0[1] + v.T[2] * u0[2] + cfg.lowpass;
-  v.B = v.T[0] * u1[0] + v.T[1] * u1[1] + v.T[2] * u1[2];
-  v.C = v.T[3] * u1[0] + v.T[4] * u1[1] + v.T[5] * u1[2] + cfg.lowpass;
-  v.det = v.A * v.C - v.B * v.B;
+  // N = T M; Sigma2D = N N^T.  det(N N^T) = |n0 x n1|^2 (Lagrange identity):
+  // a sum of squares, accurate for elongated splats where AC - B^2 cancels.
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      v.N[r * 3 + k] = v.T[r * 3 + 0] * g.M[0 * 3 + k] + v.T[r * 3 + 1] * g.M[1 * 3 + k] + v.T[r * 3 + 2] * g.M[2 * 3 + k];
+  const float* n0 = v.N;
+  const float* n1 = v.N + 3;
+  const float a0 = n0[0] * n0[0] + n0[1] * n0[1] + n0[2] * n0[2];
+  const float c0 = n1[0] * n1[0] + n1[1] * n1[1] + n1[2] * n1[2];
+  const float x0 = n0[1] * n1[2] - n0[2] * n1[1], x1 = n0[2] * n1[0] - n0[0] * n1[2], x2 = n0[0] * n1[1] - n0[1] * n1[0];
+  v.A = a0 + cfg.lowpass;
+  v.B = n0[0] * n1[0] + n0[1] * n1[1] + n0[2] * n1[2];
+  v.C = c0 + cfg.lowpass;
+  v.det = x0 * x0 + x1 * x1 + x2 * x2 + cfg.lowpass * (a0 + c0 + cfg.lowpass);
   if (!(v.det > 0.0f)) {
     v.valid = false;
     return v;

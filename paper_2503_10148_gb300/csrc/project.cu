@@ -5,7 +5,8 @@
 // job (view) of that scene is projected from registers.  Per (job, component)
 // entry the kernel writes the 48-byte render record, the FP32 depth key, the
 // tile count and the tile rectangle.  HBM traffic per component: 240 B read
-// (degree 3) + 64 B written per view.
+// (degree 3) + 64 B written per view.  The screen-space mean is evaluated in
+// FP64 and stored relative to the splat's first tile (see SplatRec).
 #include "proj_geom.cuh"
 
 namespace sss {
@@ -36,20 +37,30 @@ __device__ __forceinline__ void project_component(const sss_frame_plan& P, int s
       rect[e] = make_uint2(0u, 0u);
       continue;
     }
+    // mean2D in FP64: in FP32, fx x/z + cx at ~1000 px carries ~1e-4 px of
+    // rounding, a large relative error on (pixel - mean) near the centre
+    const float* V = J.cam.viewmat;
+    const double pxd = (double)V[0] * c.mu[0] + (double)V[1] * c.mu[1] + (double)V[2] * c.mu[2] + (double)V[3];
+    const double pyd = (double)V[4] * c.mu[0] + (double)V[5] * c.mu[1] + (double)V[6] * c.mu[2] + (double)V[7];
+    const double pzd = (double)V[8] * c.mu[0] + (double)V[9] * c.mu[1] + (double)V[10] * c.mu[2] + (double)V[11];
+    const double mxd = (double)J.cam.fx * pxd / pzd + (double)J.cam.cx;
+    const double myd = (double)J.cam.fy * pyd / pzd + (double)J.cam.cy;
     // extent: |o| T2D(h) >= tau  <=>  h <= h_max (reading of the SM's truncation)
     const float hmax = v.nu * expm1f(2.0f / (v.nu + 2.0f) * logf(fabsf(v.o) / cfg.tau));
-    const float ex = sqrtf(v.A * hmax), ey = sqrtf(v.C * hmax);
-    float fx0 = fmaxf(ceilf(v.m2[0] - ex - 0.5f), 0.0f);
-    float fx1 = fminf(floorf(v.m2[0] + ex - 0.5f), (float)(J.cam.width - 1));
-    float fy0 = fmaxf(ceilf(v.m2[1] - ey - 0.5f), 0.0f);
-    float fy1 = fminf(floorf(v.m2[1] + ey - 0.5f), (float)(J.cam.height - 1));
-    uint32_t nt = 0;
+    const double ex = sqrt((double)v.A * hmax), ey = sqrt((double)v.C * hmax);
+    const double fx0 = fmax(ceil(mxd - ex - 0.5), 0.0);
+    const double fx1 = fmin(floor(mxd + ex - 0.5), (double)(J.cam.width - 1));
+    const double fy0 = fmax(ceil(myd - ey - 0.5), 0.0);
+    const double fy1 = fmin(floor(myd + ey - 0.5), (double)(J.cam.height - 1));
+    uint32_t nt = 0, ox = 0, oy = 0;
     uint2 rc = make_uint2(0u, 0u);
     if (fx0 <= fx1 && fy0 <= fy1) {
       const uint32_t tx0 = (uint32_t)fx0 / (uint32_t)cfg.tile_w, tx1 = (uint32_t)fx1 / (uint32_t)cfg.tile_w;
       const uint32_t ty0 = (uint32_t)fy0 / (uint32_t)cfg.tile_h, ty1 = (uint32_t)fy1 / (uint32_t)cfg.tile_h;
       nt = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
       rc = make_uint2(tx0 | (tx1 << 16), ty0 | (ty1 << 16));
+      ox = tx0 * (uint32_t)cfg.tile_w;
+      oy = ty0 * (uint32_t)cfg.tile_h;
     }
     // view-dependent colour: max(SH . Y(dir) + 0.5, 0)
     float cc[3];
@@ -67,9 +78,9 @@ __device__ __forceinline__ void project_component(const sss_frame_plan& P, int s
       rgb[ch] = fmaxf(acc, 0.0f);
     }
     SplatRec r;
-    r.a = make_float4(v.m2[0], v.m2[1], v.con[0], v.con[1]);
+    r.a = make_float4((float)(mxd - (double)ox), (float)(myd - (double)oy), v.con[0], v.con[1]);
     r.b = make_float4(v.con[2], v.o, hmax, v.nu);
-    r.c = make_float4(rgb[0], rgb[1], rgb[2], 1.0f / v.nu);
+    r.c = make_float4(rgb[0], rgb[1], rgb[2], __uint_as_float(ox | (oy << 16)));
     rec[e] = r;
     dkey[e] = __float_as_uint(v.p[2]);
     ntiles[e] = nt;

@@ -7,21 +7,15 @@
 // parameter gradient is written once (planar, coalesced).
 //
 // Chain, for one view with upstream g = dL/d(mean2D, conic a b c, o, nu, rgb):
-//   conic = Sigma2D^-1, Sigma2D = [[A, B], [B, C]], D = AC - B^2:
-//     dA = (-ga C^2 + gb B C - gc B^2) / D^2
-//     dB = (2 ga B C - gb (A C + B^2) + 2 gc A B) / D^2
-//     dC = (-ga B^2 + gb A B - gc A^2) / D^2
-//   Sigma2D = T Sigma T^T (T = J W, rows t0, t1):
-//     dL/dSigma (symmetric part) = dA t0 t0^T + dB/2 (t0 t1^T + t1 t0^T) + dC t1 t1^T
-//     dL/dt0 = 2 dA Sigma t0 + dB Sigma t1,  dL/dt1 = 2 dC Sigma t1 + dB Sigma t0
+//   conic Q = Sigma2D^-1: dL/dSigma2D = -Q G Q, G = [[ga, gb/2], [gb/2, gc]]
+//   Sigma2D = K D K^T with K = T R, T = J W
 //   T = J W:  dJ_rc = sum_k dT_rk W_ck (only J00, J02, J11, J12 are non-zero)
 //   J(p) = [[fx/z, 0, -fx tx/z^2], [0, fy/z, -fy ty/z^2]], tx = x unless x/z
 //     was limited (then tx = +-lim z, and its gradient goes to z)
 //   mean2D = (fx x/z + cx, fy y/z + cy);  p = W mu + t
-//   Sigma = M M^T, M = R diag(s): dL/dM = 2 dL/dSigma M,
-//     dL/ds_k = sum_r dM_rk R_rk, dL/dlog_s = s dL/ds, dL/dR_rk = dM_rk s_k
-//   R(q / |q|): derivative of the quaternion rotation formula, then the
-//     projection (I - q q^T) / |q| of the normalisation
+//   Sigma = R D R^T, D = diag(s^2): log-scale and rotation gradients taken in
+//     the splat's frame (G' = R^T dL/dSigma R; see the kernel), the rotation
+//     as a local rotation omega mapped to the quaternion by q (x) (0, omega/2)
 //   rgb = max(SH . Y(d / |d|) + 0.5, 0), d = mu - camera centre:
 //     dL/dsh_kc = g_c Y_k (0 where clamped), dL/dd = (I - u u^T)/|d| grad_u
 //   o = tanh(raw): dL/draw = go (1 - o^2);  nu: passes where not limited.
@@ -41,7 +35,8 @@ __device__ __forceinline__ void project_bwd_component(const sss_frame_plan& P, i
   const float* g2d = ws_ptr<float>(ws, P.ws_off_grad2d);
   const size_t n = (size_t)S.n;
 
-  float d_mu[3] = {0, 0, 0}, d_Sig[6] = {0, 0, 0, 0, 0, 0}, d_o = 0.0f, d_nu = 0.0f;
+  float d_mu[3] = {0, 0, 0}, d_ls[3] = {0, 0, 0}, bw[3] = {0, 0, 0};
+  float d_o = 0.0f, d_nu = 0.0f;
   float d_sh[3 * K];
 #pragma unroll
   for (int k = 0; k < 3 * K; ++k) d_sh[k] = 0.0f;
@@ -60,41 +55,51 @@ __device__ __forceinline__ void project_bwd_component(const sss_frame_plan& P, i
     if (!v.valid) continue;
     touched = true;
     const float* V = J.cam.viewmat;
-    const float A = v.A, B = v.B, C = v.C;
-    const float id2 = 1.0f / (v.det * v.det);
-    const float ga = g0.z, gb = g0.w, gc = g1.x;
-    const float dA = (-ga * C * C + gb * B * C - gc * B * B) * id2;
-    const float dB = (2.0f * ga * B * C - gb * (A * C + B * B) + 2.0f * gc * A * B) * id2;
-    const float dC = (-ga * B * B + gb * A * B - gc * A * A) * id2;
-    const float* t0 = v.T;
-    const float* t1 = v.T + 3;
-    // dL/dSigma (symmetric part), packed xx, xy, xz, yy, yz, zz
-    {
-      const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        const int a = ia[k], b = ib[k];
-        d_Sig[k] += dA * t0[a] * t0[b] + 0.5f * dB * (t0[a] * t1[b] + t1[a] * t0[b]) + dC * t1[a] * t1[b];
-      }
-    }
-    // Sigma t0, Sigma t1
-    const float* Sg = gs.Sig;
-    float st0[3], st1[3];
-    st0[0] = Sg[0] * t0[0] + Sg[1] * t0[1] + Sg[2] * t0[2];
-    st0[1] = Sg[1] * t0[0] + Sg[3] * t0[1] + Sg[4] * t0[2];
-    st0[2] = Sg[2] * t0[0] + Sg[4] * t0[1] + Sg[5] * t0[2];
-    st1[0] = Sg[0] * t1[0] + Sg[1] * t1[1] + Sg[2] * t1[2];
-    st1[1] = Sg[1] * t1[0] + Sg[3] * t1[1] + Sg[4] * t1[2];
-    st1[2] = Sg[2] * t1[0] + Sg[4] * t1[1] + Sg[5] * t1[2];
-    float dj00 = 0.f, dj02 = 0.f, dj11 = 0.f, dj12 = 0.f;
+    // Covariance chain, in the splat's own frame.  With Gc the conic gradient
+    // as a symmetric matrix [[ga, gb/2], [gb/2, gc]]: dL/dSigma2D = -Q Gc Q
+    // (Q = conic), Sigma2D = K D K^T + lowpass I with K = T R (2x3) and
+    // D = diag(s^2).  With p_k = Q K_k and u_k = Gc p_k, the gradient w.r.t.
+    // Sigma in the local frame is G'_ij = -p_i . u_j, so
+    //   dL/dlog_s_k = 2 s_k^2 G'_kk,
+    //   dL/domega   = 2 ((d1 - d2) G'_12, (d2 - d0) G'_02, (d0 - d1) G'_01)
+    // for a local rotation R (I + [omega]x), and dL/dT = -2 Q U M^T with
+    // U_k = s_k u_k.  Only products of well-scaled terms appear: the rotation
+    // gradient of a near-isotropic splat comes out as the small difference
+    // d_i - d_j times G'_ij instead of a cancellation of large terms.
+    const float qa = v.con[0], qb = v.con[1], qc = v.con[2];
+    const float ga = g0.z, gbh = 0.5f * g0.w, gc = g1.x;
+    float p0[3], p1[3], u0[3], u1[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const float dt0 = 2.0f * dA * st0[k] + dB * st1[k];
-      const float dt1 = 2.0f * dC * st1[k] + dB * st0[k];
-      dj00 += dt0 * V[0 * 4 + k];
-      dj02 += dt0 * V[2 * 4 + k];
-      dj11 += dt1 * V[1 * 4 + k];
-      dj12 += dt1 * V[2 * 4 + k];
+      const float K0 = v.T[0] * gs.R[0 * 3 + k] + v.T[1] * gs.R[1 * 3 + k] + v.T[2] * gs.R[2 * 3 + k];
+      const float K1 = v.T[3] * gs.R[0 * 3 + k] + v.T[4] * gs.R[1 * 3 + k] + v.T[5] * gs.R[2 * 3 + k];
+      p0[k] = qa * K0 + qb * K1;
+      p1[k] = qb * K0 + qc * K1;
+      u0[k] = ga * p0[k] + gbh * p1[k];
+      u1[k] = gbh * p0[k] + gc * p1[k];
+      d_ls[k] -= 2.0f * gs.s[k] * gs.s[k] * (p0[k] * u0[k] + p1[k] * u1[k]);
+    }
+    bw[0] += p0[1] * u0[2] + p1[1] * u1[2];
+    bw[1] += p0[0] * u0[2] + p1[0] * u1[2];
+    bw[2] += p0[0] * u0[1] + p1[0] * u1[1];
+    float dj00 = 0.f, dj02 = 0.f, dj11 = 0.f, dj12 = 0.f;
+    {
+      float qu0[3], qu1[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float s2 = gs.s[k] * gs.s[k];
+        qu0[k] = s2 * (qa * u0[k] + qb * u1[k]);
+        qu1[k] = s2 * (qb * u0[k] + qc * u1[k]);
+      }
+#pragma unroll
+      for (int cidx = 0; cidx < 3; ++cidx) {
+        const float dt0 = -2.0f * (qu0[0] * gs.R[cidx * 3 + 0] + qu0[1] * gs.R[cidx * 3 + 1] + qu0[2] * gs.R[cidx * 3 + 2]);
+        const float dt1 = -2.0f * (qu1[0] * gs.R[cidx * 3 + 0] + qu1[1] * gs.R[cidx * 3 + 1] + qu1[2] * gs.R[cidx * 3 + 2]);
+        dj00 += dt0 * V[0 * 4 + cidx];
+        dj02 += dt0 * V[2 * 4 + cidx];
+        dj11 += dt1 * V[1 * 4 + cidx];
+        dj12 += dt1 * V[2 * 4 + cidx];
+      }
     }
     const float iz = v.inv_z, iz2 = iz * iz, iz3 = iz2 * iz;
     const float fx = J.cam.fx, fy = J.cam.fy;
@@ -146,35 +151,20 @@ __device__ __forceinline__ void project_bwd_component(const sss_frame_plan& P, i
     }
   }
 
-  float d_ls[3] = {0, 0, 0}, d_q[4] = {0, 0, 0, 0};
+  float d_q[4] = {0, 0, 0, 0};
   if (touched) {
-    // dL/dM = 2 dSigma_sym M, M = R diag(s)
-    const float* R = gs.R;
-    float Gs[9] = {d_Sig[0], d_Sig[1], d_Sig[2], d_Sig[1], d_Sig[3], d_Sig[4], d_Sig[2], d_Sig[4], d_Sig[5]};
-    float dR[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        float dM = 0.0f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) dM += Gs[r * 3 + a] * R[a * 3 + k] * gs.s[k];
-        dM *= 2.0f;
-        d_ls[k] += dM * R[r * 3 + k] * gs.s[k];
-        dR[r * 3 + k] = dM * gs.s[k];
-      }
+    // d_i - d_j = (s_i - s_j)(s_i + s_j); dL/dq = (2 / |q|) Xi(q) dL/domega with
+    // Xi(q) v = q (x) (0, v) (right multiplication by a pure quaternion)
+    const float* sc = gs.s;
+    const float dw0 = -2.0f * (sc[1] - sc[2]) * (sc[1] + sc[2]) * bw[0];
+    const float dw1 = -2.0f * (sc[2] - sc[0]) * (sc[2] + sc[0]) * bw[1];
+    const float dw2 = -2.0f * (sc[0] - sc[1]) * (sc[0] + sc[1]) * bw[2];
     const float w = gs.qn[0], x = gs.qn[1], y = gs.qn[2], z = gs.qn[3];
-    float dqn[4];
-    dqn[0] = 2.0f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
-    dqn[1] = 2.0f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.0f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
-                     2.0f * x * dR[8]);
-    dqn[2] = 2.0f * (-2.0f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] -
-                     2.0f * y * dR[8]);
-    dqn[3] = 2.0f * (-2.0f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.0f * z * dR[4] + y * dR[5] +
-                     x * dR[6] + y * dR[7]);
-    const float proj = dqn[0] * w + dqn[1] * x + dqn[2] * y + dqn[3] * z;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) d_q[k] = (dqn[k] - gs.qn[k] * proj) * gs.qinv_norm;
+    const float f = 2.0f * gs.qinv_norm;
+    d_q[0] = f * (-x * dw0 - y * dw1 - z * dw2);
+    d_q[1] = f * (w * dw0 - z * dw1 + y * dw2);
+    d_q[2] = f * (z * dw0 + w * dw1 - x * dw2);
+    d_q[3] = f * (-y * dw0 + x * dw1 + w * dw2);
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) G.mean[k * n + i] = d_mu[k];

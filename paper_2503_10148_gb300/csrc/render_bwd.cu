@@ -3,15 +3,26 @@
 // Same CTA/warp/lane layout as the forward.  Each pixel walks its tile's list
 // from its last contributor back to the front, recomputing the transmittance
 // before every contributor as T_k = T_{k+1} / (1 - alpha_k) (no per-pixel
-// lists are stored), and keeps S = colour composited behind the current
-// splat + T_final bg.  For a contributor k:
+// lists are stored).  With S_k the colour composited behind contributor k
+// (plus T_final bg), dC/dalpha_k = T_k rgb_k - S_k / (1 - alpha_k).  Writing
+// B_k = S_k / T_{k+1} -- the colour seen behind k, normalised -- this is
+// T_k (rgb_k - B_k), and B follows the blend B_{k-1} = alpha_k rgb_k +
+// (1 - alpha_k) B_k from B = bg at the back: no division, and the rounding of
+// the recovered T_k scales the (often small) difference instead of its two
+// large operands.  For a contributor k:
 //   dL/drgb   = alpha T_k g                               (g = dL/dC)
-//   dL/dalpha = g . (T_k rgb - S / (1 - alpha))
+//   dL/dalpha = T_k g . (rgb - B)
 //   dL/do     = dL/dalpha T2D,  dL/dT2D = dL/dalpha o   (unless alpha was clamped)
 //   dL/dh     = dL/dT2D dT2D/dh,  dT2D/dh = -(nu+2)/(2 nu) T2D / (1 + h/nu)
 //   dL/dnu    = dL/dT2D T2D [-1/2 ln(1 + h/nu) + (nu+2) h / (2 nu^2 (1 + h/nu))]
 //               (mode 1 drops the logarithm, as printed in the SM)
 //   dh/dmean2D = -2 conic d,  dh/d(a, b, c) = (dx^2, 2 dx dy, dy^2).
+// The factor of dT2D/dnu, f = -1/2 ln(1 + x) + (nu+2) x / (2 nu (1 + x)) with
+// x = h/nu, is O(x^2) while its two terms are O(x): evaluated as written it
+// cancels.  With u = x / (1 + x) it equals u/nu - g/2, g = ln(1 + x) - u =
+// sum_{k>=2} u^k / k (from -ln(1 - u)), a sum of positive terms; for
+// u < 1/4 the series to k = 13 is used (truncation < 1e-9 of g), above that the
+// direct difference (cancellation at most 8x).
 // A lane first sums its pixels; the warp then reduces the 10 sums with a
 // 16-slot reduce-scatter (16 shuffles instead of 10 x 5) and 10 lanes add the
 // totals to the splat's record with one vectorless RED each.
@@ -39,6 +50,25 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], unsigned 
   return v[0];
 }
 
+__device__ __forceinline__ float log1p_minus_u(float u, float log_base) {
+  if (u < 0.25f) {
+    float p = 1.0f / 13.0f;
+    p = fmaf(u, p, 1.0f / 12.0f);
+    p = fmaf(u, p, 1.0f / 11.0f);
+    p = fmaf(u, p, 1.0f / 10.0f);
+    p = fmaf(u, p, 1.0f / 9.0f);
+    p = fmaf(u, p, 1.0f / 8.0f);
+    p = fmaf(u, p, 1.0f / 7.0f);
+    p = fmaf(u, p, 1.0f / 6.0f);
+    p = fmaf(u, p, 1.0f / 5.0f);
+    p = fmaf(u, p, 1.0f / 4.0f);
+    p = fmaf(u, p, 1.0f / 3.0f);
+    p = fmaf(u, p, 0.5f);
+    return u * u * p;
+  }
+  return log_base - u;
+}
+
 template <int PW, int PH, int B>
 __global__ void __launch_bounds__(256) k_render_bwd(const sss_frame_plan P, void* ws,
                                                     const float* __restrict__ dl_drgb) {
@@ -60,14 +90,12 @@ __global__ void __launch_bounds__(256) k_render_bwd(const sss_frame_plan P, void
   const int bx = tx * TW + (warp & 1) * 8 * PW, by = ty * TH + (warp >> 1) * 4 * PH;
   const int lx = bx + (lane & 7) * PW, ly = by + (lane >> 3) * PH;
   const int W = J.cam.width, H = J.cam.height;
-  const float box_x0 = bx + 0.5f, box_x1 = bx + 8 * PW - 0.5f;
-  const float box_y0 = by + 0.5f, box_y1 = by + 4 * PH - 0.5f;
   const size_t hw = (size_t)W * H;
 
   const float* Tf = ws_ptr<float>(ws, P.ws_off_T);
   const uint32_t* Lf = ws_ptr<uint32_t>(ws, P.ws_off_last);
   const float* gimg = dl_drgb + 3 * (size_t)J.pix_base;
-  float T[NPIX], S[NPIX][3], g[NPIX][3];
+  float T[NPIX], Bc[NPIX][3], g[NPIX][3];
   uint32_t last[NPIX];
   uint32_t lane_max = 0;
 #pragma unroll
@@ -85,9 +113,9 @@ __global__ void __launch_bounds__(256) k_render_bwd(const sss_frame_plan P, void
       last[p] = 0u;
       g[p][0] = g[p][1] = g[p][2] = 0.0f;
     }
-    S[p][0] = T[p] * cfg.bg[0];
-    S[p][1] = T[p] * cfg.bg[1];
-    S[p][2] = T[p] * cfg.bg[2];
+    Bc[p][0] = cfg.bg[0];
+    Bc[p][1] = cfg.bg[1];
+    Bc[p][2] = cfg.bg[2];
     lane_max = max(lane_max, last[p]);
   }
   const uint32_t warp_max = __reduce_max_sync(0xffffffffu, lane_max);
@@ -127,9 +155,12 @@ __global__ void __launch_bounds__(256) k_render_bwd(const sss_frame_plan P, void
 #pragma unroll
       for (int k = 0; k < NW; ++k) {
         const float4 a = s_a[k * 32 + lane], b = s_b[k * 32 + lane];
+        int ox, oy;
+        rec_origin(s_c[k * 32 + lane].w, ox, oy);
         const bool hit = b.z >= 0.0f && (lo + k * 32 + lane) < warp_max &&
-                         ellipse_hits_box(a.x, a.y, a.z, a.w, b.x, fmaf(b.z, 2.0f * kHPad, b.z) + 1e-3f, box_x0,
-                                          box_x1, box_y0, box_y1);
+                         ellipse_hits_box(a.x, a.y, a.z, a.w, b.x, fmaf(b.z, 2.0f * kHPad, b.z) + 1e-3f,
+                                          (float)(bx - ox) + 0.5f, (float)(bx - ox + 8 * PW) - 0.5f,
+                                          (float)(by - oy) + 0.5f, (float)(by - oy + 4 * PH) - 0.5f);
         mask[k] = __ballot_sync(0xffffffffu, hit);
       }
 #pragma unroll
@@ -142,7 +173,9 @@ __global__ void __launch_bounds__(256) k_render_bwd(const sss_frame_plan P, void
           const uint32_t pos = lo + si;
           const float4 a = s_a[si], b = s_b[si], c = s_c[si];
           const float cb2 = 2.0f * a.w, hpre = fmaf(b.z, kHPad, b.z);
-          const float nu = b.w, inv_nu = c.w, o = b.y;
+          const float nu = b.w, inv_nu = __frcp_rn(nu), o = b.y;
+          int ox, oy;
+          rec_origin(c.w, ox, oy);
           const float e_exp = fmaf(nu, -0.5f, -1.0f);  // -(nu+2)/2
           float v[16];
 #pragma unroll
@@ -151,30 +184,33 @@ __global__ void __launch_bounds__(256) k_render_bwd(const sss_frame_plan P, void
 #pragma unroll
           for (int p = 0; p < NPIX; ++p) {
             if (pos >= last[p]) continue;
-            const float dx = (float)(lx + p % PW) + 0.5f - a.x;
-            const float dy = (float)(ly + p / PW) + 0.5f - a.y;
+            const float dx = (float)(lx + p % PW - ox) + 0.5f - a.x;
+            const float dy = (float)(ly + p / PW - oy) + 0.5f - a.y;
             PairEval r;
             if (!eval_pair(dx, dy, a.z, cb2, b.x, hpre, o, nu, inv_nu, tau, amax, r)) continue;
             any = true;
-            const float inv_1ma = __fdividef(1.0f, 1.0f - r.alpha);
-            const float Tk = T[p] * inv_1ma;
+            const float Tk = T[p] * __fdividef(1.0f, 1.0f - r.alpha);
             T[p] = Tk;
             const float w = r.alpha * Tk;
             float dl_da = 0.0f;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
               const float cch = ch == 0 ? c.x : (ch == 1 ? c.y : c.z);
+              const float diff = cch - Bc[p][ch];
               v[7 + ch] = fmaf(w, g[p][ch], v[7 + ch]);
-              dl_da = fmaf(g[p][ch], fmaf(Tk, cch, -S[p][ch] * inv_1ma), dl_da);
-              S[p][ch] = fmaf(w, cch, S[p][ch]);
+              dl_da = fmaf(g[p][ch], diff, dl_da);
+              Bc[p][ch] = fmaf(r.alpha, diff, Bc[p][ch]);
             }
+            dl_da *= Tk;
             if (r.clamped) continue;
             v[5] = fmaf(dl_da, r.t2d, v[5]);
             const float dl_dt = dl_da * o;
             const float inv_base = __fdividef(1.0f, fmaf(r.h, inv_nu, 1.0f));
             const float dl_dh = dl_dt * e_exp * inv_nu * r.t2d * inv_base;
-            const float second = -e_exp * r.h * inv_nu * inv_nu * inv_base;
-            const float dnu = paper_nu ? second : fmaf(-0.5f, r.log_base, second);
+            const float u = r.h * inv_nu * inv_base;  // x / (1 + x)
+            // paper form: (nu+2) x / (2 nu (1+x)) = u/2 + u/nu; exact: u/nu - g/2
+            const float dnu = paper_nu ? fmaf(0.5f, u, u * inv_nu)
+                                       : fmaf(-0.5f, log1p_minus_u(u, r.log_base), u * inv_nu);
             v[6] = fmaf(dl_dt * r.t2d, dnu, v[6]);
             v[0] = fmaf(dl_dh, -2.0f * fmaf(a.z, dx, a.w * dy), v[0]);
             v[1] = fmaf(dl_dh, -2.0f * fmaf(a.w, dx, b.x * dy), v[1]);

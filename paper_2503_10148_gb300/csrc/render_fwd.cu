@@ -32,8 +32,6 @@ __global__ void __launch_bounds__(256) k_render_fwd(const sss_frame_plan P, void
   const int bx = tx * TW + (warp & 1) * 8 * PW, by = ty * TH + (warp >> 1) * 4 * PH;
   const int lx = bx + (lane & 7) * PW, ly = by + (lane >> 3) * PH;
   const int W = J.cam.width, H = J.cam.height;
-  const float box_x0 = bx + 0.5f, box_x1 = bx + 8 * PW - 0.5f;
-  const float box_y0 = by + 0.5f, box_y1 = by + 4 * PH - 0.5f;
 
   float T[NPIX], C[NPIX][3];
   uint32_t last[NPIX];
@@ -76,9 +74,12 @@ __global__ void __launch_bounds__(256) k_render_fwd(const sss_frame_plan P, void
 #pragma unroll
     for (int k = 0; k < NW; ++k) {
       const float4 a = s_a[k * 32 + lane], b = s_b[k * 32 + lane];
+      int ox, oy;
+      rec_origin(s_c[k * 32 + lane].w, ox, oy);
       const bool hit = b.z >= 0.0f &&
-                       ellipse_hits_box(a.x, a.y, a.z, a.w, b.x, fmaf(b.z, 2.0f * kHPad, b.z) + 1e-3f, box_x0,
-                                        box_x1, box_y0, box_y1);
+                       ellipse_hits_box(a.x, a.y, a.z, a.w, b.x, fmaf(b.z, 2.0f * kHPad, b.z) + 1e-3f,
+                                        (float)(bx - ox) + 0.5f, (float)(bx - ox + 8 * PW) - 0.5f,
+                                        (float)(by - oy) + 0.5f, (float)(by - oy + 4 * PH) - 0.5f);
       mask[k] = __ballot_sync(0xffffffffu, hit);
     }
 #pragma unroll
@@ -89,16 +90,18 @@ __global__ void __launch_bounds__(256) k_render_fwd(const sss_frame_plan P, void
         m &= m - 1;
         const int si = k * 32 + bit;
         const float4 a = s_a[si], b = s_b[si], c = s_c[si];
-        const float cb2 = 2.0f * a.w, hpre = fmaf(b.z, kHPad, b.z);
+        const float cb2 = 2.0f * a.w, hpre = fmaf(b.z, kHPad, b.z), inv_nu = __frcp_rn(b.w);
+        int ox, oy;
+        rec_origin(c.w, ox, oy);
         const uint32_t pos1 = b0 + si - range.x + 1;
 #pragma unroll
         for (int p = 0; p < NPIX; ++p) {
           if (done[p]) continue;
-          const float dx = (float)(lx + p % PW) + 0.5f - a.x;
-          const float dy = (float)(ly + p / PW) + 0.5f - a.y;
+          const float dx = (float)(lx + p % PW - ox) + 0.5f - a.x;
+          const float dy = (float)(ly + p / PW - oy) + 0.5f - a.y;
           PairEval r;
           ++n_eval;
-          if (!eval_pair(dx, dy, a.z, cb2, b.x, hpre, b.y, b.w, c.w, tau, amax, r)) continue;
+          if (!eval_pair(dx, dy, a.z, cb2, b.x, hpre, b.y, b.w, inv_nu, tau, amax, r)) continue;
           const float Tn = T[p] * (1.0f - r.alpha);
           if (Tn < tmin) {
             done[p] = true;

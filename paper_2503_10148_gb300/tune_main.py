@@ -1,0 +1,33 @@
+"""Runs the autotuner on a named workload and stores the choice.
+
+    python -m paper_2503_10148_gb300.tune_main [workload] [--steps K]
+"""
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+import torch
+
+from . import autotune, build, frame as F, inputs
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workload", nargs="?", default="clusters_1p5m_4views")
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--out", default=autotune.CACHE)
+    args = ap.parse_args()
+    build.build()
+    scene_np, cams = getattr(inputs, args.workload)()
+    cams = [F.f32_camera(c) for c in cams]
+    dev = torch.device("cuda", 0)
+    scene = F.Scene.from_numpy(scene_np, dev)
+    targets = torch.as_tensor(np.concatenate([t.reshape(-1) for t in inputs.target_images(cams, seed=3)]),
+                              device=dev)
+    choice = autotune.tune(args.workload, scene, cams, targets, steps=args.steps, device=dev, path=args.out)
+    print(choice)
+
+
+if __name__ == "__main__":
+    main()

@@ -66,23 +66,44 @@ def scene_grads_flat(g: frame.Scene) -> np.ndarray:
     return np.concatenate([g.t[f].detach().cpu().numpy().reshape(-1).astype(np.float64) for f in frame.FIELDS])
 
 
-GRAD_REL = 1e-3     # per-element relative bar ...
-GRAD_FLOOR = 1e-2   # ... against max(|g_ref|, GRAD_FLOOR * sum of |summands|)
-GRAD_NORM = 1e-4    # and ||g - g_ref|| / ||g_ref|| per group
+GRAD_REL = 1e-3   # relative bar per element ...
+U32 = 2.0 ** -24  # FP32 unit roundoff
+# ... unless the difference is within the FP32 rounding bound of the sums:
+# u * (16 * sum |term| n + 256 * sum |term|), n the contributor count of each
+# term's pixel (the transmittance is recovered by one division per contributor,
+# so its rounding grows with n) and 256 u for the per-term evaluation (MUFU
+# lg2/ex2 approximations times the exponent (nu+2)/2, mean2D rounding).
+GRAD_NORM = 1e-4  # and ||g - g_ref|| / ||g_ref|| per group
 
 
-def grad_den(ref, absref, floor=GRAD_FLOOR):
-    """Denominator of the relative error: |g_ref|, but at least GRAD_FLOOR of
-    the magnitude summed into it (a sum of terms of both signs -- the gradient
-    of a splat's position sums pixels on either side of it -- is only as
-    accurate in FP32 as its summands, not as its result)."""
+def grad_den(ref, mag, extra=0.0):
+    """Per-element scale of the bar: max(|g_ref|, FP32 bound / GRAD_REL)."""
+    bound = U32 * (16.0 * mag.absn + 256.0 * mag.abs) + extra
     scale = max(float(np.abs(ref).max()), 1e-30)
-    return np.maximum(np.maximum(np.abs(ref), floor * absref), 1e-7 * scale)
+    return np.maximum(np.maximum(np.abs(ref), bound / GRAD_REL), 1e-9 * scale)
 
 
-def assert_groups_close(got, ref, n, sh_degree, absref, rel=GRAD_REL, norm=GRAD_NORM, label=""):
-    """Per parameter group: every element within ``rel`` of grad_den and the
-    group's relative L2 error within ``norm``."""
+def sh_basis_bound(n, sh_degree, mag2d):
+    """Extra FP32 bound of the SH-coefficient gradients dL/dsh_kc =
+    sum_views dL/drgb_c Y_k(dir): a degree <= 3 basis value at an FP32 unit
+    direction (coefficients <= 3) carries up to ~64 u of absolute rounding,
+    which matters where Y_k(dir) itself is near zero.  Returns a theta-sized
+    array (zero outside the SH rows)."""
+    K = (sh_degree + 1) ** 2
+    sl = oracle.theta_slices(n, sh_degree)
+    extra = np.zeros(sl["sh"].stop)
+    rgb_mag = sum(mag2d.abs[j][:, 7:10] for j in range(mag2d.abs.shape[0]))  # [n][3]
+    for k in range(K):
+        for c in range(3):
+            r = 3 * k + c
+            extra[sl["sh"].start + r * n:sl["sh"].start + (r + 1) * n] = 64.0 * U32 * rgb_mag[:, c]
+    return extra
+
+
+def assert_groups_close(got, ref, n, sh_degree, mag, rel=GRAD_REL, norm=GRAD_NORM, label="", extra=None):
+    """Per parameter group: every element within ``rel`` of grad_den (1e-3
+    relative, or the FP32 rounding bound of its sums) and the group's relative
+    L2 error within ``norm``."""
     sl = oracle.theta_slices(n, sh_degree)
     report = {}
     for name, s in sl.items():
@@ -91,7 +112,7 @@ def assert_groups_close(got, ref, n, sh_degree, absref, rel=GRAD_REL, norm=GRAD_
         if scale == 0:
             assert np.abs(a).max() == 0, (label, name)
             continue
-        den = grad_den(b, absref[s])
+        den = grad_den(b, mag[s], 0.0 if extra is None else extra[s])
         relerr = np.abs(a - b) / den
         l2 = float(np.linalg.norm(a - b) / np.linalg.norm(b))
         report[name] = (float(relerr.max()), l2)

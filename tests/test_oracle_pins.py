@@ -458,19 +458,26 @@ def test_analytic_gradient_matches_central_differences():
 
 
 def test_summand_magnitudes_bound_the_gradient():
-    """grad_abs sums |summand|: it bounds |grad| (triangle inequality) and
-    equals it when a parameter receives a single summand."""
+    """grad_abs sums operand magnitudes of the summands: it bounds |grad|
+    (triangle inequality) and equals it for a single contributor on a black
+    background (no subtraction inside the term)."""
     sc = _grad_scene(n=60, seed=4)
     cam = inputs.look_at((0.2, 0.1, 3.0), width=40, height=32)
     w = inputs.linear_loss_weights([cam], seed=2)
-    g, g2, ga, g2a = oracle.backward(sc, [cam], None, w, want_grad2d=True, want_abs=True)
+    g, g2, mag, mag2 = oracle.backward(sc, [cam], None, w, want_grad2d=True, want_abs=True)
+    ga, g2a = mag.abs, mag2.abs
     assert np.all(ga >= np.abs(g) * (1 - 1e-12)) and np.all(g2a >= np.abs(g2) * (1 - 1e-12))
     assert np.any(ga > np.abs(g) * 1.5)  # cancellation does occur
+    assert np.all(mag.absn >= ga * (1 - 1e-12))  # weights are contributor counts >= 1
     one = _one_component([0.05, -0.04, 0.1], [-2.2, -2.6, -2.4], [0.8, 0.1, 0.3, -0.2], 3.0, 0.7, rgb=[0.2, 0.5, 0.7])
     pix = [np.array([40 * 16 + 20], np.int64)]
-    dl = [np.array([[0.3], [-0.2], [0.5]])]
-    g, g2, ga, g2a = oracle.backward(one, [cam], None, dl, pix, want_grad2d=True, want_abs=True)
-    assert np.allclose(g2a, np.abs(g2), rtol=1e-14, atol=0)
+    dl = [np.array([[0.3], [0.0], [0.0]])]  # one channel: no cancellation across channels
+    g, g2, mag, mag2 = oracle.backward(one, [cam], None, dl, pix, want_grad2d=True, want_abs=True)
+    g2a = mag2.abs
+    # dL/do and dL/drgb of a lone contributor on black are single products
+    keep = [5, 7, 8, 9]
+    assert np.allclose(g2a[..., keep], np.abs(g2[..., keep]), rtol=1e-13, atol=0)
+    assert np.all(g2a >= np.abs(g2) * (1 - 1e-13))
 
 
 def test_paper_printed_nu_gradient_disagrees_with_differences():
