@@ -291,6 +291,35 @@ int sss_sghmc_step(const sss_params* params, const sss_params* grads, float* mom
 int sss_loss_l1(const float* pred, const float* target, uint32_t count, float* dL_dpred, float* loss_out,
                 sss_stream_t stream);
 
+/* -------------------------------------------- no-allocation forward */
+/* No counterpart in the paper.  A forward render of one small frame for
+ * callers that cannot allocate device memory when they render: a plug-in in
+ * a host application that owns all device memory through its own pool, code
+ * running while a stream is being captured (cudaMalloc is not allowed then),
+ * or a real-time thread that must not wait on the allocator.  The whole
+ * workspace lives in one file-scope __device__ array of
+ * SSS_STATIC_ARENA_BYTES in the library, so the caller passes only the scene,
+ * the camera, the options and the output image.
+ *   scene    device parameters of one scene, n <= SSS_STATIC_MAX_COMPONENTS
+ *   cam      width * height <= SSS_STATIC_MAX_PIXELS
+ *   out_rgb  device float[3][height][width]
+ * Same computation as sss_project + sss_bin + sss_sort + sss_render_fwd on a
+ * one-job frame.  Allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library call).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current) and caches it;
+ * make that first call before any stream capture.  Every call on a device
+ * shares the one array and leaves its contents behind: calls whose work
+ * overlaps on the GPU (other streams or host threads) race, so serialise
+ * them.  The call synchronises `stream` before it returns, to report an
+ * overflow.  Errors: SSS_ERR_INVALID_ARG (null pointer, size beyond the
+ * limits, bad options), SSS_ERR_CAPACITY (the frame's workspace or its tile
+ * pairs do not fit the array), SSS_ERR_CUDA. */
+#define SSS_STATIC_ARENA_BYTES (32u << 20)
+#define SSS_STATIC_MAX_COMPONENTS 65536
+#define SSS_STATIC_MAX_PIXELS (1024 * 1024)
+int sss_render_static(const sss_params* scene, const sss_camera* cam, const sss_raster_cfg* cfg, float* out_rgb,
+                      sss_stream_t stream);
+
 /* ----------------------------------------------------------- status */
 /* Synchronises the stream, then copies the workspace control words to the
  * host: status bits, pairs needed, pairs sorted.  Any pointer may be NULL. */

@@ -92,6 +92,7 @@ _SIGS = {
     "sss_loss_l1": [c_void_p, c_void_p, c_uint32, c_void_p, c_void_p, c_void_p],
     "sss_read_status": [POINTER(sss_frame_plan), c_void_p, POINTER(c_uint32), POINTER(c_uint32),
                         POINTER(c_uint32), c_void_p],
+    "sss_render_static": [POINTER(sss_params), POINTER(sss_camera), POINTER(sss_raster_cfg), c_void_p, c_void_p],
 }
 _RESTYPES = {"sss_default_cfg": None, "sss_status_string": c_char_p}
 
@@ -207,3 +208,9 @@ def sss_read_status(plan, ws_ptr: int, stream=None):
                                                     ctypes.byref(need), ctypes.byref(done), _stream(stream)))
     return int(st.value), int(need.value), int(done.value)
 
+
+def sss_render_static(scene: sss_params, cam: sss_camera, cfg: sss_raster_cfg, out_rgb_ptr: int, stream=None):
+    """Forward render of one small frame using the library's fixed device
+    array as workspace (no allocation); synchronises the stream."""
+    _check("sss_render_static", lib().sss_render_static(ctypes.byref(scene), ctypes.byref(cam), ctypes.byref(cfg),
+                                                        c_void_p(out_rgb_ptr), _stream(stream)))
