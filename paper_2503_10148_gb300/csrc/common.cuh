@@ -166,6 +166,56 @@ __device__ __forceinline__ void rec_origin(float w, int& ox, int& oy) {
   oy = (int)(o >> 16);
 }
 
+// ------------------------------------------------------------ staging
+// Double-buffered staging of B splat records (three float4 each) into shared
+// memory by all 256 threads of a CTA.  Thread t owns the (record, float4)
+// slots q = t + 256 l, l < kL: record q % B, component q / B.  The kernels
+// software-pipeline it: while batch i is processed from one buffer, the
+// records of batch i+1 are in registers (loads in flight) and the entry
+// indices of batch i+2 are being fetched, so the gather latency is not paid
+// at the CTA barrier.
+template <int B>
+struct Stager {
+  static constexpr int kL = (3 * B + 255) / 256;
+  uint32_t e_next[kL];  // entries of the batch whose records are loaded next
+  float4 v[kL];         // records in flight
+
+  // entry ids of list positions [base, base + cnt) owned by this thread
+  __device__ __forceinline__ void fetch_entries(const uint32_t* __restrict__ vals, uint32_t base, uint32_t cnt,
+                                                uint32_t (&e)[kL]) const {
+#pragma unroll
+    for (int l = 0; l < kL; ++l) {
+      const int q = threadIdx.x + 256 * l;
+      const uint32_t r = (uint32_t)(q % B);
+      e[l] = (q < 3 * B && r < cnt) ? __ldg(vals + base + r) : 0xffffffffu;
+    }
+  }
+  __device__ __forceinline__ void load_records(const SplatRec* __restrict__ rec, const uint32_t (&e)[kL]) {
+#pragma unroll
+    for (int l = 0; l < kL; ++l) {
+      const int q = threadIdx.x + 256 * l;
+      const int comp = q / B;
+      if (q < 3 * B && e[l] != 0xffffffffu) {
+        v[l] = __ldg(reinterpret_cast<const float4*>(rec + e[l]) + comp);
+      } else {
+        // empty slot: h_max < 0 never hits
+        v[l] = comp == 1 ? make_float4(1.0f, 0.0f, -1.0f, 1.0f) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      }
+    }
+  }
+  // s: [3][B] float4 of one buffer; s_e: optional [B] entry ids
+  __device__ __forceinline__ void store(float4* s, uint32_t* s_e, const uint32_t (&e)[kL]) const {
+#pragma unroll
+    for (int l = 0; l < kL; ++l) {
+      const int q = threadIdx.x + 256 * l;
+      if (q < 3 * B) {
+        s[q] = v[l];
+        if (s_e && q < B) s_e[q] = e[l];
+      }
+    }
+  }
+};
+
 // ------------------------------------------------------------ warp helpers
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 

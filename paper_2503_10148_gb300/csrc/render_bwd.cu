@@ -23,31 +23,41 @@
 // sum_{k>=2} u^k / k (from -ln(1 - u)), a sum of positive terms; for
 // u < 1/4 the series to k = 13 is used (truncation < 1e-9 of g), above that the
 // direct difference (cancellation at most 8x).
-// A lane first sums its pixels; the warp then reduces the 10 sums with a
-// 16-slot reduce-scatter (16 shuffles instead of 10 x 5) and 10 lanes add the
-// totals to the splat's record with one vectorless RED each.
+// Records are staged as in the forward (double buffered, next batch loaded
+// while this one is processed).  A lane first sums its pixels; the warp then
+// reduces the 10 sums with a reduce-scatter (12 shuffles instead of 10 x 5)
+// and 10 lanes add the totals to the splat's record with one RED each.
 #include "common.cuh"
 
 namespace sss {
 namespace {
 
-// v[0..15] summed over the warp; lane l ends with the total of slot
-// (l >> 1) & 15 in v[0].
-__device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], unsigned lane) {
+// Sums v[0..9] over the warp with 12 shuffles: five halving rounds over lane
+// bits 4..0 in which each lane keeps a shrinking set of slots (5, then 3 or
+// 2, then 2 or 1, then 1) and sends the rest to its partner.  Returns the
+// total of one slot, *slot = its index, or -1 on lanes whose total duplicates
+// another lane's (exactly one lane per slot gets a slot index).
+__device__ __forceinline__ float warp_reduce_scatter10(const float (&v)[10], unsigned lane, int* slot) {
+  constexpr unsigned F = 0xffffffffu;
+  const bool b4 = lane & 16u, b3 = lane & 8u, b2 = lane & 4u, b1 = lane & 2u;
+  float w[5];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int h = 8 >> r;
-    const unsigned m = 16u >> r;
-    const bool upper = (lane & m) != 0;
-#pragma unroll
-    for (int i = 0; i < h; ++i) {
-      const float send = upper ? v[i] : v[i + h];
-      const float keep = upper ? v[i + h] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
-    }
-  }
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-  return v[0];
+  for (int i = 0; i < 5; ++i) w[i] = (b4 ? v[5 + i] : v[i]) + __shfl_xor_sync(F, b4 ? v[i] : v[5 + i], 16);
+  const float y0 = (b3 ? w[3] : w[0]) + __shfl_xor_sync(F, b3 ? w[0] : w[3], 8);
+  const float y1 = (b3 ? w[4] : w[1]) + __shfl_xor_sync(F, b3 ? w[1] : w[4], 8);
+  const float y2 = w[2] + __shfl_xor_sync(F, w[2], 8);  // used where b3 == 0
+  const float send0 = b3 ? (b2 ? y0 : y1) : (b2 ? y0 : y2);
+  const float keep0 = b3 ? (b2 ? y1 : y0) : (b2 ? y2 : y0);
+  const float z0 = keep0 + __shfl_xor_sync(F, send0, 4);
+  const float z1 = y1 + __shfl_xor_sync(F, y1, 4);  // used where b3 == b2 == 0
+  const bool two = !b3 && !b2;
+  const float send = two ? (b1 ? z0 : z1) : z0;
+  const float keep = two ? (b1 ? z1 : z0) : z0;
+  float f = keep + __shfl_xor_sync(F, send, 2);
+  f += __shfl_xor_sync(F, f, 1);
+  const int local = two ? (b1 ? 1 : 0) : (!b3 ? 2 : (!b2 ? 3 : 4));
+  *slot = ((lane & 1u) == 0u && (two || !b1)) ? 5 * (b4 ? 1 : 0) + local : -1;
+  return f;
 }
 
 __device__ __forceinline__ float log1p_minus_u(float u, float log_base) {
@@ -70,13 +80,13 @@ __device__ __forceinline__ float log1p_minus_u(float u, float log_base) {
 }
 
 template <int PW, int PH, int B>
-__global__ void __launch_bounds__(256) k_render_bwd(const sss_frame_plan P, void* ws,
+__global__ void __launch_bounds__(256, (PW * PH >= 4 && B >= 256) ? 2 : 3) k_render_bwd(const sss_frame_plan P, void* ws,
                                                     const float* __restrict__ dl_drgb) {
   constexpr int NPIX = PW * PH;
   constexpr int TW = 16 * PW, TH = 16 * PH;
   constexpr int NW = B / 32;
-  __shared__ float4 s_a[B], s_b[B], s_c[B];
-  __shared__ uint32_t s_e[B];
+  __shared__ float4 s_buf[2][3 * B];
+  __shared__ uint32_t s_ebuf[2][B];
   __shared__ uint32_t s_top;
 
   const uint32_t tile = blockIdx.x;
@@ -132,24 +142,32 @@ __global__ void __launch_bounds__(256) k_render_bwd(const sss_frame_plan P, void
   const float tau = cfg.tau, amax = cfg.alpha_max;
   const bool paper_nu = cfg.nu_grad_mode == 1;
 
-  // list positions are relative to range.x; pixel p has contributors in [0, last[p])
-  for (uint32_t hi = top; hi > 0;) {
-    const uint32_t lo = hi > (uint32_t)B ? hi - B : 0u;
-    const uint32_t cnt = hi - lo;
-    __syncthreads();
-    if (threadIdx.x < B) {
-      if (threadIdx.x < cnt) {
-        const uint32_t e = vals[range.x + lo + threadIdx.x];
-        const SplatRec r = rec[e];
-        s_a[threadIdx.x] = r.a;
-        s_b[threadIdx.x] = r.b;
-        s_c[threadIdx.x] = r.c;
-        s_e[threadIdx.x] = e;
-      } else {
-        s_b[threadIdx.x] = make_float4(1.0f, 0.0f, -1.0f, 1.0f);
-      }
+  // list positions are relative to range.x; pixel p has contributors in
+  // [0, last[p]).  Batches run from the back: batch i covers positions
+  // [lo_i, hi_i) with hi_0 = top, lo_i = max(hi_i - B, 0).
+  const uint32_t n_batches = (top + B - 1) / B;
+  auto lo_of = [&](uint32_t i) { return top > (i + 1) * B ? top - (i + 1) * B : 0u; };
+  auto cnt_of = [&](uint32_t i) { return top - i * B - lo_of(i); };
+  Stager<B> stg;
+  if (n_batches > 0) {
+    uint32_t e0[Stager<B>::kL];
+    stg.fetch_entries(vals, range.x + lo_of(0), cnt_of(0), e0);
+    stg.load_records(rec, e0);
+    if (n_batches > 1) stg.fetch_entries(vals, range.x + lo_of(1), cnt_of(1), stg.e_next);
+    stg.store(s_buf[0], s_ebuf[0], e0);
+  }
+  __syncthreads();
+  for (uint32_t i = 0; i < n_batches; ++i) {
+    const uint32_t lo = lo_of(i);
+    uint32_t e_after[Stager<B>::kL];
+    if (i + 1 < n_batches) {
+      stg.load_records(rec, stg.e_next);
+      if (i + 2 < n_batches) stg.fetch_entries(vals, range.x + lo_of(i + 2), cnt_of(i + 2), e_after);
     }
-    __syncthreads();
+    const float4* s_a = s_buf[i & 1];
+    const float4* s_b = s_a + B;
+    const float4* s_c = s_a + 2 * B;
+    const uint32_t* s_e = s_ebuf[i & 1];
     if (lo < warp_max) {
       unsigned mask[NW];
 #pragma unroll
@@ -173,13 +191,13 @@ __global__ void __launch_bounds__(256) k_render_bwd(const sss_frame_plan P, void
           const uint32_t pos = lo + si;
           const float4 a = s_a[si], b = s_b[si], c = s_c[si];
           const float cb2 = 2.0f * a.w, hpre = fmaf(b.z, kHPad, b.z);
-          const float nu = b.w, inv_nu = __frcp_rn(nu), o = b.y;
+          const float nu = b.w, inv_nu = __fdividef(1.0f, nu), o = b.y;
           int ox, oy;
           rec_origin(c.w, ox, oy);
           const float e_exp = fmaf(nu, -0.5f, -1.0f);  // -(nu+2)/2
-          float v[16];
+          float v[10];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+          for (int q = 0; q < 10; ++q) v[q] = 0.0f;
           bool any = false;
 #pragma unroll
           for (int p = 0; p < NPIX; ++p) {
@@ -219,14 +237,19 @@ __global__ void __launch_bounds__(256) k_render_bwd(const sss_frame_plan P, void
             v[4] = fmaf(dl_dh, dy * dy, v[4]);
           }
           if (__any_sync(0xffffffffu, any)) {
-            const float tot = warp_reduce_scatter16(v, lane);
-            const unsigned slot = (lane >> 1) & 15u;
-            if ((lane & 1u) == 0u && slot < 10u) atomicAdd(g2d + (size_t)s_e[si] * 12 + slot, tot);
+            int slot;
+            const float tot = warp_reduce_scatter10(v, lane, &slot);
+            if (slot >= 0) atomicAdd(g2d + (size_t)s_e[si] * 12 + slot, tot);
           }
         }
       }
     }
-    hi = lo;
+    if (i + 1 < n_batches) {
+      stg.store(s_buf[(i + 1) & 1], s_ebuf[(i + 1) & 1], stg.e_next);
+#pragma unroll
+      for (int l = 0; l < Stager<B>::kL; ++l) stg.e_next[l] = e_after[l];
+    }
+    __syncthreads();
   }
 }
 

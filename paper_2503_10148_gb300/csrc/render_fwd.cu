@@ -5,7 +5,8 @@
 // are laid out 2 x 4 over the tile; warp w owns an (8 PW) x (4 PH) box and
 // lane l a PW x PH block of pixels inside it.  The tile's splat list is
 // staged in shared memory B splats at a time (48-byte records gathered by
-// entry index).  Each warp then tests the B staged splats against its own
+// entry index, double buffered: the next batch is loaded while this one is
+// processed).  Each warp then tests the B staged splats against its own
 // box in parallel (one splat per lane, exact ellipse/box test) and walks
 // only the survivors, in list (= depth) order, so pairs whose ellipse misses
 // the warp's 32 PW PH pixels cost nothing.  A warp stops evaluating when all
@@ -20,7 +21,7 @@ __global__ void __launch_bounds__(256) k_render_fwd(const sss_frame_plan P, void
   constexpr int NPIX = PW * PH;
   constexpr int TW = 16 * PW, TH = 16 * PH;
   constexpr int NW = B / 32;
-  __shared__ float4 s_a[B], s_b[B], s_c[B];
+  __shared__ float4 s_buf[2][3 * B];
 
   const uint32_t tile = blockIdx.x;
   const int j = job_of_tile(P, tile);
@@ -55,72 +56,89 @@ __global__ void __launch_bounds__(256) k_render_fwd(const sss_frame_plan P, void
   const float tau = cfg.tau, amax = cfg.alpha_max, tmin = cfg.t_min;
   uint32_t n_eval = 0, n_contrib = 0;  // pair counters for the roofline
 
-  for (uint32_t b0 = range.x; b0 < range.y; b0 += B) {
-    if (__syncthreads_count(!warp_done) == 0) break;
-    const uint32_t cnt = min((uint32_t)B, range.y - b0);
-    if (threadIdx.x < B) {
-      if (threadIdx.x < cnt) {
-        const SplatRec r = rec[vals[b0 + threadIdx.x]];
-        s_a[threadIdx.x] = r.a;
-        s_b[threadIdx.x] = r.b;
-        s_c[threadIdx.x] = r.c;
-      } else {
-        s_b[threadIdx.x] = make_float4(1.0f, 0.0f, -1.0f, 1.0f);  // h_max < 0: never hits
-      }
+  const uint32_t n_list = range.y - range.x;
+  const uint32_t n_batches = (n_list + B - 1) / B;
+  Stager<B> stg;
+  if (n_batches > 0) {
+    uint32_t e0[Stager<B>::kL];
+    stg.fetch_entries(vals, range.x, min((uint32_t)B, n_list), e0);
+    stg.load_records(rec, e0);
+    if (n_batches > 1) stg.fetch_entries(vals, range.x + B, min((uint32_t)B, n_list - B), stg.e_next);
+    stg.store(s_buf[0], nullptr, e0);
+  }
+  __syncthreads();
+  for (uint32_t i = 0; i < n_batches; ++i) {
+    const uint32_t b0 = range.x + i * B;
+    // records of batch i+1 and entry ids of batch i+2 go in flight now
+    uint32_t e_after[Stager<B>::kL];
+    if (i + 1 < n_batches) {
+      stg.load_records(rec, stg.e_next);
+      if (i + 2 < n_batches) stg.fetch_entries(vals, b0 + 2 * B, min((uint32_t)B, range.y - (b0 + 2 * B)), e_after);
     }
-    __syncthreads();
-    if (warp_done) continue;
-    unsigned mask[NW];
+    const float4* s_a = s_buf[i & 1];
+    const float4* s_b = s_a + B;
+    const float4* s_c = s_a + 2 * B;
+    if (!warp_done) {
+      unsigned mask[NW];
 #pragma unroll
-    for (int k = 0; k < NW; ++k) {
-      const float4 a = s_a[k * 32 + lane], b = s_b[k * 32 + lane];
-      int ox, oy;
-      rec_origin(s_c[k * 32 + lane].w, ox, oy);
-      const bool hit = b.z >= 0.0f &&
-                       ellipse_hits_box(a.x, a.y, a.z, a.w, b.x, fmaf(b.z, 2.0f * kHPad, b.z) + 1e-3f,
-                                        (float)(bx - ox) + 0.5f, (float)(bx - ox + 8 * PW) - 0.5f,
-                                        (float)(by - oy) + 0.5f, (float)(by - oy + 4 * PH) - 0.5f);
-      mask[k] = __ballot_sync(0xffffffffu, hit);
-    }
-#pragma unroll
-    for (int k = 0; k < NW; ++k) {
-      unsigned m = mask[k];
-      while (m && !warp_done) {
-        const int bit = __ffs(m) - 1;
-        m &= m - 1;
-        const int si = k * 32 + bit;
-        const float4 a = s_a[si], b = s_b[si], c = s_c[si];
-        const float cb2 = 2.0f * a.w, hpre = fmaf(b.z, kHPad, b.z), inv_nu = __frcp_rn(b.w);
+      for (int k = 0; k < NW; ++k) {
+        const float4 a = s_a[k * 32 + lane], b = s_b[k * 32 + lane];
         int ox, oy;
-        rec_origin(c.w, ox, oy);
-        const uint32_t pos1 = b0 + si - range.x + 1;
+        rec_origin(s_c[k * 32 + lane].w, ox, oy);
+        const bool hit = b.z >= 0.0f &&
+                         ellipse_hits_box(a.x, a.y, a.z, a.w, b.x, fmaf(b.z, 2.0f * kHPad, b.z) + 1e-3f,
+                                          (float)(bx - ox) + 0.5f, (float)(bx - ox + 8 * PW) - 0.5f,
+                                          (float)(by - oy) + 0.5f, (float)(by - oy + 4 * PH) - 0.5f);
+        mask[k] = __ballot_sync(0xffffffffu, hit);
+      }
 #pragma unroll
-        for (int p = 0; p < NPIX; ++p) {
-          if (done[p]) continue;
-          const float dx = (float)(lx + p % PW - ox) + 0.5f - a.x;
-          const float dy = (float)(ly + p / PW - oy) + 0.5f - a.y;
-          PairEval r;
-          ++n_eval;
-          if (!eval_pair(dx, dy, a.z, cb2, b.x, hpre, b.y, b.w, inv_nu, tau, amax, r)) continue;
-          const float Tn = T[p] * (1.0f - r.alpha);
-          if (Tn < tmin) {
-            done[p] = true;
-            continue;
+      for (int k = 0; k < NW; ++k) {
+        unsigned m = mask[k];
+        while (m && !warp_done) {
+          const int bit = __ffs(m) - 1;
+          m &= m - 1;
+          const int si = k * 32 + bit;
+          const float4 a = s_a[si], b = s_b[si], c = s_c[si];
+          const float cb2 = 2.0f * a.w, hpre = fmaf(b.z, kHPad, b.z), inv_nu = __fdividef(1.0f, b.w);
+          int ox, oy;
+          rec_origin(c.w, ox, oy);
+          const uint32_t pos1 = b0 + si - range.x + 1;
+#pragma unroll
+          for (int p = 0; p < NPIX; ++p) {
+            if (done[p]) continue;
+            const float dx = (float)(lx + p % PW - ox) + 0.5f - a.x;
+            const float dy = (float)(ly + p / PW - oy) + 0.5f - a.y;
+            PairEval r;
+            ++n_eval;
+            if (!eval_pair(dx, dy, a.z, cb2, b.x, hpre, b.y, b.w, inv_nu, tau, amax, r)) continue;
+            const float Tn = T[p] * (1.0f - r.alpha);
+            if (Tn < tmin) {
+              done[p] = true;
+              continue;
+            }
+            const float w = r.alpha * T[p];
+            C[p][0] = fmaf(w, c.x, C[p][0]);
+            C[p][1] = fmaf(w, c.y, C[p][1]);
+            C[p][2] = fmaf(w, c.z, C[p][2]);
+            T[p] = Tn;
+            last[p] = pos1;
+            ++n_contrib;
           }
-          const float w = r.alpha * T[p];
-          C[p][0] = fmaf(w, c.x, C[p][0]);
-          C[p][1] = fmaf(w, c.y, C[p][1]);
-          C[p][2] = fmaf(w, c.z, C[p][2]);
-          T[p] = Tn;
-          last[p] = pos1;
-          ++n_contrib;
-        }
-        bool ld = true;
+          bool ld = true;
 #pragma unroll
-        for (int p = 0; p < NPIX; ++p) ld = ld && done[p];
-        warp_done = __all_sync(0xffffffffu, ld);
+          for (int p = 0; p < NPIX; ++p) ld = ld && done[p];
+          warp_done = __all_sync(0xffffffffu, ld);
+        }
       }
     }
+    if (i + 1 < n_batches) {
+      stg.store(s_buf[(i + 1) & 1], nullptr, stg.e_next);
+#pragma unroll
+      for (int l = 0; l < Stager<B>::kL; ++l) stg.e_next[l] = e_after[l];
+    }
+    // one barrier per batch: the next buffer is complete and every warp is
+    // done with this one; also the CTA-wide early exit
+    if (__syncthreads_count(!warp_done) == 0) break;
   }
 
   {
