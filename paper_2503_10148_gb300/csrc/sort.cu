@@ -15,16 +15,25 @@
 // each owning one contiguous slice of the input, so that per-pass histograms
 // are [256][blocks] and every kernel can be launched before the element count
 // is known on the host (counts are read on the device; CUDA-graph friendly).
+// A pass is reduce-then-scan: per-CTA digit histograms (upsweep), a scan of
+// every digit's row in parallel (one CTA per digit), then the scatter
+// (downsweep).  The scatter ranks a 4096-element tile in shared memory and
+// writes it out in digit order, so consecutive threads write consecutive
+// addresses of a digit's run instead of 4-byte scattered stores.  The last
+// pass of the pair sort also records every tile's [start, end) with
+// atomicMin/atomicMax of the run ends it writes (order independent).
 #include "common.cuh"
 
 namespace sss {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 8;
+constexpr int kItems = 16;
 constexpr int kTile = kThreads * kItems;  // elements per CTA iteration
 constexpr int kRadix = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr int kWarpSpan = kItems * 32;  // elements of a tile owned by one warp
+static_assert(kThreads == kRadix, "one thread per digit");
 
 __device__ __forceinline__ uint32_t load_count(const uint32_t* count_dev, uint32_t count_max) {
   return count_dev ? min(*count_dev, count_max) : count_max;
@@ -46,137 +55,226 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
+// Inclusive scan of one value per thread over a CTA of kThreads threads;
+// `total` = the sum over the CTA.  Contains two barriers (s_w is reusable on
+// return).
+__device__ __forceinline__ uint32_t block_scan_incl(uint32_t v, uint32_t* s_w, uint32_t& total) {
+  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= (unsigned)o) x += y;
+  }
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  uint32_t before = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const uint32_t s = s_w[w];
+    before += (unsigned)w < warp ? s : 0u;
+    tot += s;
+  }
+  __syncthreads();
+  total = tot;
+  return before + x;
+}
+
 // Per-CTA digit histogram of its slice -> hist[digit * nb + cta].
 __global__ void __launch_bounds__(kThreads) k_upsweep(const uint32_t* __restrict__ keys, const uint32_t* count_dev,
                                                       uint32_t count_max, int shift, uint32_t* __restrict__ hist) {
   __shared__ uint32_t sh[kRadix];
-  for (int i = threadIdx.x; i < kRadix; i += kThreads) sh[i] = 0;
+  sh[threadIdx.x] = 0;
   __syncthreads();
   uint32_t begin, end;
   slice(load_count(count_dev, count_max), gridDim.x, blockIdx.x, begin, end);
   const unsigned lane = threadIdx.x & 31;
-  for (uint32_t base = begin; base < end; base += kThreads) {
-    const uint32_t i = base + threadIdx.x;
-    const bool ok = i < end;
-    const uint32_t d = ok ? (keys[i] >> shift) & 0xffu : 0x100u;
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
-    if (ok && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&sh[d], (uint32_t)__popc(peers));
+  for (uint32_t t0 = begin; t0 < end; t0 += kTile) {
+    uint32_t d[kItems];
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+      const uint32_t i = t0 + it * kThreads + threadIdx.x;
+      d[it] = i < end ? (__ldg(keys + i) >> shift) & 0xffu : 0x100u;
+    }
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+      const unsigned peers = __match_any_sync(0xffffffffu, d[it]);
+      if (d[it] < 0x100u && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&sh[d[it]], (uint32_t)__popc(peers));
+    }
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < kRadix; d += kThreads) hist[d * gridDim.x + blockIdx.x] = sh[d];
+  hist[threadIdx.x * gridDim.x + blockIdx.x] = sh[threadIdx.x];
 }
 
-// In-place exclusive scan of n values (one CTA of 1024 threads).
-__global__ void __launch_bounds__(1024) k_scan_exclusive(uint32_t* __restrict__ data, uint32_t n,
-                                                         uint32_t* total_out) {
-  __shared__ uint32_t warp_sums[32];
-  __shared__ uint32_t carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (uint32_t base = 0; base < n; base += 1024) {
+// Exclusive scan, in place, of each row of `rows` (one CTA per row of n
+// values); the row's sum goes to totals[row].
+__global__ void __launch_bounds__(kThreads) k_scan_rows(uint32_t* __restrict__ data, uint32_t n,
+                                                        uint32_t* __restrict__ totals) {
+  __shared__ uint32_t s_w[kWarps];
+  uint32_t* row = data + (size_t)blockIdx.x * n;
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < n; base += kThreads) {
     const uint32_t i = base + threadIdx.x;
-    const uint32_t v = i < n ? data[i] : 0u;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= (unsigned)o) x += y;
-    }
-    if (lane == 31) warp_sums[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t w = warp_sums[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= (unsigned)o) w += y;
-      }
-      warp_sums[lane] = w;
-    }
-    __syncthreads();
-    const uint32_t excl = carry + (warp ? warp_sums[warp - 1] : 0u) + x - v;
-    if (i < n) data[i] = excl;
-    __syncthreads();
-    if (threadIdx.x == 1023) carry = excl + v;
-    __syncthreads();
+    const uint32_t v = i < n ? row[i] : 0u;
+    uint32_t tot;
+    const uint32_t incl = block_scan_incl(v, s_w, tot);
+    if (i < n) row[i] = carry + incl - v;
+    carry += tot;
   }
-  if (threadIdx.x == 0 && total_out) *total_out = carry;
+  if (threadIdx.x == 0 && totals) totals[blockIdx.x] = carry;
 }
 
-// Stable scatter of one digit.  Each CTA walks its slice in kTile chunks;
-// inside a chunk warp w owns elements [w*256, w*256+256) and processes them in
-// 8 rounds of 32 consecutive elements, ranking equal digits with match.any.
-// vals_in == nullptr means the identity payload (element index).
-__global__ void __launch_bounds__(kThreads) k_downsweep(const uint32_t* __restrict__ keys_in,
-                                                        const uint32_t* __restrict__ vals_in,
-                                                        uint32_t* __restrict__ keys_out,
-                                                        uint32_t* __restrict__ vals_out, const uint32_t* count_dev,
-                                                        uint32_t count_max, int shift,
-                                                        const uint32_t* __restrict__ hist_scan) {
-  __shared__ uint32_t s_off[kRadix];
-  __shared__ uint32_t s_warp[kWarps][kRadix];
+// 4-byte asynchronous global -> shared copies (no registers held while the
+// loads are in flight).
+__device__ __forceinline__ void cp_async4(uint32_t* smem, const uint32_t* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Shared memory of k_downsweep (dynamic, 73 KB: three CTAs per SM).
+struct DownsweepSmem {
+  uint32_t kin[kTile], vin[kTile];    // chunk in input order
+  uint32_t key[kTile], val[kTile];    // chunk in digit order
+  uint32_t warp_cnt[kWarps][kRadix];  // per-warp digit counters, then offsets
+  uint32_t base[kRadix];              // global position of chunk position 0 of digit d's run
+  uint32_t w[kWarps];
+};
+
+// Stable scatter of one digit.  Each CTA walks its slice in kTile chunks,
+// copied to shared memory in input order.  Ranking: warp w owns elements
+// [w*512, w*512+512) of the chunk and ranks them in 16 rounds of 32
+// consecutive elements with match.any against its own per-digit counters; an
+// exclusive scan over the warps per digit and one over the digits give every
+// element its position in the digit-ordered chunk.  Write-out: thread t takes
+// chunk positions t, t+256, ...; position i of digit d goes to
+// (CTA's next slot of d) + (i - chunk start of d), so a digit's run is
+// written by consecutive threads.  vals_in == nullptr means the identity
+// payload (element index).  With `ranges`, runs of equal keys report their
+// global ends (keys are the tile ids and this is the last pass).
+__global__ void __launch_bounds__(kThreads, 3)
+    k_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const uint32_t* count_dev,
+                uint32_t count_max, int shift, const uint32_t* __restrict__ hist_scan,
+                const uint32_t* __restrict__ totals, uint2* __restrict__ ranges) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DownsweepSmem& S = *reinterpret_cast<DownsweepSmem*>(smem_raw);
   uint32_t begin, end;
   slice(load_count(count_dev, count_max), gridDim.x, blockIdx.x, begin, end);
   if (begin >= end) return;
-  for (int d = threadIdx.x; d < kRadix; d += kThreads) s_off[d] = hist_scan[d * gridDim.x + blockIdx.x];
   const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = lanemask_lt();
+  const uint32_t dme = threadIdx.x;  // the digit this thread keeps the counters of
+  uint32_t next;                     // global position of this CTA's next element of digit dme
+  {
+    const uint32_t v = totals[dme];
+    uint32_t tot;
+    next = block_scan_incl(v, S.w, tot) - v + hist_scan[dme * gridDim.x + blockIdx.x];
+  }
   for (uint32_t t0 = begin; t0 < end; t0 += kTile) {
+    const uint32_t n_here = min(end - t0, (uint32_t)kTile);
 #pragma unroll
-    for (int k = 0; k < kRadix / 32; ++k) s_warp[warp][k * 32 + lane] = 0;
-    __syncwarp();
-    uint32_t key[kItems], val[kItems], rank[kItems], dig[kItems];
-#pragma unroll
-    for (int it = 0; it < kItems; ++it) {
-      const uint32_t i = t0 + warp * (kItems * 32) + it * 32 + lane;
-      const bool ok = i < end;
-      key[it] = ok ? keys_in[i] : 0u;
-      val[it] = ok ? (vals_in ? vals_in[i] : i) : 0u;
-      dig[it] = ok ? (key[it] >> shift) & 0xffu : 0x100u;
-      const unsigned peers = __match_any_sync(0xffffffffu, dig[it]);
-      uint32_t basec = 0;
-      if (ok) basec = s_warp[warp][dig[it]];
-      rank[it] = basec + __popc(peers & lt);
-      __syncwarp();
-      if (ok && lane == (unsigned)(__ffs(peers) - 1)) s_warp[warp][dig[it]] = basec + __popc(peers);
-      __syncwarp();
-    }
-    __syncthreads();
-    // exclusive scan over warps per digit; chunk totals
-    uint32_t tot = 0;
-    {
-      const int d = threadIdx.x;  // kThreads == kRadix
-      uint32_t run = 0;
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) {
-        const uint32_t c = s_warp[w][d];
-        s_warp[w][d] = run;
-        run += c;
-      }
-      tot = run;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int it = 0; it < kItems; ++it) {
-      if (dig[it] < 0x100u) {
-        const uint32_t pos = s_off[dig[it]] + s_warp[warp][dig[it]] + rank[it];
-        keys_out[pos] = key[it];
-        vals_out[pos] = val[it];
+    for (int j = 0; j < kItems; ++j) {
+      const uint32_t i = j * kThreads + threadIdx.x;
+      if (i < n_here) {
+        cp_async4(&S.kin[i], keys_in + t0 + i);
+        if (vals_in) cp_async4(&S.vin[i], vals_in + t0 + i);
+        else S.vin[i] = t0 + i;
       }
     }
+#pragma unroll
+    for (int k = 0; k < kRadix / 32; ++k) S.warp_cnt[warp][k * 32 + lane] = 0;
+    cp_async_wait_all();
     __syncthreads();
-    s_off[threadIdx.x] += tot;
+    const uint32_t wloc = warp * kWarpSpan;  // chunk position of this warp's first element
+    uint32_t rk[kItems];
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+      const uint32_t i = wloc + it * 32 + lane;
+      const bool ok = i < n_here;
+      const uint32_t d = ok ? (S.kin[i] >> shift) & 0xffu : 0x100u;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t c = ok ? S.warp_cnt[warp][d] : 0u;
+      rk[it] = c + __popc(peers & lt);
+      __syncwarp();
+      if (ok && lane == (unsigned)(__ffs(peers) - 1)) S.warp_cnt[warp][d] = c + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    // digit dme: exclusive scan over warps, then over digits
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = S.warp_cnt[w][dme];
+      S.warp_cnt[w][dme] = cnt;
+      cnt += c;
+    }
+    uint32_t chunk_total;
+    const uint32_t start = block_scan_incl(cnt, S.w, chunk_total) - cnt;  // barriers inside
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) S.warp_cnt[w][dme] += start;
+    S.base[dme] = next - start;
+    next += cnt;
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+      const uint32_t i = wloc + it * 32 + lane;
+      if (i < n_here) {
+        const uint32_t k = S.kin[i];
+        const uint32_t loc = S.warp_cnt[warp][(k >> shift) & 0xffu] + rk[it];
+        S.key[loc] = k;
+        S.val[loc] = S.vin[i];
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int j = 0; j < kItems; ++j) {
+      const uint32_t i = j * kThreads + threadIdx.x;
+      if (i < n_here) {
+        const uint32_t k = S.key[i];
+        const uint32_t g = S.base[(k >> shift) & 0xffu] + i;
+        keys_out[g] = k;
+        vals_out[g] = S.val[i];
+        if (ranges) {
+          if (i == 0 || S.key[i - 1] != k) atomicMin(&ranges[k].x, g);
+          if (i + 1 == n_here || S.key[i + 1] != k) atomicMax(&ranges[k].y, g + 1);
+        }
+      }
+    }
     __syncthreads();
   }
 }
 
+// Opt-in to the dynamic shared memory of k_downsweep, once per device.
+int downsweep_smem_optin() {
+  static int done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SSS_ERR_CUDA;
+  if (!done[dev]) {
+    if (cudaFuncSetAttribute(k_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(DownsweepSmem)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return SSS_ERR_CUDA;
+    }
+    done[dev] = 1;
+  }
+  return SSS_OK;
+}
+
 // Stable LSD sort of `count` (key, val) pairs over bits [0, bits), ping-pong
-// between slot 0 and slot 1; the result lands in slot (passes & 1).
+// between slot 0 and slot 1; the result lands in slot (passes & 1).  `hist`
+// holds [256][nb] counts followed by 256 digit totals.  With `ranges`, the
+// last pass records the [start, end) of every key (which must be < the ranges
+// array's length).
 int radix_sort(uint32_t* keys0, uint32_t* keys1, uint32_t* vals0, uint32_t* vals1, const uint32_t* first_vals,
                const uint32_t* first_keys, const uint32_t* count_dev, uint32_t count_max, int bits, int nb,
-               uint32_t* hist, cudaStream_t st) {
+               uint32_t* hist, uint2* ranges, cudaStream_t st) {
   const int passes = (bits + 7) / 8;
+  uint32_t* totals = hist + (size_t)kRadix * nb;
+  if (int rc = downsweep_smem_optin()) return rc;
   for (int p = 0; p < passes; ++p) {
     const int shift = 8 * p;
     const uint32_t* kin = (p == 0 && first_keys) ? first_keys : ((p & 1) ? keys1 : keys0);
@@ -184,8 +282,9 @@ int radix_sort(uint32_t* keys0, uint32_t* keys1, uint32_t* vals0, uint32_t* vals
     uint32_t* kout = (p & 1) ? keys0 : keys1;
     uint32_t* vout = (p & 1) ? vals0 : vals1;
     k_upsweep<<<nb, kThreads, 0, st>>>(kin, count_dev, count_max, shift, hist);
-    k_scan_exclusive<<<1, 1024, 0, st>>>(hist, (uint32_t)kRadix * nb, nullptr);
-    k_downsweep<<<nb, kThreads, 0, st>>>(kin, vin, kout, vout, count_dev, count_max, shift, hist);
+    k_scan_rows<<<kRadix, kThreads, 0, st>>>(hist, (uint32_t)nb, totals);
+    k_downsweep<<<nb, kThreads, sizeof(DownsweepSmem), st>>>(kin, vin, kout, vout, count_dev, count_max, shift, hist, totals,
+                                         p + 1 == passes ? ranges : nullptr);
     SSS_LAUNCH_CHECK();
   }
   return SSS_OK;
@@ -221,75 +320,79 @@ __global__ void k_finish_count(uint32_t* ctrl, uint32_t capacity) {
   if (need > capacity) ctrl[kCtrlStatus] |= SSS_STATUS_PAIR_OVERFLOW;
 }
 
-// Emits the pairs of every entry in depth order: CTA b scans its slice again,
-// starting at block_off[b], and each entry writes (global tile, entry) for the
-// tiles of its rectangle, rows in order.  Pairs at or beyond the capacity are
-// dropped (the overflow bit is set by k_finish_count).
+// Emits the pairs of every entry in depth order.  CTA b takes its slice of
+// the depth order again, starting at output position block_off[b], in chunks
+// of 256 entries: a CTA scan of the chunk's tile counts places each entry's
+// pairs, and the threads then walk the chunk's output positions k = t,
+// t+256, ... (coalesced stores, no per-entry loop): the entry is the last one
+// whose start is <= k (binary search over the 256 starts) and the tile is
+// the (k - start)-th of its rectangle, rows in order.  Pairs at or beyond the
+// capacity are dropped (the overflow bit is set by k_finish_count).
 __global__ void __launch_bounds__(kThreads) k_emit(const sss_frame_plan P, const uint32_t* __restrict__ order,
                                                    const uint32_t* __restrict__ ntiles, const uint2* __restrict__ rect,
                                                    const uint32_t* __restrict__ block_off,
                                                    uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval) {
-  __shared__ uint32_t warp_tot[kWarps];
-  __shared__ uint32_t carry;
+  __shared__ uint32_t s_start[kThreads];  // first output position of each entry of the chunk
+  __shared__ uint32_t s_t0[kThreads];     // global tile id of the rectangle's first tile
+  __shared__ uint32_t s_wx[kThreads];     // rectangle width (tiles)
+  __shared__ uint32_t s_stride[kThreads]; // tiles per row of the entry's view
+  __shared__ uint32_t s_e[kThreads];
+  __shared__ uint32_t s_w[kWarps];
   uint32_t begin, end;
   slice(P.n_entries, gridDim.x, blockIdx.x, begin, end);
-  if (threadIdx.x == 0) carry = block_off[blockIdx.x];
-  __syncthreads();
-  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t carry = block_off[blockIdx.x];
   const uint32_t cap = P.pair_capacity;
   for (uint32_t base = begin; base < end; base += kThreads) {
     const uint32_t i = base + threadIdx.x;
-    uint32_t e = 0, c = 0;
+    uint32_t e = 0, c = 0, t0 = 0, wx = 1, stride = 0;
     if (i < end) {
       e = order[i];
       c = ntiles[e];
-    }
-    uint32_t x = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= (unsigned)o) x += y;
-    }
-    if (lane == 31) warp_tot[warp] = x;
-    __syncthreads();
-    uint32_t before = carry;
-    for (unsigned w = 0; w < warp; ++w) before += warp_tot[w];
-    const uint32_t off = before + x - c;
-    if (c) {
-      const int j = job_of_entry(P, e);
-      const sss_job_desc& J = P.jobs[j];
-      const uint2 r = rect[e];
-      const uint32_t tx0 = r.x & 0xffffu, tx1 = r.x >> 16, ty0 = r.y & 0xffffu, ty1 = r.y >> 16;
-      uint32_t k = off;
-      for (uint32_t ty = ty0; ty <= ty1; ++ty) {
-        const uint32_t row = J.tile_base + ty * (uint32_t)J.tiles_x;
-        for (uint32_t tx = tx0; tx <= tx1; ++tx, ++k) {
-          if (k < cap) {
-            pkey[k] = row + tx;
-            pval[k] = e;
-          }
-        }
+      if (c) {
+        const sss_job_desc& J = P.jobs[job_of_entry(P, e)];
+        const uint2 r = rect[e];
+        const uint32_t tx0 = r.x & 0xffffu, tx1 = r.x >> 16, ty0 = r.y & 0xffffu;
+        stride = (uint32_t)J.tiles_x;
+        t0 = J.tile_base + ty0 * stride + tx0;
+        wx = tx1 - tx0 + 1;
       }
     }
+    uint32_t total;
+    const uint32_t incl = block_scan_incl(c, s_w, total);
+    s_start[threadIdx.x] = incl - c;
+    s_t0[threadIdx.x] = t0;
+    s_wx[threadIdx.x] = wx;
+    s_stride[threadIdx.x] = stride;
+    s_e[threadIdx.x] = e;
     __syncthreads();
-    if (threadIdx.x == kThreads - 1) {
-      uint32_t t = 0;
-      for (int w = 0; w < kWarps; ++w) t += warp_tot[w];
-      carry += t;
+    for (uint32_t k = threadIdx.x; k < total; k += kThreads) {
+      uint32_t j = 0;
+#pragma unroll
+      for (uint32_t step = kThreads / 2; step; step >>= 1)
+        if (s_start[j + step] <= k) j += step;
+      const uint32_t local = k - s_start[j], w = s_wx[j];
+      const uint32_t row = local / w, col = local - row * w;
+      const uint32_t g = carry + k;
+      if (g < cap) {
+        pkey[g] = s_t0[j] + row * s_stride[j] + col;
+        pval[g] = s_e[j];
+      }
     }
+    carry += total;
     __syncthreads();
   }
 }
 
-// [start, end) of every tile from the sorted tile keys.
-__global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* count_dev, uint2* __restrict__ ranges) {
-  const uint32_t n = *count_dev;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const uint32_t t = keys[i];
-    if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
-    if (i + 1 == n || keys[i + 1] != t) ranges[t].y = i + 1;
-  }
+// Tile ranges start as (~0, 0) so that the last sort pass can take the
+// minimum start and maximum end of the runs it writes ...
+__global__ void k_ranges_init(uint2* __restrict__ ranges, uint32_t n_tiles) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x)
+    ranges[t] = make_uint2(0xffffffffu, 0u);
+}
+// ... and tiles that received no pair end as (0, 0).
+__global__ void k_ranges_fix(uint2* __restrict__ ranges, uint32_t n_tiles) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x)
+    if (ranges[t].x == 0xffffffffu) ranges[t].x = 0u;
 }
 
 }  // namespace
@@ -312,11 +415,11 @@ extern "C" int sss_bin(const sss_frame_plan* plan, void* ws, sss_stream_t stream
   uint32_t* hist = ws_ptr<uint32_t>(ws, P.ws_off_hist);
   // depth digits: 4 passes over the n entries, sorted result in slot 0
   int rc = radix_sort(okey, okey + n, order, order + n, nullptr, ws_ptr<uint32_t>(ws, P.ws_off_dkey), nullptr, n,
-                      32, nb, hist, st);
+                      32, nb, hist, nullptr, st);
   if (rc != SSS_OK) return rc;
   uint32_t* block_sums = hist;  // reused: nb words
   k_count_sum<<<nb, kThreads, 0, st>>>(order, ws_ptr<uint32_t>(ws, P.ws_off_ntiles), n, block_sums);
-  k_scan_exclusive<<<1, 1024, 0, st>>>(block_sums, nb, ctrl + kCtrlPairsNeeded);
+  k_scan_rows<<<1, kThreads, 0, st>>>(block_sums, (uint32_t)nb, ctrl + kCtrlPairsNeeded);
   k_finish_count<<<1, 1, 0, st>>>(ctrl, P.pair_capacity);
   k_emit<<<nb, kThreads, 0, st>>>(P, order, ws_ptr<uint32_t>(ws, P.ws_off_ntiles), ws_ptr<uint2>(ws, P.ws_off_rect),
                                   block_sums, ws_ptr<uint32_t>(ws, P.ws_off_pkey),
@@ -331,16 +434,19 @@ extern "C" int sss_sort(const sss_frame_plan* plan, void* ws, sss_stream_t strea
   cudaStream_t st = (cudaStream_t)stream;
   uint32_t* ctrl = ws_ptr<uint32_t>(ws, P.ws_off_ctrl);
   uint2* ranges = ws_ptr<uint2>(ws, P.ws_off_ranges);
-  if (cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)P.n_tiles, st) != cudaSuccess) return SSS_ERR_CUDA;
-  if (P.n_entries == 0) return SSS_OK;
+  if (P.n_entries == 0) {
+    if (cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)P.n_tiles, st) != cudaSuccess) return SSS_ERR_CUDA;
+    return SSS_OK;
+  }
+  const unsigned rgrid = min(ceil_div(P.n_tiles, 256), 4u * kNumSMs);
+  k_ranges_init<<<rgrid, 256, 0, st>>>(ranges, P.n_tiles);
   uint32_t* pkey = ws_ptr<uint32_t>(ws, P.ws_off_pkey);
   uint32_t* pval = ws_ptr<uint32_t>(ws, P.ws_off_pval);
   const uint32_t cap = P.pair_capacity;
   int rc = radix_sort(pkey, pkey + cap, pval, pval + cap, pval, nullptr, ctrl + kCtrlPairsSorted, cap, P.tile_bits,
-                      P.sort_blocks, ws_ptr<uint32_t>(ws, P.ws_off_hist), st);
+                      P.sort_blocks, ws_ptr<uint32_t>(ws, P.ws_off_hist), ranges, st);
   if (rc != SSS_OK) return rc;
-  const uint32_t* skeys = pkey + (size_t)P.pair_slot * cap;
-  k_ranges<<<4 * kNumSMs, 256, 0, st>>>(skeys, ctrl + kCtrlPairsSorted, ranges);
+  k_ranges_fix<<<rgrid, 256, 0, st>>>(ranges, P.n_tiles);
   SSS_LAUNCH_CHECK();
   return SSS_OK;
 }
