@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--no-plain", action="store_true", help="skip the one-frame-per-view comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-serve", action="store_true", help="skip the render-server leg")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="Poisson arrival window of the server leg")
     ap.add_argument("--workload", default="clusters_1p5m_4views", choices=sorted(WORKLOADS),
                     help="smaller seeded workloads exist for profiling; the benchmark line uses the default")
     return ap.parse_args()
@@ -188,7 +190,6 @@ def stage_breakdown(ts, reps, device):
     acc = {n: 0.0 for n in names}
     for _ in range(reps):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
-        ts.loss.zero_()
         ev[0].record(st)
         fr.project(st); ev[1].record(st)
         fr.bin(st); ev[2].record(st)
@@ -257,12 +258,13 @@ def algorithmic_bytes(stage: str, ts) -> int:
     return 0
 
 
-def kernels_per_step(plan) -> int:
+def kernels_per_step(plan, form: str = "autograd") -> int:
     """Our kernel launches in one train step (memsets excluded)."""
     pair_passes = (plan.tile_bits + 7) // 8
     bin_k = 1 + 4 * 3 + 4  # init, 4 radix passes, count/scan/finish/emit
-    sort_k = pair_passes * 3 + 1
-    return 1 + bin_k + sort_k + 1 + 1 + 1 + 1 + 2
+    sort_k = pair_passes * 3 + 2  # radix passes, range init and fix-up
+    loss_k = 2 if form == "autograd" else 1  # value, then the gradient in the backward
+    return 1 + bin_k + sort_k + 1 + loss_k + 1 + 1 + 2
 
 
 def run_ours(args):
@@ -359,23 +361,59 @@ def run_ours(args):
         "config": {"workload": WORKLOAD if args.workload == "clusters_1p5m_4views" else args.workload,
                    "views": len(cams), "width": cams[0].width, "height": cams[0].height,
                    "components": scene.n, "tile": f"{cfg.tile_w}x{cfg.tile_h}", "batch": cfg.batch,
-                   "cfg_source": cfg_src, "form": "batched frame, whole step in one CUDA graph",
+                   "cfg_source": cfg_src, "form": "batched frame through torch.autograd.Function (render, L1), whole step in one CUDA graph",
                    "pairs_per_step": pairs, "pair_capacity": ts.frame.pair_capacity,
                    "l2": "inputs larger than L2 (params 360 MB, pair lists > 1 GB, images 52 MB)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": round(world * mpix / (e2e_ms * 1e-3), 2), "unit": UNIT,
                 "h2d_bytes_per_step": int(targets.numel() * 4), "d2h_bytes_per_step": 4},
-        "gpu_launches": kernels_per_step(ts.frame.plan) * args.steps,
+        "gpu_launches": kernels_per_step(ts.frame.plan, ts.form) * args.steps,
         "roofline": roof,
         "stages_ms": {k: round(v, 3) for k, v in stages.items()},
         "pairs": {"contributing": contrib, "evaluated": evaluated},
         "clocks": clock_info,
         "plain": plain,
     }
+    if not args.no_serve:
+        result["serve"] = serve_leg(device, cfg, args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
         print(json.dumps(result), flush=True)
+
+
+# ------------------------------------------------------------------ serving
+
+SERVE_WORKLOAD = ("3 resident scenes (200k, 1M, 3M components, clusters + ground distribution), Poisson "
+                  "arrivals at 200 req/s, random camera on the radius-3 sphere, resolution uniform over "
+                  "{256x256, 800x800, 1297x840, 1920x1080}; forward render per request")
+
+
+def serve_leg(device, cfg, seconds: float) -> dict:
+    """Render server (batched multi-scene frames, two arenas) against one
+    frame per request, on the same seeded requests: latency at 200 req/s,
+    then throughput with every request arriving at once."""
+    import dataclasses
+    import torch
+    from paper_2503_10148_gb300 import frame as F, inputs, server
+    scenes = [F.Scene.from_numpy(s, device) for s in inputs.serving_scenes()]
+    reqs = server.poisson_requests(len(scenes), rate=200.0, duration=seconds, seed=21)
+    budget = 16 << 30
+    out = {"workload": SERVE_WORKLOAD, "hbm_budget_gb": budget >> 30, "arrival_window_s": seconds}
+    for name, burst in (("poisson", False), ("burst", True)):
+        rs = [dataclasses.replace(r, arrival=0.0) for r in reqs] if burst else reqs
+        srv = server.RenderServer(scenes, cfg, hbm_budget_bytes=budget, device=device)
+        lat, ov = srv.serve(rs)
+        b = server.summarize(lat, rs, srv)
+        b["overflow_rerenders"] = ov
+        del srv
+        torch.cuda.empty_cache()
+        lat_p, psrv = server.serve_plain(scenes, rs, cfg, hbm_budget_bytes=budget, device=device)
+        p = server.summarize(lat_p, rs, psrv)
+        del psrv
+        torch.cuda.empty_cache()
+        out[name] = {"batched": b, "plain": p}
+    return out
 
 
 # ------------------------------------------------------------------ oracle

@@ -12,6 +12,7 @@
  *   sss_project_bwd  2D splat gradients -> parameters        SM "Backward Pass" (chain rule)
  *   sss_sghmc_step   SGHMC on mu, Adam on the rest           Sec. 3.4 Eq. (sigmoidUpdate), SM Eq. (SGHMC)
  *   sss_loss_l1      L1 image loss and its gradient          Sec. 3.4 loss (L1 term)
+ *   sss_loss_l1_grad its gradient scaled by a device dL/dloss Sec. 3.4 loss (L1 term)
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -285,11 +286,20 @@ typedef struct sss_step_params {
 int sss_sghmc_step(const sss_params* params, const sss_params* grads, float* momentum, float* adam_m,
                    float* adam_v, const sss_step_params* sp, float* xi_out, sss_stream_t stream);
 
-/* L1 term of the loss: loss_out[0] += sum |pred - target| / count and
- * dL_dpred = sign(pred - target) / count (0 where equal).  count floats.
- * loss_out is a device float the caller zeroes (or accumulates into). */
+/* L1 term of the loss (Sec. 3.4): loss_out[0] = sum |pred - target| / count
+ * (overwritten; the partial sums are added in an unspecified order) and,
+ * when dL_dpred is not NULL, dL_dpred = sign(pred - target) / count (0 where
+ * equal).  count floats; pred, target, dL_dpred device arrays, loss_out one
+ * device float. */
 int sss_loss_l1(const float* pred, const float* target, uint32_t count, float* dL_dpred, float* loss_out,
                 sss_stream_t stream);
+
+/* Gradient of the L1 term for a caller that holds dL/dloss on the device
+ * (an autograd backward): dL_dpred = dL_dloss[0] * sign(pred - target) /
+ * count, dL_dloss[0] taken as 1 when dL_dloss is NULL.  Same layout as
+ * sss_loss_l1; dL_dpred is overwritten. */
+int sss_loss_l1_grad(const float* pred, const float* target, uint32_t count, const float* dL_dloss,
+                     float* dL_dpred, sss_stream_t stream);
 
 /* -------------------------------------------- no-allocation forward */
 /* No counterpart in the paper.  A forward render of one small frame for

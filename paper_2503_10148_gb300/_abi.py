@@ -90,6 +90,7 @@ _SIGS = {
     "sss_sghmc_step": [POINTER(sss_params), POINTER(sss_params), c_void_p, c_void_p, c_void_p,
                        POINTER(sss_step_params), c_void_p, c_void_p],
     "sss_loss_l1": [c_void_p, c_void_p, c_uint32, c_void_p, c_void_p, c_void_p],
+    "sss_loss_l1_grad": [c_void_p, c_void_p, c_uint32, c_void_p, c_void_p, c_void_p],
     "sss_read_status": [POINTER(sss_frame_plan), c_void_p, POINTER(c_uint32), POINTER(c_uint32),
                         POINTER(c_uint32), c_void_p],
     "sss_render_static": [POINTER(sss_params), POINTER(sss_camera), POINTER(sss_raster_cfg), c_void_p, c_void_p],
@@ -200,6 +201,11 @@ def sss_sghmc_step(params: sss_params, grads: sss_params, momentum_ptr: int, ada
 def sss_loss_l1(pred_ptr: int, target_ptr: int, count: int, grad_ptr: int, loss_ptr: int, stream=None):
     _check("sss_loss_l1", lib().sss_loss_l1(c_void_p(pred_ptr), c_void_p(target_ptr), int(count), c_void_p(grad_ptr),
                                             c_void_p(loss_ptr), _stream(stream)))
+
+
+def sss_loss_l1_grad(pred_ptr: int, target_ptr: int, count: int, dloss_ptr: int, grad_ptr: int, stream=None):
+    _check("sss_loss_l1_grad", lib().sss_loss_l1_grad(c_void_p(pred_ptr), c_void_p(target_ptr), int(count),
+                                                      c_void_p(dloss_ptr), c_void_p(grad_ptr), _stream(stream)))
 
 
 def sss_read_status(plan, ws_ptr: int, stream=None):

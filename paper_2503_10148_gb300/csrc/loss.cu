@@ -15,7 +15,7 @@ __global__ void __launch_bounds__(256) k_loss_l1(const float* __restrict__ pred,
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
     const float d = pred[i] - target[i];
     acc += fabsf(d);
-    grad[i] = d > 0.0f ? inv_count : (d < 0.0f ? -inv_count : 0.0f);
+    if (grad) grad[i] = d > 0.0f ? inv_count : (d < 0.0f ? -inv_count : 0.0f);
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -28,16 +28,42 @@ __global__ void __launch_bounds__(256) k_loss_l1(const float* __restrict__ pred,
   }
 }
 
+// dL/dpred = dL/dloss * sign(pred - target) / count, dL/dloss read on the
+// device (1 when absent).
+__global__ void __launch_bounds__(256) k_loss_l1_grad(const float* __restrict__ pred,
+                                                      const float* __restrict__ target, uint32_t count,
+                                                      float inv_count, const float* __restrict__ dl_dloss,
+                                                      float* __restrict__ grad) {
+  const float s = dl_dloss ? *dl_dloss * inv_count : inv_count;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    const float d = pred[i] - target[i];
+    grad[i] = d > 0.0f ? s : (d < 0.0f ? -s : 0.0f);
+  }
+}
+
 }  // namespace
 }  // namespace sss
 
 extern "C" int sss_loss_l1(const float* pred, const float* target, uint32_t count, float* dL_dpred, float* loss_out,
                            sss_stream_t stream) {
-  if (!pred || !target || !dL_dpred || !loss_out) return SSS_ERR_INVALID_ARG;
+  if (!pred || !target || !loss_out) return SSS_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(loss_out, 0, sizeof(float), st) != cudaSuccess) return SSS_ERR_CUDA;
   if (count == 0) return SSS_OK;
   const unsigned blocks = std::min<unsigned>(sss::ceil_div(count, 256), 8 * sss::kNumSMs);
-  sss::k_loss_l1<<<blocks, 256, 0, (cudaStream_t)stream>>>(pred, target, count, 1.0f / (float)count, dL_dpred,
-                                                          loss_out);
+  sss::k_loss_l1<<<blocks, 256, 0, st>>>(pred, target, count, 1.0f / (float)count, dL_dpred, loss_out);
+  SSS_LAUNCH_CHECK();
+  return SSS_OK;
+}
+
+extern "C" int sss_loss_l1_grad(const float* pred, const float* target, uint32_t count, const float* dL_dloss,
+                                float* dL_dpred, sss_stream_t stream) {
+  if (!pred || !target || !dL_dpred) return SSS_ERR_INVALID_ARG;
+  if (count == 0) return SSS_OK;
+  const unsigned blocks = std::min<unsigned>(sss::ceil_div(count, 256), 8 * sss::kNumSMs);
+  sss::k_loss_l1_grad<<<blocks, 256, 0, (cudaStream_t)stream>>>(pred, target, count, 1.0f / (float)count, dL_dloss,
+                                                               dL_dpred);
   SSS_LAUNCH_CHECK();
   return SSS_OK;
 }

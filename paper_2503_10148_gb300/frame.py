@@ -114,21 +114,36 @@ class Frame:
     """One batch of (scene, camera) jobs with its plan and workspace."""
 
     def __init__(self, scenes, cams, job_scene=None, cfg: abi.sss_raster_cfg | None = None,
-                 pair_capacity: int | None = None, device="cuda"):
+                 pair_capacity: int | None = None, device="cuda", arena: torch.Tensor | None = None):
+        """``arena``: optional uint8 device buffer holding the workspace and
+        the output image (a resident buffer reused across frames); a fresh
+        one is allocated when it is missing or too small."""
         self.scenes = list(scenes)
         self.cams = list(cams)
         self.job_scene = list(job_scene) if job_scene is not None else [0] * len(self.cams)
         self.cfg = cfg if cfg is not None else abi.sss_default_cfg()
         self.device = torch.device(device)
+        self.arena = arena
         n_entries = sum(self.scenes[s].n for s in self.job_scene)
         self.pair_capacity = int(pair_capacity or max(1 << 16, 16 * n_entries))
+        self.generation = 0  # forwards run through the autograd form
         self._replan()
+
+    @staticmethod
+    def bytes_needed(plan) -> int:
+        return ((int(plan.ws_bytes) + 255) & ~255) + 12 * int(plan.n_pixels)
 
     def _replan(self):
         self.plan = abi.sss_plan_frame([s.params() for s in self.scenes], [camera_struct(c) for c in self.cams],
                                        self.job_scene, self.cfg, self.pair_capacity)
-        self.ws = torch.empty(int(self.plan.ws_bytes), dtype=torch.uint8, device=self.device)
-        self.rgb = torch.empty(3 * int(self.plan.n_pixels), dtype=torch.float32, device=self.device)
+        need = self.bytes_needed(self.plan)
+        if self.arena is not None and self.arena.numel() >= need:
+            wsb = (int(self.plan.ws_bytes) + 255) & ~255
+            self.ws = self.arena[:int(self.plan.ws_bytes)]
+            self.rgb = self.arena[wsb:wsb + 12 * int(self.plan.n_pixels)].view(torch.float32)
+        else:
+            self.ws = torch.empty(int(self.plan.ws_bytes), dtype=torch.uint8, device=self.device)
+            self.rgb = torch.empty(3 * int(self.plan.n_pixels), dtype=torch.float32, device=self.device)
 
     # ------------------------------------------------------------ steps
     @property
@@ -144,8 +159,11 @@ class Frame:
     def sort(self, stream=None):
         abi.sss_sort(self.plan, self.ws_ptr, stream)
 
-    def render_fwd(self, stream=None):
-        abi.sss_render_fwd(self.plan, self.ws_ptr, self.rgb.data_ptr(), stream)
+    def render_fwd(self, stream=None, out: torch.Tensor | None = None):
+        if out is None:
+            out = self.rgb
+        assert out.dtype == torch.float32 and out.is_contiguous() and out.numel() == 3 * int(self.plan.n_pixels)
+        abi.sss_render_fwd(self.plan, self.ws_ptr, out.data_ptr(), stream)
 
     def render_bwd(self, dl_drgb: torch.Tensor, stream=None):
         assert dl_drgb.dtype == torch.float32 and dl_drgb.is_contiguous()
@@ -159,7 +177,9 @@ class Frame:
         """(status bits, pairs needed, pairs sorted); synchronises the stream."""
         return abi.sss_read_status(self.plan, self.ws_ptr, stream)
 
-    def forward(self, stream=None, grow: bool = True):
+    def forward(self, stream=None, grow: bool = True, out: torch.Tensor | None = None):
+        """project -> bin -> sort -> render_fwd; the images go to ``out``
+        (flat float32 [3 * n_pixels]) or to the frame's own buffer."""
         self.project(stream)
         self.bin(stream)
         if grow:
@@ -170,8 +190,8 @@ class Frame:
                 self.project(stream)
                 self.bin(stream)
         self.sort(stream)
-        self.render_fwd(stream)
-        return self.rgb
+        self.render_fwd(stream, out)
+        return self.rgb if out is None else out
 
     def backward(self, dl_drgb: torch.Tensor, grads, stream=None):
         self.render_bwd(dl_drgb, stream)
@@ -183,10 +203,14 @@ class Frame:
         return self.ws[int(off):int(off) + nbytes].view(dtype)
 
     def image(self, j: int) -> torch.Tensor:
+        return self.image_of(self.rgb, j)
+
+    def image_of(self, flat: torch.Tensor, j: int) -> torch.Tensor:
+        """Job j's [3][H][W] image inside a flat [3 * n_pixels] buffer."""
         J = self.plan.jobs[j]
         H, W = J.cam.height, J.cam.width
         b = 3 * J.pix_base
-        return self.rgb[b:b + 3 * H * W].view(3, H, W)
+        return flat[b:b + 3 * H * W].view(3, H, W)
 
     def image_slices(self):
         return [self.image(j) for j in range(self.plan.n_jobs)]

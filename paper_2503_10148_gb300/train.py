@@ -6,6 +6,11 @@ dL/dC); backward render and projection backward (gradients summed over the
 views); SGHMC on the means and Adam on the rest.  Every step is a libsss
 entry point; nothing is computed in Python.
 
+Two forms of the same launches: ``form="autograd"`` (default) goes through
+the torch.autograd.Functions of ``autograd.py`` (render, l1_loss,
+torch.autograd.grad), ``form="direct"`` calls the entry points one after
+the other with buffers the step owns.
+
 ``TrainStep.capture()`` records the whole step (about 40 kernels) into one
 CUDA graph.  The number of (tile, splat) pairs is data dependent, so the
 frame is planned with a pair capacity measured on an eager step plus
@@ -19,12 +24,16 @@ from __future__ import annotations
 
 import torch
 
+from . import autograd as AG
 from . import frame as F
 
 
 class TrainStep:
     def __init__(self, scene: F.Scene, cams, targets: torch.Tensor, cfg=None, sampler: dict | None = None,
-                 headroom: float = 1.5, device="cuda"):
+                 headroom: float = 1.5, device="cuda", form: str = "autograd"):
+        if form not in ("autograd", "direct"):
+            raise ValueError(form)
+        self.form = form
         self.scene = scene
         self.cams = list(cams)
         self.device = torch.device(device)
@@ -40,6 +49,9 @@ class TrainStep:
         self.sp = F.step_params(step_counter=self.step_counter, **(sampler or {}))
         self.headroom = headroom
         self.graph = None
+        if form == "autograd":
+            self.leaves = AG.leaves(scene)
+            self.one = torch.ones((), dtype=torch.float32, device=self.device)
 
     def calibrate(self):
         """Eager forward with capacity growth, then re-plan with headroom."""
@@ -55,7 +67,14 @@ class TrainStep:
         """Enqueue one step on the current stream (no host synchronisation)."""
         st = torch.cuda.current_stream(self.device)
         fr = self.frame
-        self.loss.zero_()
+        if self.form == "autograd":
+            rgb = AG.render(fr, self.leaves, grow=False)
+            loss = AG.l1_loss(rgb, self.targets)
+            grads = torch.autograd.grad(loss, self.leaves, grad_outputs=self.one)
+            self.rgb_out, self.loss = rgb, loss
+            self.grads = F.Scene(dict(zip(F.FIELDS, grads)), self.scene.n, self.scene.sh_degree)
+            F.sghmc_step(self.scene, self.grads, self.state, self.sp, stream=st)
+            return
         fr.project(st)
         fr.bin(st)
         fr.sort(st)
@@ -66,11 +85,24 @@ class TrainStep:
         F.sghmc_step(self.scene, self.grads, self.state, self.sp, stream=st)
 
     def capture(self):
-        self.run()  # warm-up on the capture-free path (lazy module loading)
+        """Warm-up steps on a side stream (the autograd engine must not have
+        run this backward on the legacy stream before a capture: it would
+        touch that stream during the capture), then one captured step."""
+        cur = torch.cuda.current_stream(self.device)
+        side = torch.cuda.Stream(self.device)
+        side.wait_stream(cur)
+        with torch.cuda.stream(side):
+            for _ in range(2):
+                self.run()
+        cur.wait_stream(side)
         torch.cuda.synchronize(self.device)
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            self.run()
+        try:
+            with torch.cuda.graph(g):
+                self.run()
+        except BaseException:
+            torch.cuda.set_stream(cur)  # a failed capture_end leaves the capture stream current
+            raise
         self.graph = g
         return g
 
@@ -104,15 +136,14 @@ class PlainStep:
         self.total = scene.zeros_like()
         self.state = F.SamplerState(scene)
         self.dl = [torch.zeros_like(fr.rgb) for fr in self.frames]
-        self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        self.loss = torch.zeros(len(self.frames), dtype=torch.float32, device=self.device)  # per view
         self.step_counter = torch.zeros(1, dtype=torch.int64, device=self.device)
         self.sp = F.step_params(step_counter=self.step_counter, **(sampler or {}))
 
     def run(self):
-        self.loss.zero_()
-        for fr, tgt, dl, g in zip(self.frames, self.targets, self.dl, self.grads):
+        for v, (fr, tgt, dl, g) in enumerate(zip(self.frames, self.targets, self.dl, self.grads)):
             fr.forward(grow=True)
-            F.loss_l1(fr.rgb, tgt, dl, self.loss)
+            F.loss_l1(fr.rgb, tgt, dl, self.loss[v:v + 1])
             fr.backward(dl, [g])
         for f in F.FIELDS:
             self.total.t[f].copy_(torch.stack([g.t[f] for g in self.grads]).sum(0))

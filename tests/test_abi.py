@@ -150,3 +150,4 @@ def test_device_entry_points_reject_null_arguments(lib):
     assert lib.sss_render_fwd(None, None, None, None) == _abi.SSS_ERR_INVALID_ARG
     assert lib.sss_sghmc_step(None, None, None, None, None, None, None, None) == _abi.SSS_ERR_INVALID_ARG
     assert lib.sss_loss_l1(None, None, 0, None, None, None) == _abi.SSS_ERR_INVALID_ARG
+    assert lib.sss_loss_l1_grad(None, None, 0, None, None, None) == _abi.SSS_ERR_INVALID_ARG
