@@ -89,44 +89,67 @@ __device__ __forceinline__ float mufu_ex2(float x) {
 }
 
 // One (splat, pixel) evaluation shared by the forward and backward kernels so
-// that both take identical FP32 decisions.  Returns false when the pair does
-// not contribute (outside the extent or |alpha| < tau).  Fast path: two MUFU
-// ops (lg2, ex2).  For nu > kFastNuMax the exponent -(nu+2)/2 is large enough
-// that the absolute error of lg2.approx would show, so log1pf/expf are used
-// (the branch is uniform across a warp: all lanes evaluate the same splat).
+// that both take identical FP32 decisions.  Returns whether the pair
+// contributes (h within the padded extent and |alpha| >= tau); the fields of
+// r are computed either way (finite for any finite offsets, alpha already
+// clamped to [-alpha_max, alpha_max]), so callers can evaluate all their
+// pixels in straight-line code and mask.  Fast path: two MUFU ops (lg2,
+// ex2).  For nu > kFastNuMax the exponent -(nu+2)/2 is large enough that the
+// absolute error of lg2.approx would show, so eval_pair_slow uses
+// log1pf/expf; callers pick the path per splat (uniform over a warp).
 struct PairEval {
   float h, t2d, alpha, log_base;  // log_base = ln(1 + h/nu)
   bool clamped;
 };
 
-__device__ __forceinline__ bool eval_pair(float dx, float dy, float ca, float cb2, float cc, float hmax_pre,
-                                          float o, float nu, float inv_nu, float tau, float amax, PairEval& r) {
+__device__ __forceinline__ float conic_h(float dx, float dy, float ca, float cb2, float cc) {
   float t = ca * dx;
   t = fmaf(cb2, dy, t);
-  float h = fmaf(dx, t, cc * dy * dy);
-  if (!(h <= hmax_pre)) return false;
-  float e = fmaf(nu, -0.5f, -1.0f);  // -(nu + 2) / 2
-  float t2d, lb;
-  if (nu <= kFastNuMax) {
-    float base = fmaf(h, inv_nu, 1.0f);
-    float l2 = mufu_lg2(base);
-    t2d = mufu_ex2(e * l2);
-    lb = l2 * 0.69314718055994531f;
-  } else {
-    lb = log1pf(h * inv_nu);
-    t2d = expf(e * lb);
-  }
-  float alpha = o * t2d;
-  if (!(fabsf(alpha) >= tau)) return false;
-  bool cl = false;
-  if (alpha > amax) { alpha = amax; cl = true; }
-  if (alpha < -amax) { alpha = -amax; cl = true; }
+  return fmaf(dx, t, cc * dy * dy);
+}
+
+__device__ __forceinline__ bool finish_pair(float h, float t2d, float lb, float o, float hmax_pre, float tau,
+                                            float amax, PairEval& r) {
+  const float alpha = o * t2d;
+  const bool ok = (h <= hmax_pre) && (fabsf(alpha) >= tau);
   r.h = h;
   r.t2d = t2d;
-  r.alpha = alpha;
+  r.alpha = fminf(fmaxf(alpha, -amax), amax);
   r.log_base = lb;
-  r.clamped = cl;
-  return true;
+  r.clamped = fabsf(alpha) > amax;
+  return ok;
+}
+
+__device__ __forceinline__ bool eval_pair_fast(float dx, float dy, float ca, float cb2, float cc, float hmax_pre,
+                                               float o, float nu, float inv_nu, float tau, float amax,
+                                               PairEval& r) {
+  const float h = conic_h(dx, dy, ca, cb2, cc);
+  const float e = fmaf(nu, -0.5f, -1.0f);  // -(nu + 2) / 2
+  const float l2 = mufu_lg2(fmaf(h, inv_nu, 1.0f));
+  return finish_pair(h, mufu_ex2(e * l2), l2 * 0.69314718055994531f, o, hmax_pre, tau, amax, r);
+}
+
+__device__ __forceinline__ bool eval_pair_slow(float dx, float dy, float ca, float cb2, float cc, float hmax_pre,
+                                               float o, float nu, float inv_nu, float tau, float amax,
+                                               PairEval& r) {
+  const float h = conic_h(dx, dy, ca, cb2, cc);
+  const float e = fmaf(nu, -0.5f, -1.0f);
+  const float lb = log1pf(h * inv_nu);
+  return finish_pair(h, expf(e * lb), lb, o, hmax_pre, tau, amax, r);
+}
+
+__device__ __forceinline__ bool eval_pair(float dx, float dy, float ca, float cb2, float cc, float hmax_pre,
+                                          float o, float nu, float inv_nu, float tau, float amax, PairEval& r) {
+  return nu <= kFastNuMax ? eval_pair_fast(dx, dy, ca, cb2, cc, hmax_pre, o, nu, inv_nu, tau, amax, r)
+                          : eval_pair_slow(dx, dy, ca, cb2, cc, hmax_pre, o, nu, inv_nu, tau, amax, r);
+}
+
+// Offset of a pixel centre from the splat mean along one axis: fb is the
+// lane's first pixel minus the record origin (an exact small integer as a
+// float), d the pixel's index inside the lane's block.  fb + (d + 0.5) is
+// exact, so the result is rounded once, as (x + 0.5) - mean is.
+__device__ __forceinline__ float pixel_offset(float fb, int d, float mean_rel) {
+  return (fb + ((float)d + 0.5f)) - mean_rel;
 }
 
 // Conservative test: can the ellipse h <= hmax_test reach the axis-aligned box

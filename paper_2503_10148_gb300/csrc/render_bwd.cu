@@ -194,22 +194,44 @@ __global__ void __launch_bounds__(256, (PW * PH >= 4 && B >= 256) ? 2 : 3) k_ren
           const float nu = b.w, inv_nu = __fdividef(1.0f, nu), o = b.y;
           int ox, oy;
           rec_origin(c.w, ox, oy);
+          const float fbx = (float)(lx - ox), fby = (float)(ly - oy);
           const float e_exp = fmaf(nu, -0.5f, -1.0f);  // -(nu+2)/2
+          // all pixels of the lane in straight-line code, masked; nu branch
+          // uniform over the warp
+          PairEval r[NPIX];
+          bool ok[NPIX];
+          float dxs[NPIX], dys[NPIX];
+#pragma unroll
+          for (int p = 0; p < NPIX; ++p) {
+            dxs[p] = pixel_offset(fbx, p % PW, a.x);
+            dys[p] = pixel_offset(fby, p / PW, a.y);
+          }
+          if (nu <= kFastNuMax) {
+#pragma unroll
+            for (int p = 0; p < NPIX; ++p)
+              ok[p] = eval_pair_fast(dxs[p], dys[p], a.z, cb2, b.x, hpre, o, nu, inv_nu, tau, amax, r[p]);
+          } else {
+#pragma unroll
+            for (int p = 0; p < NPIX; ++p)
+              ok[p] = eval_pair_slow(dxs[p], dys[p], a.z, cb2, b.x, hpre, o, nu, inv_nu, tau, amax, r[p]);
+          }
+          // per-lane sums: rgb (v7..9), opacity (v5), nu (v6) and the
+          // q-weighted moments of the pixel offsets, q = dL/dh, from which
+          // dL/dmean and dL/dconic follow once per splat (h is quadratic in
+          // the offsets, so its gradients are linear in these moments)
           float v[10];
 #pragma unroll
           for (int q = 0; q < 10; ++q) v[q] = 0.0f;
+          float m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f, m5 = 0.0f;
           bool any = false;
 #pragma unroll
           for (int p = 0; p < NPIX; ++p) {
-            if (pos >= last[p]) continue;
-            const float dx = (float)(lx + p % PW - ox) + 0.5f - a.x;
-            const float dy = (float)(ly + p / PW - oy) + 0.5f - a.y;
-            PairEval r;
-            if (!eval_pair(dx, dy, a.z, cb2, b.x, hpre, o, nu, inv_nu, tau, amax, r)) continue;
-            any = true;
-            const float Tk = T[p] * __fdividef(1.0f, 1.0f - r.alpha);
+            const bool live = ok[p] && pos < last[p];
+            any = any || live;
+            const float alpha = r[p].alpha;
+            const float Tk = live ? T[p] * __fdividef(1.0f, 1.0f - alpha) : T[p];
             T[p] = Tk;
-            const float w = r.alpha * Tk;
+            const float w = live ? alpha * Tk : 0.0f;
             float dl_da = 0.0f;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
@@ -217,25 +239,31 @@ __global__ void __launch_bounds__(256, (PW * PH >= 4 && B >= 256) ? 2 : 3) k_ren
               const float diff = cch - Bc[p][ch];
               v[7 + ch] = fmaf(w, g[p][ch], v[7 + ch]);
               dl_da = fmaf(g[p][ch], diff, dl_da);
-              Bc[p][ch] = fmaf(r.alpha, diff, Bc[p][ch]);
+              Bc[p][ch] = live ? fmaf(alpha, diff, Bc[p][ch]) : Bc[p][ch];
             }
-            dl_da *= Tk;
-            if (r.clamped) continue;
-            v[5] = fmaf(dl_da, r.t2d, v[5]);
+            dl_da = (live && !r[p].clamped) ? dl_da * Tk : 0.0f;
+            v[5] = fmaf(dl_da, r[p].t2d, v[5]);
             const float dl_dt = dl_da * o;
-            const float inv_base = __fdividef(1.0f, fmaf(r.h, inv_nu, 1.0f));
-            const float dl_dh = dl_dt * e_exp * inv_nu * r.t2d * inv_base;
-            const float u = r.h * inv_nu * inv_base;  // x / (1 + x)
+            const float inv_base = __fdividef(1.0f, fmaf(r[p].h, inv_nu, 1.0f));
+            const float qh = dl_dt * e_exp * inv_nu * r[p].t2d * inv_base;  // dL/dh
+            const float u = r[p].h * inv_nu * inv_base;  // x / (1 + x)
             // paper form: (nu+2) x / (2 nu (1+x)) = u/2 + u/nu; exact: u/nu - g/2
             const float dnu = paper_nu ? fmaf(0.5f, u, u * inv_nu)
-                                       : fmaf(-0.5f, log1p_minus_u(u, r.log_base), u * inv_nu);
-            v[6] = fmaf(dl_dt * r.t2d, dnu, v[6]);
-            v[0] = fmaf(dl_dh, -2.0f * fmaf(a.z, dx, a.w * dy), v[0]);
-            v[1] = fmaf(dl_dh, -2.0f * fmaf(a.w, dx, b.x * dy), v[1]);
-            v[2] = fmaf(dl_dh, dx * dx, v[2]);
-            v[3] = fmaf(dl_dh, 2.0f * dx * dy, v[3]);
-            v[4] = fmaf(dl_dh, dy * dy, v[4]);
+                                       : fmaf(-0.5f, log1p_minus_u(u, r[p].log_base), u * inv_nu);
+            v[6] = fmaf(dl_dt * r[p].t2d, dnu, v[6]);
+            const float qdx = qh * dxs[p], qdy = qh * dys[p];
+            m1 += qdx;
+            m2 += qdy;
+            m3 = fmaf(qdx, dxs[p], m3);
+            m4 = fmaf(qdx, dys[p], m4);
+            m5 = fmaf(qdy, dys[p], m5);
           }
+          // dh/dmean = -2 (a dx + b dy, b dx + c dy); dh/dconic = (dx^2, 2 dx dy, dy^2)
+          v[0] = -2.0f * fmaf(a.z, m1, a.w * m2);
+          v[1] = -2.0f * fmaf(a.w, m1, b.x * m2);
+          v[2] = m3;
+          v[3] = 2.0f * m4;
+          v[4] = m5;
           if (__any_sync(0xffffffffu, any)) {
             int slot;
             const float tot = warp_reduce_scatter10(v, lane, &slot);

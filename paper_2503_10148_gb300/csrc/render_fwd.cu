@@ -102,27 +102,39 @@ __global__ void __launch_bounds__(256) k_render_fwd(const sss_frame_plan P, void
           const float cb2 = 2.0f * a.w, hpre = fmaf(b.z, kHPad, b.z), inv_nu = __fdividef(1.0f, b.w);
           int ox, oy;
           rec_origin(c.w, ox, oy);
+          const float fbx = (float)(lx - ox), fby = (float)(ly - oy);
           const uint32_t pos1 = b0 + si - range.x + 1;
+          // every pixel of the lane through the same straight-line code (no
+          // branches between pixels, so their chains interleave); the nu
+          // branch is uniform over the warp
+          PairEval r[NPIX];
+          bool ok[NPIX];
+          if (b.w <= kFastNuMax) {
+#pragma unroll
+            for (int p = 0; p < NPIX; ++p)
+              ok[p] = eval_pair_fast(pixel_offset(fbx, p % PW, a.x), pixel_offset(fby, p / PW, a.y), a.z, cb2,
+                                     b.x, hpre, b.y, b.w, inv_nu, tau, amax, r[p]);
+          } else {
+#pragma unroll
+            for (int p = 0; p < NPIX; ++p)
+              ok[p] = eval_pair(pixel_offset(fbx, p % PW, a.x), pixel_offset(fby, p / PW, a.y), a.z, cb2, b.x,
+                                hpre, b.y, b.w, inv_nu, tau, amax, r[p]);
+          }
 #pragma unroll
           for (int p = 0; p < NPIX; ++p) {
-            if (done[p]) continue;
-            const float dx = (float)(lx + p % PW - ox) + 0.5f - a.x;
-            const float dy = (float)(ly + p / PW - oy) + 0.5f - a.y;
-            PairEval r;
-            ++n_eval;
-            if (!eval_pair(dx, dy, a.z, cb2, b.x, hpre, b.y, b.w, inv_nu, tau, amax, r)) continue;
-            const float Tn = T[p] * (1.0f - r.alpha);
-            if (Tn < tmin) {
-              done[p] = true;
-              continue;
-            }
-            const float w = r.alpha * T[p];
+            n_eval += done[p] ? 0u : 1u;
+            const bool live = ok[p] && !done[p];
+            const float Tn = T[p] * (1.0f - r[p].alpha);
+            const bool term = live && Tn < tmin;  // stops before this splat
+            const bool add = live && !term;
+            const float w = add ? r[p].alpha * T[p] : 0.0f;
             C[p][0] = fmaf(w, c.x, C[p][0]);
             C[p][1] = fmaf(w, c.y, C[p][1]);
             C[p][2] = fmaf(w, c.z, C[p][2]);
-            T[p] = Tn;
-            last[p] = pos1;
-            ++n_contrib;
+            T[p] = add ? Tn : T[p];
+            last[p] = add ? pos1 : last[p];
+            done[p] = done[p] || term;
+            n_contrib += add ? 1u : 0u;
           }
           bool ld = true;
 #pragma unroll
