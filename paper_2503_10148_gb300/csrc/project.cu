@@ -5,11 +5,60 @@
 // job (view) of that scene is projected from registers.  Per (job, component)
 // entry the kernel writes the 48-byte render record, the FP32 depth key, the
 // tile count and the tile rectangle.  HBM traffic per component: 240 B read
-// (degree 3) + 64 B written per view.  The screen-space mean is evaluated in
-// FP64 and stored relative to the splat's first tile (see SplatRec).
+// (degree 3) + 64 B written per view.  The screen-space mean is evaluated to
+// about 46 bits with error-free FP32 transformations and stored relative to
+// the splat's first tile (see SplatRec).
 #include "proj_geom.cuh"
 
 namespace sss {
+
+// Unevaluated sum hi + lo of two floats (double-float arithmetic).  Error-free
+// transformations: two_sum (Knuth), two_prod with an FMA (the rounding error
+// of a*b is fma(a, b, -a*b) exactly).  On this part FP64 runs at a small
+// fraction of the FP32 rate, so the extended-precision mean is done in FP32.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ DF two_prod(float a, float b) {
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+
+// r0 m0 + r1 m1 + r2 m2 + t, compensated (Ogita, Rump and Oishi's Dot2: as
+// accurate as the sum evaluated in twice the precision, then kept as a pair).
+__device__ __forceinline__ DF dot3_plus(const float* r, const float* m, float t) {
+  DF p = two_prod(r[0], m[0]);
+  float s = p.hi, err = p.lo;
+#pragma unroll
+  for (int k = 1; k < 3; ++k) {
+    const DF q = two_prod(r[k], m[k]);
+    const DF u = two_sum(s, q.hi);
+    s = u.hi;
+    err += u.lo + q.lo;
+  }
+  const DF u = two_sum(s, t);
+  return fast_two_sum(u.hi, err + u.lo);
+}
+
+// f x / z + c for double-float x, z: a correctly rounded quotient of the
+// high parts, refined once with the exact residual.
+__device__ __forceinline__ DF screen_coord(float f, DF x, DF z, float c) {
+  const float q1 = __fdiv_rn(x.hi, z.hi);
+  const float r = fmaf(-q1, z.hi, x.hi) + (x.lo - q1 * z.lo);
+  const DF q = fast_two_sum(q1, __fdiv_rn(r, z.hi));
+  const DF a = two_prod(f, q.hi);
+  const DF s = two_sum(a.hi, c);
+  return fast_two_sum(s.hi, fmaf(f, q.lo, a.lo) + s.lo);
+}
 
 template <int DEG>
 __device__ __forceinline__ void project_component(const sss_frame_plan& P, int s, uint32_t i, void* ws) {
@@ -37,21 +86,21 @@ __device__ __forceinline__ void project_component(const sss_frame_plan& P, int s
       rect[e] = make_uint2(0u, 0u);
       continue;
     }
-    // mean2D in FP64: in FP32, fx x/z + cx at ~1000 px carries ~1e-4 px of
-    // rounding, a large relative error on (pixel - mean) near the centre
+    // mean2D to ~46 bits: in FP32, fx x/z + cx at ~1000 px carries ~1e-4 px
+    // of rounding, a large relative error on (pixel - mean) near the centre
     const float* V = J.cam.viewmat;
-    const double pxd = (double)V[0] * c.mu[0] + (double)V[1] * c.mu[1] + (double)V[2] * c.mu[2] + (double)V[3];
-    const double pyd = (double)V[4] * c.mu[0] + (double)V[5] * c.mu[1] + (double)V[6] * c.mu[2] + (double)V[7];
-    const double pzd = (double)V[8] * c.mu[0] + (double)V[9] * c.mu[1] + (double)V[10] * c.mu[2] + (double)V[11];
-    const double mxd = (double)J.cam.fx * pxd / pzd + (double)J.cam.cx;
-    const double myd = (double)J.cam.fy * pyd / pzd + (double)J.cam.cy;
+    const DF pxd = dot3_plus(V + 0, c.mu, V[3]);
+    const DF pyd = dot3_plus(V + 4, c.mu, V[7]);
+    const DF pzd = dot3_plus(V + 8, c.mu, V[11]);
+    const DF mxd = screen_coord(J.cam.fx, pxd, pzd, J.cam.cx);
+    const DF myd = screen_coord(J.cam.fy, pyd, pzd, J.cam.cy);
     // extent: |o| T2D(h) >= tau  <=>  h <= h_max (reading of the SM's truncation)
     const float hmax = v.nu * expm1f(2.0f / (v.nu + 2.0f) * logf(fabsf(v.o) / cfg.tau));
-    const double ex = sqrt((double)v.A * hmax), ey = sqrt((double)v.C * hmax);
-    const double fx0 = fmax(ceil(mxd - ex - 0.5), 0.0);
-    const double fx1 = fmin(floor(mxd + ex - 0.5), (double)(J.cam.width - 1));
-    const double fy0 = fmax(ceil(myd - ey - 0.5), 0.0);
-    const double fy1 = fmin(floor(myd + ey - 0.5), (double)(J.cam.height - 1));
+    const float ex = sqrtf(v.A * hmax), ey = sqrtf(v.C * hmax);
+    const float fx0 = fmaxf(ceilf(mxd.hi - ex - 0.5f), 0.0f);
+    const float fx1 = fminf(floorf(mxd.hi + ex - 0.5f), (float)(J.cam.width - 1));
+    const float fy0 = fmaxf(ceilf(myd.hi - ey - 0.5f), 0.0f);
+    const float fy1 = fminf(floorf(myd.hi + ey - 0.5f), (float)(J.cam.height - 1));
     uint32_t nt = 0, ox = 0, oy = 0;
     uint2 rc = make_uint2(0u, 0u);
     if (fx0 <= fx1 && fy0 <= fy1) {
@@ -78,7 +127,8 @@ __device__ __forceinline__ void project_component(const sss_frame_plan& P, int s
       rgb[ch] = fmaxf(acc, 0.0f);
     }
     SplatRec r;
-    r.a = make_float4((float)(mxd - (double)ox), (float)(myd - (double)oy), v.con[0], v.con[1]);
+    // (hi - origin) is exact for |hi - origin| < 1024 px (both on hi's grid)
+    r.a = make_float4((mxd.hi - (float)ox) + mxd.lo, (myd.hi - (float)oy) + myd.lo, v.con[0], v.con[1]);
     r.b = make_float4(v.con[2], v.o, hmax, v.nu);
     r.c = make_float4(rgb[0], rgb[1], rgb[2], __uint_as_float(ox | (oy << 16)));
     rec[e] = r;

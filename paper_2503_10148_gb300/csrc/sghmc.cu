@@ -71,13 +71,12 @@ __device__ __forceinline__ void adam(float* p, const float* g, float* m, float* 
 }
 
 template <int DEG>
-__device__ __forceinline__ void step_component(const StepArgs& a, uint32_t i) {
+__device__ __forceinline__ void step_component(const StepArgs& a, uint32_t i, const StepNow& t) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   const size_t n = (size_t)a.p.n;
   const float o = tanhf(a.p.opacity_raw[i]);
   const float gate = 1.0f / (1.0f + expf(a.k * (fabsf(o) - a.t0)));
   // three standard normals
-  const StepNow t = step_now(a);
   const uint4 w = philox4x32_10(make_uint4(i, 0u, t.lo, t.hi), a.seed_lo, a.seed_hi);
   const float s24 = 1.0f / 16777216.0f;
   const float u1 = (float)((w.x >> 8) + 1u) * s24, u2 = (float)(w.y >> 8) * s24;
@@ -140,13 +139,18 @@ __device__ __forceinline__ void step_component(const StepArgs& a, uint32_t i) {
 __global__ void k_step_advance(uint64_t* counter) { *counter += 1; }
 
 __global__ void __launch_bounds__(256) k_sghmc(const StepArgs a) {
+  // the step index and its FP64 bias corrections, once per CTA
+  __shared__ StepNow s_t;
+  if (threadIdx.x == 0) s_t = step_now(a);
+  __syncthreads();
+  const StepNow t = s_t;
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (uint32_t)a.p.n) return;
   switch (a.p.sh_degree) {
-    case 0: step_component<0>(a, i); break;
-    case 1: step_component<1>(a, i); break;
-    case 2: step_component<2>(a, i); break;
-    default: step_component<3>(a, i); break;
+    case 0: step_component<0>(a, i, t); break;
+    case 1: step_component<1>(a, i, t); break;
+    case 2: step_component<2>(a, i, t); break;
+    default: step_component<3>(a, i, t); break;
   }
 }
 
