@@ -60,14 +60,28 @@ __device__ __forceinline__ StepNow step_now(const StepArgs& a) {
   return t;
 }
 
-__device__ __forceinline__ void adam(float* p, const float* g, float* m, float* v, float lr, const StepArgs& a,
-                                     const StepNow& t) {
-  const float gg = *g;
-  const float mm = fmaf(a.beta1, *m, (1.0f - a.beta1) * gg);
-  const float vv = fmaf(a.beta2, *v, (1.0f - a.beta2) * gg * gg);
-  *m = mm;
-  *v = vv;
-  *p -= lr * (mm * t.inv_bc1) / (sqrtf(vv * t.inv_bc2) + a.adam_eps);
+// Adam on R rows (stride n) of one component: every load of the group is
+// issued before the first update, so each thread keeps 4R loads in flight.
+template <int R>
+__device__ __forceinline__ void adam_rows(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                                          float* __restrict__ v, size_t n, float lr, const StepArgs& a,
+                                          const StepNow& t) {
+  float pp[R], gg[R], mo[R], vo[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    gg[r] = __ldg(g + r * n);
+    pp[r] = p[r * n];
+    mo[r] = m[r * n];
+    vo[r] = v[r * n];
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const float mm = fmaf(a.beta1, mo[r], (1.0f - a.beta1) * gg[r]);
+    const float vv = fmaf(a.beta2, vo[r], (1.0f - a.beta2) * gg[r] * gg[r]);
+    m[r * n] = mm;
+    v[r * n] = vv;
+    p[r * n] = pp[r] - lr * (mm * t.inv_bc1) / (sqrtf(vv * t.inv_bc2) + a.adam_eps);
+  }
 }
 
 template <int DEG>
@@ -122,18 +136,17 @@ __device__ __forceinline__ void step_component(const StepArgs& a, uint32_t i, co
     a.p.mean[j] = mu;
   }
   // Adam: log_scale (rows 0-2 of m, v), quat (3-6), nu (7), opacity (8), sh (9..)
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-    adam(a.p.log_scale + c * n + i, a.g.log_scale + c * n + i, a.m + c * n + i, a.v + c * n + i, a.lr[0], a, t);
-#pragma unroll
-  for (int c = 0; c < 4; ++c)
-    adam(a.p.quat + c * n + i, a.g.quat + c * n + i, a.m + (3 + c) * n + i, a.v + (3 + c) * n + i, a.lr[1], a, t);
-  adam(a.p.nu + i, a.g.nu + i, a.m + 7 * n + i, a.v + 7 * n + i, a.lr[2], a, t);
+  adam_rows<3>(a.p.log_scale + i, a.g.log_scale + i, a.m + i, a.v + i, n, a.lr[0], a, t);
+  adam_rows<4>(a.p.quat + i, a.g.quat + i, a.m + 3 * n + i, a.v + 3 * n + i, n, a.lr[1], a, t);
+  adam_rows<1>(a.p.nu + i, a.g.nu + i, a.m + 7 * n + i, a.v + 7 * n + i, n, a.lr[2], a, t);
   a.p.nu[i] = fminf(fmaxf(a.p.nu[i], 1.0f), 1e4f);
-  adam(a.p.opacity_raw + i, a.g.opacity_raw + i, a.m + 8 * n + i, a.v + 8 * n + i, a.lr[3], a, t);
-#pragma unroll 4
-  for (int c = 0; c < 3 * K; ++c)
-    adam(a.p.sh + c * n + i, a.g.sh + c * n + i, a.m + (9 + c) * n + i, a.v + (9 + c) * n + i, a.lr[4], a, t);
+  adam_rows<1>(a.p.opacity_raw + i, a.g.opacity_raw + i, a.m + 8 * n + i, a.v + 8 * n + i, n, a.lr[3], a, t);
+  constexpr int SH_ROWS = 3 * K;
+  constexpr int CH = SH_ROWS % 8 == 0 ? 8 : (SH_ROWS % 4 == 0 ? 4 : 3);
+#pragma unroll 1
+  for (int c = 0; c < SH_ROWS; c += CH)
+    adam_rows<CH>(a.p.sh + c * n + i, a.g.sh + c * n + i, a.m + (9 + c) * n + i, a.v + (9 + c) * n + i, n, a.lr[4],
+                  a, t);
 }
 
 __global__ void k_step_advance(uint64_t* counter) { *counter += 1; }
