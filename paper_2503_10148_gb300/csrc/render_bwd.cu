@@ -79,8 +79,8 @@ __device__ __forceinline__ float log1p_minus_u(float u, float log_base) {
   return log_base - u;
 }
 
-template <int PW, int PH, int B>
-__global__ void __launch_bounds__(256, (PW * PH >= 4 && B >= 256) ? 2 : 3) k_render_bwd(const sss_frame_plan P, void* ws,
+template <int PW, int PH, int B, bool PAPER_NU>
+__global__ void __launch_bounds__(256, (PW * PH >= 4 && B >= 256) ? 2 : 4) k_render_bwd(const sss_frame_plan P, void* ws,
                                                     const float* __restrict__ dl_drgb) {
   constexpr int NPIX = PW * PH;
   constexpr int TW = 16 * PW, TH = 16 * PH;
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(256, (PW * PH >= 4 && B >= 256) ? 2 : 3) k_ren
   const float* Tf = ws_ptr<float>(ws, P.ws_off_T);
   const uint32_t* Lf = ws_ptr<uint32_t>(ws, P.ws_off_last);
   const float* gimg = dl_drgb + 3 * (size_t)J.pix_base;
-  float T[NPIX], Bc[NPIX][3], g[NPIX][3];
+  float T[NPIX], Sg[NPIX], g[NPIX][3];  // Sg = dL/dC . (colour behind)
   uint32_t last[NPIX];
   uint32_t lane_max = 0;
 #pragma unroll
@@ -123,9 +123,7 @@ __global__ void __launch_bounds__(256, (PW * PH >= 4 && B >= 256) ? 2 : 3) k_ren
       last[p] = 0u;
       g[p][0] = g[p][1] = g[p][2] = 0.0f;
     }
-    Bc[p][0] = cfg.bg[0];
-    Bc[p][1] = cfg.bg[1];
-    Bc[p][2] = cfg.bg[2];
+    Sg[p] = fmaf(g[p][0], cfg.bg[0], fmaf(g[p][1], cfg.bg[1], g[p][2] * cfg.bg[2]));
     lane_max = max(lane_max, last[p]);
   }
   const uint32_t warp_max = __reduce_max_sync(0xffffffffu, lane_max);
@@ -140,7 +138,6 @@ __global__ void __launch_bounds__(256, (PW * PH >= 4 && B >= 256) ? 2 : 3) k_ren
   const SplatRec* rec = ws_ptr<SplatRec>(ws, P.ws_off_rec);
   float* g2d = ws_ptr<float>(ws, P.ws_off_grad2d);
   const float tau = cfg.tau, amax = cfg.alpha_max;
-  const bool paper_nu = cfg.nu_grad_mode == 1;
 
   // list positions are relative to range.x; pixel p has contributors in
   // [0, last[p]).  Batches run from the back: batch i covers positions
@@ -195,7 +192,7 @@ __global__ void __launch_bounds__(256, (PW * PH >= 4 && B >= 256) ? 2 : 3) k_ren
           int ox, oy;
           rec_origin(c.w, ox, oy);
           const float fbx = (float)(lx - ox), fby = (float)(ly - oy);
-          const float e_exp = fmaf(nu, -0.5f, -1.0f);  // -(nu+2)/2
+          const float e_over_nu = fmaf(nu, -0.5f, -1.0f) * inv_nu;  // -(nu+2)/(2 nu)
           // all pixels of the lane in straight-line code, masked; nu branch
           // uniform over the warp
           PairEval r[NPIX];
@@ -232,23 +229,22 @@ __global__ void __launch_bounds__(256, (PW * PH >= 4 && B >= 256) ? 2 : 3) k_ren
             const float Tk = live ? T[p] * __fdividef(1.0f, 1.0f - alpha) : T[p];
             T[p] = Tk;
             const float w = live ? alpha * Tk : 0.0f;
-            float dl_da = 0.0f;
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-              const float cch = ch == 0 ? c.x : (ch == 1 ? c.y : c.z);
-              const float diff = cch - Bc[p][ch];
-              v[7 + ch] = fmaf(w, g[p][ch], v[7 + ch]);
-              dl_da = fmaf(g[p][ch], diff, dl_da);
-              Bc[p][ch] = live ? fmaf(alpha, diff, Bc[p][ch]) : Bc[p][ch];
-            }
-            dl_da = (live && !r[p].clamped) ? dl_da * Tk : 0.0f;
+            v[7] = fmaf(w, g[p][0], v[7]);
+            v[8] = fmaf(w, g[p][1], v[8]);
+            v[9] = fmaf(w, g[p][2], v[9]);
+            // dL/dalpha = T_k dL/dC . (rgb - B) with B the colour behind; only
+            // its projection on dL/dC is needed: Sg = dL/dC . B, and
+            // B <- alpha rgb + (1 - alpha) B gives Sg <- Sg + alpha (g.rgb - Sg)
+            const float gdiff = fmaf(g[p][0], c.x, fmaf(g[p][1], c.y, g[p][2] * c.z)) - Sg[p];
+            Sg[p] = live ? fmaf(alpha, gdiff, Sg[p]) : Sg[p];
+            const float dl_da = (live && !r[p].clamped) ? gdiff * Tk : 0.0f;
             v[5] = fmaf(dl_da, r[p].t2d, v[5]);
             const float dl_dt = dl_da * o;
             const float inv_base = __fdividef(1.0f, fmaf(r[p].h, inv_nu, 1.0f));
-            const float qh = dl_dt * e_exp * inv_nu * r[p].t2d * inv_base;  // dL/dh
+            const float qh = dl_dt * e_over_nu * r[p].t2d * inv_base;  // dL/dh
             const float u = r[p].h * inv_nu * inv_base;  // x / (1 + x)
             // paper form: (nu+2) x / (2 nu (1+x)) = u/2 + u/nu; exact: u/nu - g/2
-            const float dnu = paper_nu ? fmaf(0.5f, u, u * inv_nu)
+            const float dnu = PAPER_NU ? fmaf(0.5f, u, u * inv_nu)
                                        : fmaf(-0.5f, log1p_minus_u(u, r[p].log_base), u * inv_nu);
             v[6] = fmaf(dl_dt * r[p].t2d, dnu, v[6]);
             const float qdx = qh * dxs[p], qdy = qh * dys[p];
@@ -281,18 +277,23 @@ __global__ void __launch_bounds__(256, (PW * PH >= 4 && B >= 256) ? 2 : 3) k_ren
   }
 }
 
-template <int PW, int PH>
+template <int PW, int PH, bool PAPER_NU>
 int launch_batch(const sss_frame_plan& P, void* ws, const float* g, cudaStream_t st) {
   const unsigned grid = P.n_tiles;
   switch (P.cfg.batch) {
-    case 32: k_render_bwd<PW, PH, 32><<<grid, 256, 0, st>>>(P, ws, g); break;
-    case 64: k_render_bwd<PW, PH, 64><<<grid, 256, 0, st>>>(P, ws, g); break;
-    case 128: k_render_bwd<PW, PH, 128><<<grid, 256, 0, st>>>(P, ws, g); break;
-    case 256: k_render_bwd<PW, PH, 256><<<grid, 256, 0, st>>>(P, ws, g); break;
+    case 32: k_render_bwd<PW, PH, 32, PAPER_NU><<<grid, 256, 0, st>>>(P, ws, g); break;
+    case 64: k_render_bwd<PW, PH, 64, PAPER_NU><<<grid, 256, 0, st>>>(P, ws, g); break;
+    case 128: k_render_bwd<PW, PH, 128, PAPER_NU><<<grid, 256, 0, st>>>(P, ws, g); break;
+    case 256: k_render_bwd<PW, PH, 256, PAPER_NU><<<grid, 256, 0, st>>>(P, ws, g); break;
     default: return SSS_ERR_UNSUPPORTED;
   }
   SSS_LAUNCH_CHECK();
   return SSS_OK;
+}
+
+template <int PW, int PH>
+int launch_tile(const sss_frame_plan& P, void* ws, const float* g, cudaStream_t st) {
+  return P.cfg.nu_grad_mode == 1 ? launch_batch<PW, PH, true>(P, ws, g, st) : launch_batch<PW, PH, false>(P, ws, g, st);
 }
 
 }  // namespace
@@ -305,9 +306,9 @@ extern "C" int sss_render_bwd(const sss_frame_plan* plan, void* ws, const float*
   if (cudaMemsetAsync(sss::ws_ptr<float>(ws, P.ws_off_grad2d), 0, 48 * (size_t)P.n_entries, st) != cudaSuccess)
     return SSS_ERR_CUDA;
   const int pw = P.cfg.tile_w / 16, ph = P.cfg.tile_h / 16;
-  if (pw == 1 && ph == 1) return sss::launch_batch<1, 1>(P, ws, dL_drgb, st);
-  if (pw == 2 && ph == 1) return sss::launch_batch<2, 1>(P, ws, dL_drgb, st);
-  if (pw == 1 && ph == 2) return sss::launch_batch<1, 2>(P, ws, dL_drgb, st);
-  if (pw == 2 && ph == 2) return sss::launch_batch<2, 2>(P, ws, dL_drgb, st);
+  if (pw == 1 && ph == 1) return sss::launch_tile<1, 1>(P, ws, dL_drgb, st);
+  if (pw == 2 && ph == 1) return sss::launch_tile<2, 1>(P, ws, dL_drgb, st);
+  if (pw == 1 && ph == 2) return sss::launch_tile<1, 2>(P, ws, dL_drgb, st);
+  if (pw == 2 && ph == 2) return sss::launch_tile<2, 2>(P, ws, dL_drgb, st);
   return SSS_ERR_UNSUPPORTED;
 }
