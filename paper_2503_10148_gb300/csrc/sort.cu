@@ -55,6 +55,21 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
+// Lanes of the warp whose 8-bit digit equals this lane's, among the lanes
+// in `valid` (a match.any built from eight ballots: two lanes match when
+// they agree on every bit).  Ballots are plain vote instructions, where
+// match.any goes through the MIO pipe and its latency dominated the passes.
+__device__ __forceinline__ unsigned digit_peers(uint32_t d, unsigned valid) {
+  unsigned peers = valid;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const unsigned m = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? m : ~m;
+  }
+  return peers;
+}
+
 // Inclusive scan of one value per thread over a CTA of kThreads threads;
 // `total` = the sum over the CTA.  Contains two barriers (s_w is reusable on
 // return).
@@ -80,30 +95,39 @@ __device__ __forceinline__ uint32_t block_scan_incl(uint32_t v, uint32_t* s_w, u
   return before + x;
 }
 
-// Per-CTA digit histogram of its slice -> hist[digit * nb + cta].
+// Per-CTA digit histogram of its slice -> hist[digit * nb + cta].  Each warp
+// counts into its own sub-histogram (the leader of each group of equal
+// digits adds the group's size: distinct addresses, no atomics), and the
+// eight are summed at the end.
 __global__ void __launch_bounds__(kThreads) k_upsweep(const uint32_t* __restrict__ keys, const uint32_t* count_dev,
                                                       uint32_t count_max, int shift, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t sh[kRadix];
-  sh[threadIdx.x] = 0;
+  __shared__ uint32_t sh[kWarps][kRadix];
+  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) sh[w][threadIdx.x] = 0;
   __syncthreads();
   uint32_t begin, end;
   slice(load_count(count_dev, count_max), gridDim.x, blockIdx.x, begin, end);
-  const unsigned lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
   for (uint32_t t0 = begin; t0 < end; t0 += kTile) {
     uint32_t d[kItems];
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
       const uint32_t i = t0 + it * kThreads + threadIdx.x;
-      d[it] = i < end ? (__ldg(keys + i) >> shift) & 0xffu : 0x100u;
+      d[it] = i < end ? (__ldg(keys + i) >> shift) & 0xffu : 0u;
     }
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
-      const unsigned peers = __match_any_sync(0xffffffffu, d[it]);
-      if (d[it] < 0x100u && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&sh[d[it]], (uint32_t)__popc(peers));
+      const bool ok = t0 + it * kThreads + threadIdx.x < end;
+      const unsigned peers = digit_peers(d[it], __ballot_sync(0xffffffffu, ok));
+      if (ok && (peers & lt) == 0u) sh[warp][d[it]] += (uint32_t)__popc(peers);
     }
   }
   __syncthreads();
-  hist[threadIdx.x * gridDim.x + blockIdx.x] = sh[threadIdx.x];
+  uint32_t tot = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) tot += sh[w][threadIdx.x];
+  hist[threadIdx.x * gridDim.x + blockIdx.x] = tot;
 }
 
 // Exclusive scan, in place, of each row of `rows` (one CTA per row of n
@@ -195,12 +219,12 @@ __global__ void __launch_bounds__(kThreads, 3)
     for (int it = 0; it < kItems; ++it) {
       const uint32_t i = wloc + it * 32 + lane;
       const bool ok = i < n_here;
-      const uint32_t d = ok ? (S.kin[i] >> shift) & 0xffu : 0x100u;
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t d = ok ? (S.kin[i] >> shift) & 0xffu : 0u;
+      const unsigned peers = digit_peers(d, __ballot_sync(0xffffffffu, ok));
       const uint32_t c = ok ? S.warp_cnt[warp][d] : 0u;
       rk[it] = c + __popc(peers & lt);
       __syncwarp();
-      if (ok && lane == (unsigned)(__ffs(peers) - 1)) S.warp_cnt[warp][d] = c + __popc(peers);
+      if (ok && (peers & lt) == 0u) S.warp_cnt[warp][d] = c + __popc(peers);
       __syncwarp();
     }
     __syncthreads();
