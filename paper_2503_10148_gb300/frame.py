@@ -127,6 +127,10 @@ class Frame:
         n_entries = sum(self.scenes[s].n for s in self.job_scene)
         self.pair_capacity = int(pair_capacity or max(1 << 16, 16 * n_entries))
         self.generation = 0  # forwards run through the autograd form
+        # optional {"render_fwd" | "render_bwd": (start, end)} CUDA events
+        # recorded around those launches (also inside a captured graph when
+        # the events are external), for kernel timing
+        self.timing = None
         self._replan()
 
     @staticmethod
@@ -159,16 +163,25 @@ class Frame:
     def sort(self, stream=None):
         abi.sss_sort(self.plan, self.ws_ptr, stream)
 
+    def _mark(self, name: str, i: int, stream):
+        if self.timing and name in self.timing:
+            ev = self.timing[name][i]
+            ev.record(stream) if stream is not None else ev.record()
+
     def render_fwd(self, stream=None, out: torch.Tensor | None = None):
         if out is None:
             out = self.rgb
         assert out.dtype == torch.float32 and out.is_contiguous() and out.numel() == 3 * int(self.plan.n_pixels)
+        self._mark("render_fwd", 0, stream)
         abi.sss_render_fwd(self.plan, self.ws_ptr, out.data_ptr(), stream)
+        self._mark("render_fwd", 1, stream)
 
     def render_bwd(self, dl_drgb: torch.Tensor, stream=None):
         assert dl_drgb.dtype == torch.float32 and dl_drgb.is_contiguous()
         assert dl_drgb.numel() == self.rgb.numel()
+        self._mark("render_bwd", 0, stream)
         abi.sss_render_bwd(self.plan, self.ws_ptr, dl_drgb.data_ptr(), stream)
+        self._mark("render_bwd", 1, stream)
 
     def project_bwd(self, grads, stream=None):
         abi.sss_project_bwd(self.plan, self.ws_ptr, [g.params() for g in grads], stream)

@@ -84,6 +84,23 @@ class TrainStep:
         fr.project_bwd([self.grads], st)
         F.sghmc_step(self.scene, self.grads, self.state, self.sp, stream=st)
 
+    def time_kernels(self, names=("render_fwd", "render_bwd")) -> bool:
+        """Record CUDA events around these launches in every later step,
+        captured ones included (external events become record nodes of the
+        graph).  Returns False when this PyTorch has no external events."""
+        try:
+            self.frame.timing = {n: (torch.cuda.Event(enable_timing=True, external=True),
+                                     torch.cuda.Event(enable_timing=True, external=True)) for n in names}
+        except TypeError:
+            self.frame.timing = None
+            return False
+        return True
+
+    def kernel_ms(self, name: str) -> float:
+        """Duration of the named launch in the last completed step."""
+        e0, e1 = self.frame.timing[name]
+        return e0.elapsed_time(e1)
+
     def capture(self):
         """Warm-up steps on a side stream (the autograd engine must not have
         run this backward on the legacy stream before a capture: it would
