@@ -13,6 +13,9 @@
  *   sss_sghmc_step   SGHMC on mu, Adam on the rest           Sec. 3.4 Eq. (sigmoidUpdate), SM Eq. (SGHMC)
  *   sss_loss_l1      L1 image loss and its gradient          Sec. 3.4 loss (L1 term)
  *   sss_loss_l1_grad its gradient scaled by a device dL/dloss Sec. 3.4 loss (L1 term)
+ *   sss_loss_image   L1 + D-SSIM over a frame's images      Sec. 3.4 loss
+ *   sss_loss_image_grad  its gradient                       Sec. 3.4 loss
+ *   sss_regularizers opacity and scale regularisers         Sec. 3.4 loss
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -266,6 +269,11 @@ int sss_project_bwd(const sss_frame_plan* plan, void* ws, const sss_params* grad
  *   burn-in: mu' = mu - eps^2 G + g eps sqrt(2 eps C) Sigma xi (no friction).
  * Adam (bias-corrected, t = step + 1) on log_scale, quat, nu, opacity_raw,
  * sh with lr[0..4]; nu limited to [1, 1e4] afterwards.
+ * The regularisers of the loss (Sec. 3.4) enter here, their gradients being
+ * closed forms of the parameters: Adam sees G + reg_opacity sign(o)(1 - o^2)
+ * for opacity_raw (d/draw of reg_opacity |o|) and G + reg_scale exp(s_j) for
+ * log_scale_j (d/ds_j of reg_scale sqrt(lambda_j), sqrt(lambda_j) being the
+ * scale exp(s_j)); zero weights leave the step unchanged.
  *   momentum   device float[3][n]
  *   adam_m/v   device float[(9 + 3K)][n]: rows log_scale(3), quat(4), nu,
  *              opacity_raw, sh(3K)
@@ -281,6 +289,8 @@ typedef struct sss_step_params {
                              incremented by one after the update, so a
                              graph-replayed step draws fresh noise and
                              bias-corrects with the right t */
+  float reg_opacity;      /* eps_o of the loss, >= 0 */
+  float reg_scale;        /* eps_Sigma of the loss, >= 0 */
 } sss_step_params;
 
 int sss_sghmc_step(const sss_params* params, const sss_params* grads, float* momentum, float* adam_m,
@@ -300,6 +310,41 @@ int sss_loss_l1(const float* pred, const float* target, uint32_t count, float* d
  * sss_loss_l1; dL_dpred is overwritten. */
 int sss_loss_l1_grad(const float* pred, const float* target, uint32_t count, const float* dL_dloss,
                      float* dL_dpred, sss_stream_t stream);
+
+/* Image loss of Sec. 3.4 over every image of a frame (NEXT-1):
+ *   L = (1 - eps_dssim) L1 + eps_dssim (1 - SSIM),
+ * L1 and SSIM both averaged over all pixels and channels of all jobs.  SSIM
+ * as in 3DGS (the loss the paper cites): 11 x 11 Gaussian window with sigma
+ * 1.5 (weights normalised to 1), zero padding outside each image,
+ * C1 = 0.01^2, C2 = 0.03^2; windows never cross images.
+ *   pred, target  device float[3 * n_pixels], the layout of sss_render_fwd's
+ *                 out_rgb for this plan
+ *   loss_out      device float[3]: L, L1, 1 - SSIM (overwritten)
+ *   scratch       device buffer of sss_loss_image_scratch_bytes(plan)
+ *                 bytes, 16-byte aligned: receives the per-pixel SSIM
+ *                 partials that sss_loss_image_grad needs.
+ * Errors: SSS_ERR_INVALID_ARG for NULL pointers, a misaligned scratch or
+ * eps_dssim outside [0, 1]. */
+size_t sss_loss_image_scratch_bytes(const sss_frame_plan* plan);
+int sss_loss_image(const sss_frame_plan* plan, const float* pred, const float* target, float eps_dssim,
+                   float* loss_out, void* scratch, sss_stream_t stream);
+
+/* dL/dpred of sss_loss_image, scaled by dL_dloss[0] (device float; 1 when
+ * NULL): (1 - eps) sign(x - y) / count - eps (w*a + 2 x (w*b) + y (w*c)) /
+ * count, where a, b, c are the SSIM partials the value call left in
+ * `scratch` (same plan, pred and target) and w* the windowed sum.  dL_dpred
+ * (overwritten) has the layout of pred. */
+int sss_loss_image_grad(const sss_frame_plan* plan, const float* pred, const float* target, float eps_dssim,
+                        const float* dL_dloss, const void* scratch, float* dL_dpred, sss_stream_t stream);
+
+/* Value of the regularisers of Sec. 3.4 for one scene:
+ *   loss_out[0] = reg_opacity sum_i |tanh(opacity_raw_i)|
+ *               + reg_scale sum_i sum_j exp(log_scale_ij)
+ * (sqrt(lambda_ij) of Sigma_i = R S S^T R^T is the scale exp(log_scale_ij)).
+ * loss_out: one device float, overwritten.  Their gradients are added by
+ * sss_sghmc_step (reg_opacity, reg_scale of sss_step_params). */
+int sss_regularizers(const sss_params* params, float reg_opacity, float reg_scale, float* loss_out,
+                     sss_stream_t stream);
 
 /* -------------------------------------------- no-allocation forward */
 /* No counterpart in the paper.  A forward render of one small frame for

@@ -63,7 +63,8 @@ class sss_frame_plan(Structure):
 class sss_step_params(Structure):
     _fields_ = [("eps", c_float), ("C", c_float), ("k", c_float), ("t0", c_float), ("burn_in", c_int32),
                 ("seed", c_uint64), ("step", c_uint64), ("lr", c_float * 5), ("beta1", c_float),
-                ("beta2", c_float), ("adam_eps", c_float), ("step_counter", c_void_p)]
+                ("beta2", c_float), ("adam_eps", c_float), ("step_counter", c_void_p), ("reg_opacity", c_float),
+                ("reg_scale", c_float)]
 
 
 class SSSError(RuntimeError):
@@ -91,11 +92,16 @@ _SIGS = {
                        POINTER(sss_step_params), c_void_p, c_void_p],
     "sss_loss_l1": [c_void_p, c_void_p, c_uint32, c_void_p, c_void_p, c_void_p],
     "sss_loss_l1_grad": [c_void_p, c_void_p, c_uint32, c_void_p, c_void_p, c_void_p],
+    "sss_loss_image": [POINTER(sss_frame_plan), c_void_p, c_void_p, c_float, c_void_p, c_void_p, c_void_p],
+    "sss_loss_image_grad": [POINTER(sss_frame_plan), c_void_p, c_void_p, c_float, c_void_p, c_void_p, c_void_p,
+                            c_void_p],
+    "sss_regularizers": [POINTER(sss_params), c_float, c_float, c_void_p, c_void_p],
     "sss_read_status": [POINTER(sss_frame_plan), c_void_p, POINTER(c_uint32), POINTER(c_uint32),
                         POINTER(c_uint32), c_void_p],
     "sss_render_static": [POINTER(sss_params), POINTER(sss_camera), POINTER(sss_raster_cfg), c_void_p, c_void_p],
 }
-_RESTYPES = {"sss_default_cfg": None, "sss_status_string": c_char_p}
+_SIGS["sss_loss_image_scratch_bytes"] = [POINTER(sss_frame_plan)]
+_RESTYPES = {"sss_default_cfg": None, "sss_status_string": c_char_p, "sss_loss_image_scratch_bytes": c_size_t}
 
 
 def lib_path() -> str:
@@ -206,6 +212,30 @@ def sss_loss_l1(pred_ptr: int, target_ptr: int, count: int, grad_ptr: int, loss_
 def sss_loss_l1_grad(pred_ptr: int, target_ptr: int, count: int, dloss_ptr: int, grad_ptr: int, stream=None):
     _check("sss_loss_l1_grad", lib().sss_loss_l1_grad(c_void_p(pred_ptr), c_void_p(target_ptr), int(count),
                                                       c_void_p(dloss_ptr), c_void_p(grad_ptr), _stream(stream)))
+
+
+def sss_loss_image_scratch_bytes(plan) -> int:
+    return int(lib().sss_loss_image_scratch_bytes(ctypes.byref(plan)))
+
+
+def sss_loss_image(plan, pred_ptr: int, target_ptr: int, eps_dssim: float, loss_ptr: int, scratch_ptr: int,
+                   stream=None):
+    _check("sss_loss_image", lib().sss_loss_image(ctypes.byref(plan), c_void_p(pred_ptr), c_void_p(target_ptr),
+                                                  float(eps_dssim), c_void_p(loss_ptr), c_void_p(scratch_ptr),
+                                                  _stream(stream)))
+
+
+def sss_loss_image_grad(plan, pred_ptr: int, target_ptr: int, eps_dssim: float, dloss_ptr: int, scratch_ptr: int,
+                        grad_ptr: int, stream=None):
+    _check("sss_loss_image_grad", lib().sss_loss_image_grad(ctypes.byref(plan), c_void_p(pred_ptr),
+                                                            c_void_p(target_ptr), float(eps_dssim),
+                                                            c_void_p(dloss_ptr or None), c_void_p(scratch_ptr),
+                                                            c_void_p(grad_ptr), _stream(stream)))
+
+
+def sss_regularizers(params: sss_params, reg_opacity: float, reg_scale: float, loss_ptr: int, stream=None):
+    _check("sss_regularizers", lib().sss_regularizers(ctypes.byref(params), float(reg_opacity), float(reg_scale),
+                                                      c_void_p(loss_ptr), _stream(stream)))
 
 
 def sss_read_status(plan, ws_ptr: int, stream=None):

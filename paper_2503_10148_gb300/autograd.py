@@ -1,8 +1,8 @@
-"""The rasterizer and the L1 loss as torch.autograd.Functions.
+"""The rasterizer and the image losses as torch.autograd.Functions.
 
     leaves = autograd.leaves(scene)                # six tensors, requires_grad
     images = autograd.render(frame, leaves)        # flat [3 * n_pixels]
-    loss = autograd.l1_loss(images, target)
+    loss = autograd.l1_loss(images, target)        # or image_loss(frame, ...)
     grads = torch.autograd.grad(loss, leaves)      # or loss.backward()
 
 ``frame`` is a Frame built on the scenes whose parameter tensors are passed
@@ -95,6 +95,39 @@ class L1LossFunction(torch.autograd.Function):
         out = torch.empty_like(pred)
         abi.sss_loss_l1_grad(pred.data_ptr(), target.data_ptr(), pred.numel(), g.data_ptr(), out.data_ptr(), st)
         return out, None
+
+
+class ImageLossFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, frame: F.Frame, eps_dssim: float, pred, target):
+        n = 3 * int(frame.plan.n_pixels)
+        if pred.dtype != torch.float32 or target.dtype != torch.float32 or pred.numel() != n or target.numel() != n:
+            raise ValueError("image_loss takes float32 images in the frame's layout")
+        if not pred.is_contiguous() or not target.is_contiguous():
+            raise ValueError("image_loss takes contiguous tensors")
+        st = torch.cuda.current_stream(frame.device)
+        scratch = F.loss_image_scratch(frame)
+        out = torch.empty(3, dtype=torch.float32, device=frame.device)
+        F.loss_image(frame, pred, target, eps_dssim, out, scratch, st)
+        frame.loss_parts = out  # [L, L1, 1 - SSIM] of the last evaluation
+        ctx.frame, ctx.eps, ctx.scratch = frame, eps_dssim, scratch
+        ctx.save_for_backward(pred, target)
+        return out[0]
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        pred, target = ctx.saved_tensors
+        g = grad_loss.float().contiguous()
+        st = torch.cuda.current_stream(pred.device)
+        grad = torch.empty_like(pred)
+        F.loss_image_grad(ctx.frame, pred, target, ctx.eps, ctx.scratch, grad, g, st)
+        return None, None, grad, None
+
+
+def image_loss(frame: F.Frame, pred: torch.Tensor, target: torch.Tensor, eps_dssim: float = 0.2):
+    """(1 - eps) L1 + eps (1 - SSIM) over the frame's images (Sec. 3.4) as a
+    0-d tensor; ``frame.loss_parts`` then holds [L, L1, 1 - SSIM]."""
+    return ImageLossFunction.apply(frame, eps_dssim, pred, target)
 
 
 def render(frame: F.Frame, tensors, grow: bool = True) -> torch.Tensor:

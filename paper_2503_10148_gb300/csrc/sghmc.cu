@@ -41,6 +41,7 @@ struct StepArgs {
   const uint64_t* step_counter;
   float lr[5];
   float beta1, beta2, adam_eps;
+  float reg_o, reg_s;  // regulariser weights of the loss
 };
 
 // Per-thread view of the step: index and bias corrections 1 / (1 - beta^t).
@@ -62,10 +63,13 @@ __device__ __forceinline__ StepNow step_now(const StepArgs& a) {
 
 // Adam on R rows (stride n) of one component: every load of the group is
 // issued before the first update, so each thread keeps 4R loads in flight.
-template <int R>
+// REG adds a regulariser's gradient, a closed form of the parameter p:
+// 1: reg exp(p) (scale term, p = log_scale), 2: reg sign(tanh p)(1 - tanh^2 p)
+// (opacity term, p = opacity_raw).
+template <int R, int REG = 0>
 __device__ __forceinline__ void adam_rows(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                                           float* __restrict__ v, size_t n, float lr, const StepArgs& a,
-                                          const StepNow& t) {
+                                          const StepNow& t, float reg = 0.0f) {
   float pp[R], gg[R], mo[R], vo[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -76,6 +80,12 @@ __device__ __forceinline__ void adam_rows(float* __restrict__ p, const float* __
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
+    if (REG == 1) gg[r] = fmaf(reg, expf(pp[r]), gg[r]);
+    if (REG == 2) {
+      const float o = tanhf(pp[r]);
+      const float sg = o > 0.0f ? 1.0f : (o < 0.0f ? -1.0f : 0.0f);
+      gg[r] = fmaf(reg * sg, fmaf(-o, o, 1.0f), gg[r]);
+    }
     const float mm = fmaf(a.beta1, mo[r], (1.0f - a.beta1) * gg[r]);
     const float vv = fmaf(a.beta2, vo[r], (1.0f - a.beta2) * gg[r] * gg[r]);
     m[r * n] = mm;
@@ -136,11 +146,18 @@ __device__ __forceinline__ void step_component(const StepArgs& a, uint32_t i, co
     a.p.mean[j] = mu;
   }
   // Adam: log_scale (rows 0-2 of m, v), quat (3-6), nu (7), opacity (8), sh (9..)
-  adam_rows<3>(a.p.log_scale + i, a.g.log_scale + i, a.m + i, a.v + i, n, a.lr[0], a, t);
+  if (a.reg_s != 0.0f)
+    adam_rows<3, 1>(a.p.log_scale + i, a.g.log_scale + i, a.m + i, a.v + i, n, a.lr[0], a, t, a.reg_s);
+  else
+    adam_rows<3>(a.p.log_scale + i, a.g.log_scale + i, a.m + i, a.v + i, n, a.lr[0], a, t);
   adam_rows<4>(a.p.quat + i, a.g.quat + i, a.m + 3 * n + i, a.v + 3 * n + i, n, a.lr[1], a, t);
   adam_rows<1>(a.p.nu + i, a.g.nu + i, a.m + 7 * n + i, a.v + 7 * n + i, n, a.lr[2], a, t);
   a.p.nu[i] = fminf(fmaxf(a.p.nu[i], 1.0f), 1e4f);
-  adam_rows<1>(a.p.opacity_raw + i, a.g.opacity_raw + i, a.m + 8 * n + i, a.v + 8 * n + i, n, a.lr[3], a, t);
+  if (a.reg_o != 0.0f)
+    adam_rows<1, 2>(a.p.opacity_raw + i, a.g.opacity_raw + i, a.m + 8 * n + i, a.v + 8 * n + i, n, a.lr[3], a, t,
+                    a.reg_o);
+  else
+    adam_rows<1>(a.p.opacity_raw + i, a.g.opacity_raw + i, a.m + 8 * n + i, a.v + 8 * n + i, n, a.lr[3], a, t);
   constexpr int SH_ROWS = 3 * K;
   constexpr int CH = SH_ROWS % 8 == 0 ? 8 : (SH_ROWS % 4 == 0 ? 4 : 3);
 #pragma unroll 1
@@ -178,7 +195,7 @@ extern "C" int sss_sghmc_step(const sss_params* params, const sss_params* grads,
     return SSS_ERR_INVALID_ARG;
   if (params->n == 0) return SSS_OK;
   if (!(sp->beta1 >= 0.0f && sp->beta1 < 1.0f && sp->beta2 >= 0.0f && sp->beta2 < 1.0f && sp->eps >= 0.0f &&
-        sp->C >= 0.0f))
+        sp->C >= 0.0f && sp->reg_opacity >= 0.0f && sp->reg_scale >= 0.0f))
     return SSS_ERR_INVALID_ARG;
   sss::StepArgs a;
   a.p = *params;
@@ -200,6 +217,8 @@ extern "C" int sss_sghmc_step(const sss_params* params, const sss_params* grads,
   a.beta1 = sp->beta1;
   a.beta2 = sp->beta2;
   a.adam_eps = sp->adam_eps;
+  a.reg_o = sp->reg_opacity;
+  a.reg_s = sp->reg_scale;
   sss::k_sghmc<<<sss::ceil_div((size_t)params->n, 256), 256, 0, (cudaStream_t)stream>>>(a);
   SSS_LAUNCH_CHECK();
   if (sp->step_counter) {

@@ -1,0 +1,284 @@
+// Image loss of Sec. 3.4: (1 - eps) L1 + eps D-SSIM over every image of a
+// frame, value and gradient.  SSIM as in 3DGS (the loss the paper cites):
+// 11 x 11 Gaussian window, sigma 1.5, zero padding, C1 = 0.01^2, C2 = 0.03^2,
+// D-SSIM = 1 - mean SSIM over all pixels and channels.
+//
+// Value pass: one CTA per (32 x 16 tile, channel) of an image.  The tile
+// plus a 5-pixel halo of prediction x and target y is staged in shared
+// memory; a horizontal 11-tap pass over the 26 rows gives the windowed sums
+// of x, y, x^2, y^2, xy, a vertical pass the five window statistics at each
+// pixel, then SSIM and its partials
+//   a = dS/dmx - 2 mx dS/dsx2 - my dS/dsxy,  b = dS/dsx2,  c = dS/dsxy
+// (written to the scratch maps) and the sums of S and |x - y| (one FP64
+// atomic per CTA).  Gradient pass: the same tiling over the maps gives
+// dS_total/dx = (w * a) + 2 x (w * b) + y (w * c) (the window is symmetric,
+// so the adjoint of the windowed sum is the windowed sum).
+#include "common.cuh"
+
+namespace sss {
+namespace {
+
+constexpr int TX = 32, TY = 16, R = 5, HX = TX + 2 * R, HY = TY + 2 * R, NT = 256;
+
+struct SsimArgs {
+  const float* pred;
+  const float* target;
+  float* maps;    // [3 maps][3 n_pixels], the frame's image layout each
+  double* acc;    // [0] sum |x - y|, [1] sum S
+  float w[2 * R + 1];
+  float eps, inv_count;
+  uint32_t n_pixels;
+  uint32_t tile_base[SSS_MAX_JOBS + 1];  // tiles per job, prefix
+  const float* dl_dloss;
+  float* grad;
+  float* loss_out;
+};
+
+__device__ __forceinline__ int job_of_ssim_tile(const sss_frame_plan& P, const SsimArgs& A, uint32_t t) {
+  int lo = 0, hi = P.n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (A.tile_base[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Stage rows [y0 - R, y0 + TY + R) x cols [x0 - R, x0 + TX + R) of one
+// channel plane (zero outside the image) into s, minus `shift`.
+__device__ __forceinline__ void stage(float (*s)[HX], const float* plane, int W, int H, int x0, int y0,
+                                      float shift = 0.0f) {
+  for (int i = threadIdx.x; i < HY * HX; i += NT) {
+    const int r = i / HX, q = i - r * HX;
+    const int gy = y0 - R + r, gx = x0 - R + q;
+    s[r][q] = ((gx >= 0 && gx < W && gy >= 0 && gy < H) ? plane[(size_t)gy * W + gx] : 0.0f) - shift;
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_ssim_value(const sss_frame_plan P, const SsimArgs A) {
+  __shared__ float sx[HY][HX], sy[HY][HX];
+  __shared__ float hsum[5][HY][TX];
+  __shared__ double red[2][NT / 32];
+  const uint32_t t = blockIdx.x;
+  const int ch = blockIdx.y;
+  const int j = job_of_ssim_tile(P, A, t);
+  const sss_job_desc& J = P.jobs[j];
+  const int W = J.cam.width, H = J.cam.height;
+  const int tiles_x = (W + TX - 1) / TX;
+  const int lt = (int)(t - A.tile_base[j]);
+  const int x0 = (lt % tiles_x) * TX, y0 = (lt / tiles_x) * TY;
+  const size_t plane_off = 3 * (size_t)J.pix_base + (size_t)ch * W * H;
+  // Window statistics of x - cx, y - cy with cx, cy the tile's first pixel:
+  // the variances E[(x-c)^2] - E[x-c]^2 then carry no cancellation in flat
+  // regions (out-of-image pixels stage as -c, i.e. zero padding is kept;
+  // the window weights sum to 1, so the statistics are shift-invariant).
+  const float cx = A.pred[plane_off + (size_t)y0 * W + x0], cy = A.target[plane_off + (size_t)y0 * W + x0];
+  stage(sx, A.pred + plane_off, W, H, x0, y0, cx);
+  stage(sy, A.target + plane_off, W, H, x0, y0, cy);
+  __syncthreads();
+  for (int i = threadIdx.x; i < HY * TX; i += NT) {
+    const int r = i / TX, q = i - r * TX;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 2 * R + 1; ++k) {
+      const float xv = sx[r][q + k], yv = sy[r][q + k], wk = A.w[k];
+      s0 = fmaf(wk, xv, s0);
+      s1 = fmaf(wk, yv, s1);
+      s2 = fmaf(wk, xv * xv, s2);
+      s3 = fmaf(wk, yv * yv, s3);
+      s4 = fmaf(wk, xv * yv, s4);
+    }
+    hsum[0][r][q] = s0;
+    hsum[1][r][q] = s1;
+    hsum[2][r][q] = s2;
+    hsum[3][r][q] = s3;
+    hsum[4][r][q] = s4;
+  }
+  __syncthreads();
+  double l1 = 0.0, ssum = 0.0;
+  constexpr float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+  for (int i = threadIdx.x; i < TY * TX; i += NT) {
+    const int r = i / TX, q = i - r * TX;
+    const int gx = x0 + q, gy = y0 + r;
+    float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 2 * R + 1; ++k) {
+      const float wk = A.w[k];
+#pragma unroll
+      for (int s = 0; s < 5; ++s) m[s] = fmaf(wk, hsum[s][r + k][q], m[s]);
+    }
+    if (gx >= W || gy >= H) continue;
+    const float sx2 = m[2] - m[0] * m[0], sy2 = m[3] - m[1] * m[1], sxy = m[4] - m[0] * m[1];
+    const float mx = m[0] + cx, my = m[1] + cy;
+    const float A1 = fmaf(2.0f * mx, my, C1), A2 = fmaf(2.0f, sxy, C2);
+    const float B1 = fmaf(mx, mx, fmaf(my, my, C1)), B2 = sx2 + sy2 + C2;
+    const float D = 1.0f / (B1 * B2);
+    const float S = A1 * A2 * D;
+    // product forms: no division by A1 or A2 (either can vanish)
+    const float dS_dmx = 2.0f * my * A2 * D - 2.0f * mx * S / B1;
+    const float dS_dsx2 = -S / B2;
+    const float dS_dsxy = 2.0f * A1 * D;
+    const size_t o = plane_off + (size_t)gy * W + gx;
+    A.maps[o] = dS_dmx - 2.0f * mx * dS_dsx2 - my * dS_dsxy;
+    A.maps[3 * (size_t)A.n_pixels + o] = dS_dsx2;
+    A.maps[6 * (size_t)A.n_pixels + o] = dS_dsxy;
+    ssum += (double)S;
+    l1 += (double)fabsf(A.pred[o] - A.target[o]);
+  }
+  // CTA sums -> one FP64 atomic each
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    l1 += __shfl_xor_sync(0xffffffffu, l1, off);
+    ssum += __shfl_xor_sync(0xffffffffu, ssum, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = l1;
+    red[1][threadIdx.x >> 5] = ssum;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < NT / 32; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    atomicAdd(A.acc, a);
+    atomicAdd(A.acc + 1, b);
+  }
+}
+
+__global__ void k_ssim_finish(const SsimArgs A) {
+  const double l1 = A.acc[0] * (double)A.inv_count;
+  const double dssim = 1.0 - A.acc[1] * (double)A.inv_count;
+  A.loss_out[1] = (float)l1;
+  A.loss_out[2] = (float)dssim;
+  A.loss_out[0] = (float)((1.0 - (double)A.eps) * l1 + (double)A.eps * dssim);
+}
+
+__global__ void __launch_bounds__(NT) k_ssim_grad(const sss_frame_plan P, const SsimArgs A) {
+  __shared__ float sm[3][HY][HX];
+  __shared__ float hsum[3][HY][TX];
+  const uint32_t t = blockIdx.x;
+  const int ch = blockIdx.y;
+  const int j = job_of_ssim_tile(P, A, t);
+  const sss_job_desc& J = P.jobs[j];
+  const int W = J.cam.width, H = J.cam.height;
+  const int tiles_x = (W + TX - 1) / TX;
+  const int lt = (int)(t - A.tile_base[j]);
+  const int x0 = (lt % tiles_x) * TX, y0 = (lt / tiles_x) * TY;
+  const size_t plane_off = 3 * (size_t)J.pix_base + (size_t)ch * W * H;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) stage(sm[m], A.maps + m * 3 * (size_t)A.n_pixels + plane_off, W, H, x0, y0);
+  __syncthreads();
+  for (int i = threadIdx.x; i < HY * TX; i += NT) {
+    const int r = i / TX, q = i - r * TX;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 2 * R + 1; ++k) {
+      const float wk = A.w[k];
+      s0 = fmaf(wk, sm[0][r][q + k], s0);
+      s1 = fmaf(wk, sm[1][r][q + k], s1);
+      s2 = fmaf(wk, sm[2][r][q + k], s2);
+    }
+    hsum[0][r][q] = s0;
+    hsum[1][r][q] = s1;
+    hsum[2][r][q] = s2;
+  }
+  __syncthreads();
+  const float scale = A.dl_dloss ? *A.dl_dloss * A.inv_count : A.inv_count;
+  const float w1 = (1.0f - A.eps) * scale, ws = A.eps * scale;
+  for (int i = threadIdx.x; i < TY * TX; i += NT) {
+    const int r = i / TX, q = i - r * TX;
+    const int gx = x0 + q, gy = y0 + r;
+    if (gx >= W || gy >= H) continue;
+    float ca = 0.f, cb = 0.f, cc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 2 * R + 1; ++k) {
+      const float wk = A.w[k];
+      ca = fmaf(wk, hsum[0][r + k][q], ca);
+      cb = fmaf(wk, hsum[1][r + k][q], cb);
+      cc = fmaf(wk, hsum[2][r + k][q], cc);
+    }
+    const size_t o = plane_off + (size_t)gy * W + gx;
+    const float x = A.pred[o], y = A.target[o];
+    const float dS = fmaf(2.0f * x, cb, fmaf(y, cc, ca));
+    const float d = x - y;
+    const float sg = d > 0.0f ? w1 : (d < 0.0f ? -w1 : 0.0f);
+    A.grad[o] = fmaf(-ws, dS, sg);
+  }
+}
+
+// Byte offset of the two FP64 sums in the scratch (after the nine maps).
+size_t acc_offset(uint32_t n_pixels) { return (9 * (size_t)n_pixels * sizeof(float) + 15) & ~(size_t)15; }
+
+// Arguments shared by both passes; false when the plan has no pixels.
+bool make_args(const sss_frame_plan& P, float eps, void* scratch, SsimArgs& A) {
+  A.maps = static_cast<float*>(scratch);
+  A.acc = reinterpret_cast<double*>(static_cast<char*>(scratch) + acc_offset(P.n_pixels));
+  // the window: normalised Gaussian, sigma 1.5, evaluated in FP64
+  double g[2 * R + 1], tot = 0.0;
+  for (int k = 0; k <= 2 * R; ++k) {
+    const double d = (double)(k - R);
+    g[k] = exp(-d * d / (2.0 * 1.5 * 1.5));
+    tot += g[k];
+  }
+  for (int k = 0; k <= 2 * R; ++k) A.w[k] = (float)(g[k] / tot);
+  A.eps = eps;
+  A.n_pixels = P.n_pixels;
+  A.inv_count = P.n_pixels ? (float)(1.0 / (3.0 * (double)P.n_pixels)) : 0.0f;
+  uint32_t t = 0;
+  for (int j = 0; j < P.n_jobs; ++j) {
+    A.tile_base[j] = t;
+    const int W = P.jobs[j].cam.width, H = P.jobs[j].cam.height;
+    t += (uint32_t)(((W + TX - 1) / TX) * ((H + TY - 1) / TY));
+  }
+  A.tile_base[P.n_jobs] = t;
+  return t > 0;
+}
+
+}  // namespace
+}  // namespace sss
+
+using namespace sss;
+
+extern "C" size_t sss_loss_image_scratch_bytes(const sss_frame_plan* plan) {
+  if (!plan) return 0;
+  return acc_offset(plan->n_pixels) + 2 * sizeof(double);
+}
+
+extern "C" int sss_loss_image(const sss_frame_plan* plan, const float* pred, const float* target, float eps_dssim,
+                              float* loss_out, void* scratch, sss_stream_t stream) {
+  if (!plan || !pred || !target || !loss_out || !scratch) return SSS_ERR_INVALID_ARG;
+  if (!(eps_dssim >= 0.0f && eps_dssim <= 1.0f)) return SSS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(scratch) % 16 != 0) return SSS_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  SsimArgs A{};
+  A.pred = pred;
+  A.target = target;
+  A.loss_out = loss_out;
+  const bool any = make_args(*plan, eps_dssim, scratch, A);
+  if (cudaMemsetAsync(A.acc, 0, 2 * sizeof(double), st) != cudaSuccess) return SSS_ERR_CUDA;
+  if (any) {
+    k_ssim_value<<<dim3(A.tile_base[plan->n_jobs], 3), NT, 0, st>>>(*plan, A);
+    SSS_LAUNCH_CHECK();
+  }
+  k_ssim_finish<<<1, 1, 0, st>>>(A);
+  SSS_LAUNCH_CHECK();
+  return SSS_OK;
+}
+
+extern "C" int sss_loss_image_grad(const sss_frame_plan* plan, const float* pred, const float* target,
+                                   float eps_dssim, const float* dL_dloss, const void* scratch, float* dL_dpred,
+                                   sss_stream_t stream) {
+  if (!plan || !pred || !target || !scratch || !dL_dpred) return SSS_ERR_INVALID_ARG;
+  if (!(eps_dssim >= 0.0f && eps_dssim <= 1.0f)) return SSS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(scratch) % 16 != 0) return SSS_ERR_INVALID_ARG;
+  SsimArgs A{};
+  A.pred = pred;
+  A.target = target;
+  A.dl_dloss = dL_dloss;
+  A.grad = dL_dpred;
+  if (!make_args(*plan, eps_dssim, const_cast<void*>(scratch), A)) return SSS_OK;
+  k_ssim_grad<<<dim3(A.tile_base[plan->n_jobs], 3), NT, 0, (cudaStream_t)stream>>>(*plan, A);
+  SSS_LAUNCH_CHECK();
+  return SSS_OK;
+}

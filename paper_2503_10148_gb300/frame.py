@@ -262,10 +262,12 @@ class Frame:
 
 def step_params(eps=1e-3, C=0.5, k=100.0, t0=0.005, burn_in=False, seed=0, step=0,
                 lr=(5e-3, 1e-3, 1e-2, 5e-2, 2.5e-3), beta1=0.9, beta2=0.999, adam_eps=1e-15,
-                step_counter: torch.Tensor | None = None) -> abi.sss_step_params:
+                step_counter: torch.Tensor | None = None, reg_opacity=0.0, reg_scale=0.0) -> abi.sss_step_params:
     """Sampler options.  With ``step_counter`` (a 1-element int64 device
     tensor) the step index is read from and advanced on the device, so a
-    CUDA-graph replay of the step draws fresh noise."""
+    CUDA-graph replay of the step draws fresh noise.  ``reg_opacity`` and
+    ``reg_scale`` are the loss's regulariser weights, whose gradients the
+    step adds."""
     sp = abi.sss_step_params()
     if step_counter is not None:
         assert step_counter.dtype == torch.int64 and step_counter.numel() == 1
@@ -276,6 +278,7 @@ def step_params(eps=1e-3, C=0.5, k=100.0, t0=0.005, burn_in=False, seed=0, step=
     for i in range(5):
         sp.lr[i] = float(lr[i])
     sp.beta1, sp.beta2, sp.adam_eps = beta1, beta2, adam_eps
+    sp.reg_opacity, sp.reg_scale = float(reg_opacity), float(reg_scale)
     return sp
 
 
@@ -299,3 +302,29 @@ def sghmc_step(scene: Scene, grads: Scene, state: SamplerState, sp: abi.sss_step
 def loss_l1(pred: torch.Tensor, target: torch.Tensor, grad_out: torch.Tensor, loss_out: torch.Tensor, stream=None):
     abi.sss_loss_l1(pred.data_ptr(), target.data_ptr(), pred.numel(), grad_out.data_ptr(), loss_out.data_ptr(),
                     stream)
+
+
+def loss_image_scratch(frame: Frame) -> torch.Tensor:
+    """Device scratch for sss_loss_image on this frame's plan."""
+    nbytes = abi.sss_loss_image_scratch_bytes(frame.plan)
+    # float64 elements, two per 16 bytes: at least nbytes, 16-byte aligned
+    buf = torch.empty(2 * ((nbytes + 15) // 16), dtype=torch.float64, device=frame.device)
+    assert buf.numel() * buf.element_size() >= nbytes and buf.data_ptr() % 16 == 0
+    return buf
+
+
+def loss_image(frame: Frame, pred: torch.Tensor, target: torch.Tensor, eps_dssim: float, loss_out: torch.Tensor,
+               scratch: torch.Tensor, stream=None):
+    abi.sss_loss_image(frame.plan, pred.data_ptr(), target.data_ptr(), eps_dssim, loss_out.data_ptr(),
+                       scratch.data_ptr(), stream)
+
+
+def loss_image_grad(frame: Frame, pred: torch.Tensor, target: torch.Tensor, eps_dssim: float,
+                    scratch: torch.Tensor, grad_out: torch.Tensor, dloss: torch.Tensor | None = None, stream=None):
+    abi.sss_loss_image_grad(frame.plan, pred.data_ptr(), target.data_ptr(), eps_dssim,
+                            dloss.data_ptr() if dloss is not None else 0, scratch.data_ptr(), grad_out.data_ptr(),
+                            stream)
+
+
+def regularizers(scene: Scene, reg_opacity: float, reg_scale: float, loss_out: torch.Tensor, stream=None):
+    abi.sss_regularizers(scene.params(), reg_opacity, reg_scale, loss_out.data_ptr(), stream)

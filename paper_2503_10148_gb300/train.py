@@ -30,10 +30,15 @@ from . import frame as F
 
 class TrainStep:
     def __init__(self, scene: F.Scene, cams, targets: torch.Tensor, cfg=None, sampler: dict | None = None,
-                 headroom: float = 1.5, device="cuda", form: str = "autograd"):
-        if form not in ("autograd", "direct"):
-            raise ValueError(form)
+                 headroom: float = 1.5, device="cuda", form: str = "autograd", loss: str = "l1",
+                 eps_dssim: float = 0.2, reg_opacity: float = 0.01, reg_scale: float = 0.01):
+        """``loss="l1"``: the L1 term alone; ``loss="full"``: the loss of
+        Sec. 3.4, (1 - eps_dssim) L1 + eps_dssim D-SSIM plus the opacity and
+        scale regularisers (their gradients added by the sampler step)."""
+        if form not in ("autograd", "direct") or loss not in ("l1", "full"):
+            raise ValueError((form, loss))
         self.form = form
+        self.loss_kind, self.eps_dssim = loss, float(eps_dssim)
         self.scene = scene
         self.cams = list(cams)
         self.device = torch.device(device)
@@ -46,7 +51,12 @@ class TrainStep:
         self.dl = torch.zeros_like(self.frame.rgb)
         self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
         self.step_counter = torch.zeros(1, dtype=torch.int64, device=self.device)
-        self.sp = F.step_params(step_counter=self.step_counter, **(sampler or {}))
+        regs = dict(reg_opacity=reg_opacity, reg_scale=reg_scale) if loss == "full" else {}
+        self.sp = F.step_params(step_counter=self.step_counter, **{**regs, **(sampler or {})})
+        if loss == "full":
+            self.scratch = F.loss_image_scratch(self.frame)
+            self.loss3 = torch.zeros(3, dtype=torch.float32, device=self.device)  # [L, L1, 1 - SSIM]
+            self.loss = self.loss3[0:1]
         self.headroom = headroom
         self.graph = None
         if form == "autograd":
@@ -69,7 +79,10 @@ class TrainStep:
         fr = self.frame
         if self.form == "autograd":
             rgb = AG.render(fr, self.leaves, grow=False)
-            loss = AG.l1_loss(rgb, self.targets)
+            if self.loss_kind == "full":
+                loss = AG.image_loss(fr, rgb, self.targets, self.eps_dssim)
+            else:
+                loss = AG.l1_loss(rgb, self.targets)
             grads = torch.autograd.grad(loss, self.leaves, grad_outputs=self.one)
             self.rgb_out, self.loss = rgb, loss
             self.grads = F.Scene(dict(zip(F.FIELDS, grads)), self.scene.n, self.scene.sh_degree)
@@ -79,7 +92,11 @@ class TrainStep:
         fr.bin(st)
         fr.sort(st)
         fr.render_fwd(st)
-        F.loss_l1(fr.rgb, self.targets, self.dl, self.loss, st)
+        if self.loss_kind == "full":
+            F.loss_image(fr, fr.rgb, self.targets, self.eps_dssim, self.loss3, self.scratch, st)
+            F.loss_image_grad(fr, fr.rgb, self.targets, self.eps_dssim, self.scratch, self.dl, stream=st)
+        else:
+            F.loss_l1(fr.rgb, self.targets, self.dl, self.loss, st)
         fr.render_bwd(self.dl, st)
         fr.project_bwd([self.grads], st)
         F.sghmc_step(self.scene, self.grads, self.state, self.sp, stream=st)
