@@ -31,10 +31,15 @@ from . import frame as F
 class TrainStep:
     def __init__(self, scene: F.Scene, cams, targets: torch.Tensor, cfg=None, sampler: dict | None = None,
                  headroom: float = 1.5, device="cuda", form: str = "autograd", loss: str = "l1",
-                 eps_dssim: float = 0.2, reg_opacity: float = 0.01, reg_scale: float = 0.01):
+                 eps_dssim: float = 0.2, reg_opacity: float = 0.01, reg_scale: float = 0.01,
+                 restart: bool = False):
         """``loss="l1"``: the L1 term alone; ``loss="full"``: the loss of
         Sec. 3.4, (1 - eps_dssim) L1 + eps_dssim D-SSIM plus the opacity and
-        scale regularisers (their gradients added by the sampler step)."""
+        scale regularisers (their gradients added by the sampler step).
+        ``restart=True`` starts every step from the parameters the step was
+        built with (one device-to-device copy at the start of the step, part
+        of the captured graph): repeated steps then run the same workload
+        instead of a scene that drifts under the sampler (for timing)."""
         if form not in ("autograd", "direct") or loss not in ("l1", "full"):
             raise ValueError((form, loss))
         self.form = form
@@ -59,6 +64,7 @@ class TrainStep:
             self.loss = self.loss3[0:1]
         self.headroom = headroom
         self.graph = None
+        self.initial = {f: scene.t[f].detach().clone() for f in F.FIELDS} if restart else None
         if form == "autograd":
             self.leaves = AG.leaves(scene)
             self.one = torch.ones((), dtype=torch.float32, device=self.device)
@@ -77,6 +83,10 @@ class TrainStep:
         """Enqueue one step on the current stream (no host synchronisation)."""
         st = torch.cuda.current_stream(self.device)
         fr = self.frame
+        if self.initial is not None:
+            with torch.no_grad():
+                for f in F.FIELDS:
+                    self.scene.t[f].copy_(self.initial[f])
         if self.form == "autograd":
             rgb = AG.render(fr, self.leaves, grow=False)
             if self.loss_kind == "full":
@@ -155,10 +165,15 @@ class PlainStep:
     """Same step with one frame per view, launched eagerly view after view."""
 
     def __init__(self, scene: F.Scene, cams, targets: torch.Tensor, cfg=None, sampler: dict | None = None,
-                 device="cuda"):
+                 device="cuda", loss: str = "l1", eps_dssim: float = 0.2, reg_opacity: float = 0.01,
+                 reg_scale: float = 0.01, restart: bool = False):
+        """Same options as TrainStep; each view's loss is a mean over that
+        view's pixels (the per-view gradients are summed by a PyTorch
+        reduction before the sampler step)."""
         self.scene = scene
         self.device = torch.device(device)
         self.cfg = cfg if cfg is not None else F.make_cfg()
+        self.loss_kind, self.eps_dssim = loss, float(eps_dssim)
         self.frames = [F.Frame([scene], [c], cfg=self.cfg, device=self.device) for c in cams]
         self.targets = []
         off = 0
@@ -170,14 +185,25 @@ class PlainStep:
         self.total = scene.zeros_like()
         self.state = F.SamplerState(scene)
         self.dl = [torch.zeros_like(fr.rgb) for fr in self.frames]
-        self.loss = torch.zeros(len(self.frames), dtype=torch.float32, device=self.device)  # per view
+        self.loss = torch.zeros(3 * len(self.frames), dtype=torch.float32, device=self.device)  # per view
         self.step_counter = torch.zeros(1, dtype=torch.int64, device=self.device)
-        self.sp = F.step_params(step_counter=self.step_counter, **(sampler or {}))
+        regs = dict(reg_opacity=reg_opacity, reg_scale=reg_scale) if loss == "full" else {}
+        self.sp = F.step_params(step_counter=self.step_counter, **{**regs, **(sampler or {})})
+        self.scratch = [F.loss_image_scratch(fr) for fr in self.frames] if loss == "full" else None
+        self.initial = {f: scene.t[f].detach().clone() for f in F.FIELDS} if restart else None
 
     def run(self):
+        if self.initial is not None:
+            with torch.no_grad():
+                for f in F.FIELDS:
+                    self.scene.t[f].copy_(self.initial[f])
         for v, (fr, tgt, dl, g) in enumerate(zip(self.frames, self.targets, self.dl, self.grads)):
             fr.forward(grow=True)
-            F.loss_l1(fr.rgb, tgt, dl, self.loss[v:v + 1])
+            if self.loss_kind == "full":
+                F.loss_image(fr, fr.rgb, tgt, self.eps_dssim, self.loss[3 * v:3 * v + 3], self.scratch[v])
+                F.loss_image_grad(fr, fr.rgb, tgt, self.eps_dssim, self.scratch[v], dl)
+            else:
+                F.loss_l1(fr.rgb, tgt, dl, self.loss[v:v + 1])
             fr.backward(dl, [g])
         for f in F.FIELDS:
             self.total.t[f].copy_(torch.stack([g.t[f] for g in self.grads]).sum(0))
