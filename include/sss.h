@@ -16,6 +16,7 @@
  *   sss_loss_image   L1 + D-SSIM over a frame's images      Sec. 3.4 loss
  *   sss_loss_image_grad  its gradient                       Sec. 3.4 loss
  *   sss_regularizers opacity and scale regularisers         Sec. 3.4 loss
+ *   sss_relocate     component recycling                    Sec. 3.4, Eq. relocation
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -345,6 +346,42 @@ int sss_loss_image_grad(const sss_frame_plan* plan, const float* pred, const flo
  * sss_sghmc_step (reg_opacity, reg_scale of sss_step_params). */
 int sss_regularizers(const sss_params* params, float reg_opacity, float reg_scale, float* loss_out,
                      sss_stream_t stream);
+
+/* Component recycling (Sec. 3.4 "Adding and Recycling Components", Eq.
+ * relocation, SM "Component Recycling"), in place on one scene:
+ *  - dead: |o| = |tanh(opacity_raw)| < dead_opacity (FP64); the first
+ *    floor(max_fraction n) dead components in index order move;
+ *  - each draws a target from the multinomial over live components with
+ *    weight floor(|o| 2^12): x = word 0 of Philox4x32-10 on counter
+ *    (dead rank, 1, step_lo, step_hi) and key (seed_lo, seed_hi),
+ *    v = (x W) >> 32 (W the weight total), target = the first index whose
+ *    inclusive weight prefix exceeds v;
+ *  - a target keeps its first n_max - 1 draws in dead-rank order (later ones
+ *    stay dead); with N = 1 + copies, in FP64:
+ *      o_new = 1 - (1 - |o|)^(1/N) (sign of o),
+ *      Sigma_new = F Sigma_old, F = o^2 (B(1/2, (nu+2)/2) / K)^2,
+ *      K = sum_{i=1..N} sum_{k<i} C(i-1,k) (-1)^k o_new^(k+1)
+ *          B(1/2, ((k+1)(nu+3)-1)/2), nu kept, B from ln Gamma,
+ *    i.e. every log-scale of the target grows by ln(F)/2;
+ *  - the copies take the target's mean, quaternion, nu, SH, new opacity and
+ *    scale; their momentum and Adam moments (layouts of sss_sghmc_step) are
+ *    set to zero.
+ *   params     device parameters of the scene, modified in place
+ *   moved_out  device uint32: number of components moved (overwritten)
+ *   scratch    device buffer of sss_relocate_scratch_bytes(n, max_fraction)
+ *              bytes, 256-byte aligned.
+ * Errors: SSS_ERR_INVALID_ARG for NULL pointers, a misaligned scratch,
+ * max_fraction outside [0, 1], dead_opacity < 0 or n_max outside [2, 64]. */
+typedef struct sss_relocate_params {
+  float dead_opacity; /* 0.005: the sampler's gate opens below it */
+  float max_fraction; /* 0.05: at most 5 % of the components per call */
+  int32_t n_max;      /* at most n_max - 1 copies per target */
+  uint64_t seed, step;
+} sss_relocate_params;
+
+size_t sss_relocate_scratch_bytes(int32_t n, float max_fraction);
+int sss_relocate(const sss_params* params, float* momentum, float* adam_m, float* adam_v,
+                 const sss_relocate_params* rp, uint32_t* moved_out, void* scratch, sss_stream_t stream);
 
 /* -------------------------------------------- no-allocation forward */
 /* No counterpart in the paper.  A forward render of one small frame for

@@ -67,6 +67,11 @@ class sss_step_params(Structure):
                 ("reg_scale", c_float)]
 
 
+class sss_relocate_params(Structure):
+    _fields_ = [("dead_opacity", c_float), ("max_fraction", c_float), ("n_max", c_int32), ("seed", c_uint64),
+                ("step", c_uint64)]
+
+
 class SSSError(RuntimeError):
     def __init__(self, fn: str, status: int):
         super().__init__(f"{fn} failed: {status_string(status)} ({status})")
@@ -96,12 +101,16 @@ _SIGS = {
     "sss_loss_image_grad": [POINTER(sss_frame_plan), c_void_p, c_void_p, c_float, c_void_p, c_void_p, c_void_p,
                             c_void_p],
     "sss_regularizers": [POINTER(sss_params), c_float, c_float, c_void_p, c_void_p],
+    "sss_relocate": [POINTER(sss_params), c_void_p, c_void_p, c_void_p, POINTER(sss_relocate_params), c_void_p,
+                     c_void_p, c_void_p],
     "sss_read_status": [POINTER(sss_frame_plan), c_void_p, POINTER(c_uint32), POINTER(c_uint32),
                         POINTER(c_uint32), c_void_p],
     "sss_render_static": [POINTER(sss_params), POINTER(sss_camera), POINTER(sss_raster_cfg), c_void_p, c_void_p],
 }
 _SIGS["sss_loss_image_scratch_bytes"] = [POINTER(sss_frame_plan)]
-_RESTYPES = {"sss_default_cfg": None, "sss_status_string": c_char_p, "sss_loss_image_scratch_bytes": c_size_t}
+_SIGS["sss_relocate_scratch_bytes"] = [c_int32, c_float]
+_RESTYPES = {"sss_default_cfg": None, "sss_status_string": c_char_p, "sss_loss_image_scratch_bytes": c_size_t,
+             "sss_relocate_scratch_bytes": c_size_t}
 
 
 def lib_path() -> str:
@@ -250,3 +259,14 @@ def sss_render_static(scene: sss_params, cam: sss_camera, cfg: sss_raster_cfg, o
     array as workspace (no allocation); synchronises the stream."""
     _check("sss_render_static", lib().sss_render_static(ctypes.byref(scene), ctypes.byref(cam), ctypes.byref(cfg),
                                                         c_void_p(out_rgb_ptr), _stream(stream)))
+
+
+def sss_relocate_scratch_bytes(n: int, max_fraction: float) -> int:
+    return int(lib().sss_relocate_scratch_bytes(int(n), float(max_fraction)))
+
+
+def sss_relocate(params: sss_params, momentum_ptr: int, adam_m_ptr: int, adam_v_ptr: int, rp: sss_relocate_params,
+                 moved_ptr: int, scratch_ptr: int, stream=None):
+    _check("sss_relocate", lib().sss_relocate(ctypes.byref(params), c_void_p(momentum_ptr), c_void_p(adam_m_ptr),
+                                              c_void_p(adam_v_ptr), ctypes.byref(rp), c_void_p(moved_ptr),
+                                              c_void_p(scratch_ptr), _stream(stream)))

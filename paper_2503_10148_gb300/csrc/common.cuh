@@ -239,6 +239,35 @@ struct Stager {
   }
 };
 
+// ------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
+// multiplications by the published multipliers on counter words 0 and 2,
+// xor of the high halves with words 1, 3 and the round key, a word
+// permutation, and a Weyl-sequence key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// ------------------------------------------------------------ radix sort
+// Stable LSD sort of `count` (key, value) pairs of 32-bit words over key bits
+// [0, bits), in the library's workspace conventions (sort.cu): the result
+// lands in slot (ceil(bits / 8) & 1) of the two key / value copies; `hist`
+// holds 256 * nb + 256 words; count_dev (device) overrides count_max when
+// not NULL.  Host function: enqueues kernels on `st`.
+int radix_sort_pairs(uint32_t* keys0, uint32_t* keys1, uint32_t* vals0, uint32_t* vals1, const uint32_t* first_vals,
+                     const uint32_t* first_keys, const uint32_t* count_dev, uint32_t count_max, int bits, int nb,
+                     uint32_t* hist, cudaStream_t st);
+
 // ------------------------------------------------------------ warp helpers
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 

@@ -102,7 +102,7 @@ __device__ __forceinline__ uint32_t block_scan_incl(uint32_t v, uint32_t* s_w, u
 __global__ void __launch_bounds__(kThreads) k_upsweep(const uint32_t* __restrict__ keys, const uint32_t* count_dev,
                                                       uint32_t count_max, int shift, uint32_t* __restrict__ hist) {
   __shared__ uint32_t sh[kWarps][kRadix];
-  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned warp = threadIdx.x >> 5;
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) sh[w][threadIdx.x] = 0;
   __syncthreads();
@@ -420,6 +420,14 @@ __global__ void k_ranges_fix(uint2* __restrict__ ranges, uint32_t n_tiles) {
 }
 
 }  // namespace
+
+int radix_sort_pairs(uint32_t* keys0, uint32_t* keys1, uint32_t* vals0, uint32_t* vals1, const uint32_t* first_vals,
+                     const uint32_t* first_keys, const uint32_t* count_dev, uint32_t count_max, int bits, int nb,
+                     uint32_t* hist, cudaStream_t st) {
+  return radix_sort(keys0, keys1, vals0, vals1, first_vals, first_keys, count_dev, count_max, bits, nb, hist, nullptr,
+                    st);
+}
+
 }  // namespace sss
 
 using namespace sss;

@@ -328,3 +328,21 @@ def loss_image_grad(frame: Frame, pred: torch.Tensor, target: torch.Tensor, eps_
 
 def regularizers(scene: Scene, reg_opacity: float, reg_scale: float, loss_out: torch.Tensor, stream=None):
     abi.sss_regularizers(scene.params(), reg_opacity, reg_scale, loss_out.data_ptr(), stream)
+
+
+def relocate(scene: Scene, state: SamplerState, dead_opacity=0.005, max_fraction=0.05, n_max=32, seed=0, step=0,
+             moved_out: torch.Tensor | None = None, scratch: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Component recycling in place (sss_relocate); returns the device count
+    of moved components (int32 tensor of one element)."""
+    rp = abi.sss_relocate_params()
+    rp.dead_opacity, rp.max_fraction, rp.n_max = float(dead_opacity), float(max_fraction), int(n_max)
+    rp.seed, rp.step = int(seed), int(step)
+    dev = scene.t["mean"].device
+    if scratch is None:
+        nbytes = abi.sss_relocate_scratch_bytes(scene.n, max_fraction)
+        scratch = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    off = (-scratch.data_ptr()) % 256
+    moved = moved_out if moved_out is not None else torch.zeros(1, dtype=torch.int32, device=dev)
+    abi.sss_relocate(scene.params(), state.r.data_ptr(), state.m.data_ptr(), state.v.data_ptr(), rp,
+                     moved.data_ptr(), scratch.data_ptr() + off, stream)
+    return moved
