@@ -125,6 +125,10 @@ typedef struct sss_raster_cfg {
   float lowpass;          /* added to the diagonal of Sigma2D; 0 in the
                              paper's final model, 0.3 in its ablation         */
   float bg[3];            /* background colour                                */
+  int32_t kernel;         /* 0: Student's t (default); 1: Gaussian, the limit
+                             nu -> infinity, T2D = exp(-h/2) with extent
+                             h <= 2 ln(|o|/tau) and no nu gradient (the
+                             paper's "SGHMC + 3DGS" ablation kernel)          */
 } sss_raster_cfg;
 
 /* Fills *cfg with the defaults quoted above. */
@@ -292,6 +296,12 @@ typedef struct sss_step_params {
                              bias-corrects with the right t */
   float reg_opacity;      /* eps_o of the loss, >= 0 */
   float reg_scale;        /* eps_Sigma of the loss, >= 0 */
+  float* mu_adam_m;       /* optional device float[3][n] (both or neither):
+                             Adam moments of dL/dmu; when given, G in the
+                             SGHMC update is Adam's m^ / (sqrt(v^) + adam_eps)
+                             of dL/dmu (Implementation Details: the Adam
+                             gradient in SGHMC) and the moments are updated */
+  float* mu_adam_v;
 } sss_step_params;
 
 int sss_sghmc_step(const sss_params* params, const sss_params* grads, float* momentum, float* adam_m,

@@ -31,7 +31,7 @@ G_STRIDE = len(G_FIELDS)
 F_NEAR_TAU, F_NEAR_TMIN = 1, 2
 
 DEFAULT_CFG = dict(tau=1.0 / 255.0, t_min=1e-4, alpha_max=0.99, znear=0.2, lowpass=0.0,
-                   bg=(0.0, 0.0, 0.0), tile_w=16, tile_h=16, nu_grad_mode=0)
+                   bg=(0.0, 0.0, 0.0), tile_w=16, tile_h=16, nu_grad_mode=0, kernel=0)
 
 _lib = None
 
@@ -128,7 +128,7 @@ def cfg_arrays(cfg=None):
     if cfg:
         c.update(cfg)
     d = np.array([c["tau"], c["t_min"], c["alpha_max"], c["znear"], c["lowpass"], *c["bg"]], np.float64)
-    i = np.array([c["tile_w"], c["tile_h"], c["nu_grad_mode"]], np.int32)
+    i = np.array([c["tile_w"], c["tile_h"], c["nu_grad_mode"], c.get("kernel", 0)], np.int32)
     return d, i
 
 
@@ -243,6 +243,19 @@ def sghmc_step(theta, grad, r, m, v, *, n, sh_degree, params=None, burn_in=False
     lib().orc_sghmc_step(n, sh_degree, th, np.ascontiguousarray(grad, np.float64), rr, mm, vv, sp,
                          int(bool(burn_in)), int(seed), int(step), xi)
     return th, rr, mm, vv, xi.reshape(3, n)
+
+
+def adam_preconditioned(g_mu, m, v, *, step: int, beta1: float, beta2: float, adam_eps: float):
+    """The Adam gradient used in SGHMC (Implementation Details): updates the
+    moments of dL/dmu and returns (m^ / (sqrt(v^) + eps), m', v') with the
+    bias corrections of step t = step + 1.  Plain numpy, FP64."""
+    g = np.asarray(g_mu, np.float64)
+    m2 = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v2 = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    t = step + 1
+    mhat = m2 / (1.0 - beta1 ** t)
+    vhat = v2 / (1.0 - beta2 ** t)
+    return mhat / (np.sqrt(vhat) + adam_eps), m2, v2
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

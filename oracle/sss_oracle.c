@@ -81,6 +81,8 @@ typedef struct {
 typedef struct {
   double tau, t_min, alpha_max, znear, lowpass, bg[3];
   int tile_w, tile_h, nu_grad_mode;
+  int kernel; /* 0: Student's t (Eq. t_2D); 1: Gaussian, the nu -> infinity
+                 limit exp(-h/2) (Sec. 3.1; the paper's SGHMC + 3DGS ablation) */
 } ocfg;
 
 static ocam read_cam(const double* c, const int* wh) {
@@ -95,7 +97,7 @@ static ocfg read_cfg(const double* d, const int* i) {
   ocfg g;
   g.tau = d[0]; g.t_min = d[1]; g.alpha_max = d[2]; g.znear = d[3]; g.lowpass = d[4];
   g.bg[0] = d[5]; g.bg[1] = d[6]; g.bg[2] = d[7];
-  g.tile_w = i[0]; g.tile_h = i[1]; g.nu_grad_mode = i[2];
+  g.tile_w = i[0]; g.tile_h = i[1]; g.nu_grad_mode = i[2]; g.kernel = i[3];
   return g;
 }
 
@@ -312,6 +314,16 @@ static double h_limit(double o_abs, double nu, double a) {
   return nu * expm1(2.0 / (nu + 2.0) * log(o_abs / a));
 }
 
+/* The splat kernel of the chosen family and its extent: the t profile of
+ * Eq. t_2D, or the Gaussian exp(-h/2) (the limit nu -> infinity) for which
+ * |o| exp(-h/2) >= a  <=>  h <= 2 ln(|o| / a). */
+static double kernel_value(double h, double nu, const ocfg* cfg) {
+  return cfg->kernel == 1 ? exp(-0.5 * h) : orc_t2d(h, nu);
+}
+static double kernel_limit(double o_abs, double nu, double a, const ocfg* cfg) {
+  return cfg->kernel == 1 ? 2.0 * log(o_abs / a) : h_limit(o_abs, nu, a);
+}
+
 static void project_record(int n, int sh_deg, const double* th, size_t i, const ocam* cam, const ocfg* cfg,
                            double* rec) {
   cx buf[12 + 48];
@@ -346,7 +358,7 @@ static void project_record(int n, int sh_deg, const double* th, size_t i, const 
    * is cut where |alpha| = |o| T2D falls below tau, i.e. h <= h_max.  The
    * pixel centres (i + 0.5, j + 0.5) inside the bounding box of that ellipse
    * give the pixel range; the tiles covering it give the tile rectangle. */
-  double hmax = h_limit(fabs(o), rec[P_NU], cfg->tau);
+  double hmax = kernel_limit(fabs(o), rec[P_NU], cfg->tau, cfg);
   rec[P_HMAX] = hmax;
   double ex = sqrt(rec[P_COV_A] * hmax), ey = sqrt(rec[P_COV_C] * hmax);
   double px0 = ceil(rec[P_MX] - ex - 0.5), px1 = floor(rec[P_MX] + ex - 0.5);
@@ -436,7 +448,7 @@ static void composite_pixel(const double* proj, const long* order, long m, const
     double dx = u - r[P_MX], dy = v - r[P_MY];
     double h = r[P_CON_A] * dx * dx + 2.0 * r[P_CON_B] * dx * dy + r[P_CON_C] * dy * dy;
     if (h > hpre[i]) continue; /* |alpha| < tau (1 - 2e-4) for sure */
-    double t2d = orc_t2d(h, r[P_NU]);
+    double t2d = kernel_value(h, r[P_NU], cfg);
     double alpha = r[P_O] * t2d;
     if (fabs(fabs(alpha) - cfg->tau) < 1e-4 * cfg->tau) fl |= F_NEAR_TAU;
     if (!(fabs(alpha) >= cfg->tau)) continue;
@@ -466,7 +478,7 @@ static double* prefilter_bounds(int n, const double* proj, const ocfg* cfg) {
   double* hpre = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   for (long i = 0; i < n; ++i) {
     const double* r = proj + (size_t)i * P_STRIDE;
-    hpre[i] = r[P_VALID] != 0.0 ? h_limit(fabs(r[P_O]), r[P_NU], cfg->tau * (1.0 - 2e-4)) : -1.0;
+    hpre[i] = r[P_VALID] != 0.0 ? kernel_limit(fabs(r[P_O]), r[P_NU], cfg->tau * (1.0 - 2e-4), cfg) : -1.0;
   }
   return hpre;
 }
@@ -553,8 +565,9 @@ static void pixel_backward(const double* proj, const cvec* cs, double T_final, c
     double nu = r[P_NU];
     double d_o = dL_dalpha * c->t2d;
     double dL_dT = dL_dalpha * r[P_O];
-    double dL_dh = dL_dT * dT_dh(c->h, nu);
-    double d_nu = dL_dT * dT_dnu(c->h, nu, cfg->nu_grad_mode);
+    const int gauss = cfg->kernel == 1;
+    double dL_dh = dL_dT * (gauss ? -0.5 * exp(-0.5 * c->h) : dT_dh(c->h, nu));
+    double d_nu = gauss ? 0.0 : dL_dT * dT_dnu(c->h, nu, cfg->nu_grad_mode);
     /* h = a dx^2 + 2 b dx dy + c dy^2 with (dx, dy) = u - mean2D */
     double d_mx = dL_dh * (-2.0 * (r[P_CON_A] * c->dx + r[P_CON_B] * c->dy));
     double d_my = dL_dh * (-2.0 * (r[P_CON_B] * c->dx + r[P_CON_C] * c->dy));
@@ -582,8 +595,8 @@ static void pixel_backward(const double* proj, const cvec* cs, double T_final, c
        * terms of dT/dnu): the scale a floating-point evaluation rounds
        * against. */
       double dT_mag = fabs(r[P_O]) * dL_dalpha_mag;
-      double dh_mag = dT_mag * fabs(dT_dh(c->h, nu));
-      double nu_mag = 0.5 * log1p(c->h / nu) + (nu + 2.0) / 2.0 * c->h / (nu * nu) / (1.0 + c->h / nu);
+      double dh_mag = dT_mag * (gauss ? 0.5 * exp(-0.5 * c->h) : fabs(dT_dh(c->h, nu)));
+      double nu_mag = gauss ? 0.0 : 0.5 * log1p(c->h / nu) + (nu + 2.0) / 2.0 * c->h / (nu * nu) / (1.0 + c->h / nu);
       const double t[7] = {
           dh_mag * 2.0 * (fabs(r[P_CON_A] * c->dx) + fabs(r[P_CON_B] * c->dy)),
           dh_mag * 2.0 * (fabs(r[P_CON_B] * c->dx) + fabs(r[P_CON_C] * c->dy)),

@@ -38,7 +38,7 @@ class sss_camera(Structure):
 class sss_raster_cfg(Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("batch", c_int32), ("nu_grad_mode", c_int32),
                 ("tau", c_float), ("t_min", c_float), ("alpha_max", c_float), ("znear", c_float),
-                ("lowpass", c_float), ("bg", c_float * 3)]
+                ("lowpass", c_float), ("bg", c_float * 3), ("kernel", c_int32)]
 
 
 class sss_job_desc(Structure):
@@ -64,7 +64,7 @@ class sss_step_params(Structure):
     _fields_ = [("eps", c_float), ("C", c_float), ("k", c_float), ("t0", c_float), ("burn_in", c_int32),
                 ("seed", c_uint64), ("step", c_uint64), ("lr", c_float * 5), ("beta1", c_float),
                 ("beta2", c_float), ("adam_eps", c_float), ("step_counter", c_void_p), ("reg_opacity", c_float),
-                ("reg_scale", c_float)]
+                ("reg_scale", c_float), ("mu_adam_m", c_void_p), ("mu_adam_v", c_void_p)]
 
 
 class sss_relocate_params(Structure):

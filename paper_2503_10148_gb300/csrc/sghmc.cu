@@ -28,6 +28,8 @@ struct StepArgs {
   float lr[5];
   float beta1, beta2, adam_eps;
   float reg_o, reg_s;  // regulariser weights of the loss
+  float* mu_m;         // optional Adam moments of dL/dmu (Adam gradient in SGHMC)
+  float* mu_v;
 };
 
 // Per-thread view of the step: index and bias corrections 1 / (1 - beta^t).
@@ -123,7 +125,14 @@ __device__ __forceinline__ void step_component(const StepArgs& a, uint32_t i, co
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const size_t j = c * n + i;
-    const float G = a.g.mean[j];
+    float G = a.g.mean[j];
+    if (a.mu_m) {  // the Adam gradient in SGHMC: m^ / (sqrt(v^) + eps) of dL/dmu
+      const float mm = fmaf(a.beta1, a.mu_m[j], (1.0f - a.beta1) * G);
+      const float vv = fmaf(a.beta2, a.mu_v[j], (1.0f - a.beta2) * G * G);
+      a.mu_m[j] = mm;
+      a.mu_v[j] = vv;
+      G = (mm * t.inv_bc1) / (sqrtf(vv * t.inv_bc2) + a.adam_eps);
+    }
     const float rr = a.r[j];
     a.r[j] = fr * rr - a.eps * G + sq * xi[c];
     float mu = a.p.mean[j] - a.eps * a.eps * G;
@@ -205,6 +214,9 @@ extern "C" int sss_sghmc_step(const sss_params* params, const sss_params* grads,
   a.adam_eps = sp->adam_eps;
   a.reg_o = sp->reg_opacity;
   a.reg_s = sp->reg_scale;
+  if ((sp->mu_adam_m == nullptr) != (sp->mu_adam_v == nullptr)) return SSS_ERR_INVALID_ARG;
+  a.mu_m = sp->mu_adam_m;
+  a.mu_v = sp->mu_adam_v;
   sss::k_sghmc<<<sss::ceil_div((size_t)params->n, 256), 256, 0, (cudaStream_t)stream>>>(a);
   SSS_LAUNCH_CHECK();
   if (sp->step_counter) {

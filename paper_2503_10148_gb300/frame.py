@@ -107,7 +107,7 @@ def cfg_dict(c: abi.sss_raster_cfg) -> dict:
     """The options as the oracle's dictionary (float64 of the FP32 values)."""
     return dict(tau=float(c.tau), t_min=float(c.t_min), alpha_max=float(c.alpha_max), znear=float(c.znear),
                 lowpass=float(c.lowpass), bg=tuple(float(c.bg[i]) for i in range(3)), tile_w=int(c.tile_w),
-                tile_h=int(c.tile_h), nu_grad_mode=int(c.nu_grad_mode))
+                tile_h=int(c.tile_h), nu_grad_mode=int(c.nu_grad_mode), kernel=int(c.kernel))
 
 
 class Frame:
@@ -262,12 +262,14 @@ class Frame:
 
 def step_params(eps=1e-3, C=0.5, k=100.0, t0=0.005, burn_in=False, seed=0, step=0,
                 lr=(5e-3, 1e-3, 1e-2, 5e-2, 2.5e-3), beta1=0.9, beta2=0.999, adam_eps=1e-15,
-                step_counter: torch.Tensor | None = None, reg_opacity=0.0, reg_scale=0.0) -> abi.sss_step_params:
+                step_counter: torch.Tensor | None = None, reg_opacity=0.0, reg_scale=0.0,
+                mu_adam: tuple | None = None) -> abi.sss_step_params:
     """Sampler options.  With ``step_counter`` (a 1-element int64 device
     tensor) the step index is read from and advanced on the device, so a
     CUDA-graph replay of the step draws fresh noise.  ``reg_opacity`` and
     ``reg_scale`` are the loss's regulariser weights, whose gradients the
-    step adds."""
+    step adds.  ``mu_adam`` = (m, v), two float32 [3][n] device tensors:
+    the SGHMC gradient becomes Adam's normalised gradient of dL/dmu."""
     sp = abi.sss_step_params()
     if step_counter is not None:
         assert step_counter.dtype == torch.int64 and step_counter.numel() == 1
@@ -279,6 +281,8 @@ def step_params(eps=1e-3, C=0.5, k=100.0, t0=0.005, burn_in=False, seed=0, step=
         sp.lr[i] = float(lr[i])
     sp.beta1, sp.beta2, sp.adam_eps = beta1, beta2, adam_eps
     sp.reg_opacity, sp.reg_scale = float(reg_opacity), float(reg_scale)
+    if mu_adam is not None:
+        sp.mu_adam_m, sp.mu_adam_v = mu_adam[0].data_ptr(), mu_adam[1].data_ptr()
     return sp
 
 
