@@ -138,8 +138,17 @@ __device__ __forceinline__ bool eval_pair_slow(float dx, float dy, float ca, flo
   return finish_pair(h, expf(e * lb), lb, o, hmax_pre, tau, amax, r);
 }
 
+// Gaussian kernel (the nu -> infinity limit; records carry nu = +inf):
+// T2D = exp(-h/2) = 2^(-h log2(e) / 2), one MUFU op.
+__device__ __forceinline__ bool eval_pair_gauss(float dx, float dy, float ca, float cb2, float cc, float hmax_pre,
+                                                float o, float tau, float amax, PairEval& r) {
+  const float h = conic_h(dx, dy, ca, cb2, cc);
+  return finish_pair(h, mufu_ex2(h * -0.72134752044448170f), 0.0f, o, hmax_pre, tau, amax, r);
+}
+
 __device__ __forceinline__ bool eval_pair(float dx, float dy, float ca, float cb2, float cc, float hmax_pre,
                                           float o, float nu, float inv_nu, float tau, float amax, PairEval& r) {
+  if (isinf(nu)) return eval_pair_gauss(dx, dy, ca, cb2, cc, hmax_pre, o, tau, amax, r);
   return nu <= kFastNuMax ? eval_pair_fast(dx, dy, ca, cb2, cc, hmax_pre, o, nu, inv_nu, tau, amax, r)
                           : eval_pair_slow(dx, dy, ca, cb2, cc, hmax_pre, o, nu, inv_nu, tau, amax, r);
 }

@@ -95,7 +95,10 @@ __device__ __forceinline__ void project_component(const sss_frame_plan& P, int s
     const DF mxd = screen_coord(J.cam.fx, pxd, pzd, J.cam.cx);
     const DF myd = screen_coord(J.cam.fy, pyd, pzd, J.cam.cy);
     // extent: |o| T2D(h) >= tau  <=>  h <= h_max (reading of the SM's truncation)
-    const float hmax = v.nu * expm1f(2.0f / (v.nu + 2.0f) * logf(fabsf(v.o) / cfg.tau));
+    // Gaussian kernel (nu -> infinity): |o| exp(-h/2) >= tau <=> h <= 2 ln(|o|/tau)
+    const bool gauss = cfg.kernel == 1;
+    const float hmax = gauss ? 2.0f * logf(fabsf(v.o) / cfg.tau)
+                             : v.nu * expm1f(2.0f / (v.nu + 2.0f) * logf(fabsf(v.o) / cfg.tau));
     const float ex = sqrtf(v.A * hmax), ey = sqrtf(v.C * hmax);
     const float fx0 = fmaxf(ceilf(mxd.hi - ex - 0.5f), 0.0f);
     const float fx1 = fminf(floorf(mxd.hi + ex - 0.5f), (float)(J.cam.width - 1));
@@ -129,7 +132,7 @@ __device__ __forceinline__ void project_component(const sss_frame_plan& P, int s
     SplatRec r;
     // (hi - origin) is exact for |hi - origin| < 1024 px (both on hi's grid)
     r.a = make_float4((mxd.hi - (float)ox) + mxd.lo, (myd.hi - (float)oy) + myd.lo, v.con[0], v.con[1]);
-    r.b = make_float4(v.con[2], v.o, hmax, v.nu);
+    r.b = make_float4(v.con[2], v.o, hmax, gauss ? __int_as_float(0x7f800000) : v.nu);  // +inf: Gaussian
     r.c = make_float4(rgb[0], rgb[1], rgb[2], __uint_as_float(ox | (oy << 16)));
     rec[e] = r;
     dkey[e] = __float_as_uint(v.p[2]);

@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(256, (PW * PH >= 4 && B >= 256) ? 2 : 4) k_ren
           int ox, oy;
           rec_origin(c.w, ox, oy);
           const float fbx = (float)(lx - ox), fby = (float)(ly - oy);
-          const float e_over_nu = fmaf(nu, -0.5f, -1.0f) * inv_nu;  // -(nu+2)/(2 nu)
+          // dT/dh = -(nu+2)/(2 nu) T / (1 + h/nu); -1/2 T for the Gaussian (nu = inf, inv_nu = 0)
+          const float e_over_nu = isinf(nu) ? -0.5f : fmaf(nu, -0.5f, -1.0f) * inv_nu;
           // all pixels of the lane in straight-line code, masked; nu branch
           // uniform over the warp
           PairEval r[NPIX];
@@ -207,6 +208,10 @@ __global__ void __launch_bounds__(256, (PW * PH >= 4 && B >= 256) ? 2 : 4) k_ren
 #pragma unroll
             for (int p = 0; p < NPIX; ++p)
               ok[p] = eval_pair_fast(dxs[p], dys[p], a.z, cb2, b.x, hpre, o, nu, inv_nu, tau, amax, r[p]);
+          } else if (isinf(nu)) {
+#pragma unroll
+            for (int p = 0; p < NPIX; ++p)
+              ok[p] = eval_pair_gauss(dxs[p], dys[p], a.z, cb2, b.x, hpre, o, tau, amax, r[p]);
           } else {
 #pragma unroll
             for (int p = 0; p < NPIX; ++p)

@@ -114,6 +114,11 @@ __global__ void __launch_bounds__(256) k_render_fwd(const sss_frame_plan P, void
             for (int p = 0; p < NPIX; ++p)
               ok[p] = eval_pair_fast(pixel_offset(fbx, p % PW, a.x), pixel_offset(fby, p / PW, a.y), a.z, cb2,
                                      b.x, hpre, b.y, b.w, inv_nu, tau, amax, r[p]);
+          } else if (isinf(b.w)) {
+#pragma unroll
+            for (int p = 0; p < NPIX; ++p)
+              ok[p] = eval_pair_gauss(pixel_offset(fbx, p % PW, a.x), pixel_offset(fby, p / PW, a.y), a.z, cb2,
+                                      b.x, hpre, b.y, tau, amax, r[p]);
           } else {
 #pragma unroll
             for (int p = 0; p < NPIX; ++p)

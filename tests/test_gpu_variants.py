@@ -43,10 +43,42 @@ def test_sghmc_with_the_adam_gradient_against_oracle(burn_in):
     th, rr, _, _, _ = oracle.sghmc_step(oracle.theta_from_scene(scene), gpre, np.zeros(3 * n),
                                         np.zeros(sl["sh"].stop), np.zeros(sl["sh"].stop), n=n, sh_degree=0,
                                         params=params, burn_in=burn_in, seed=9, step=step)
-    assert np.allclose(mm.cpu().numpy(), m2, rtol=1e-6, atol=1e-12)
-    assert np.allclose(vv.cpu().numpy(), v2, rtol=1e-6, atol=1e-14)
+    # m' = b1 m + (1 - b1) g can cancel: bound its FP32 rounding by the magnitudes of the two terms
+    g_mu = g0[sl["mean"]].reshape(3, n).astype(np.float64)
+    assert np.all(np.abs(mm.cpu().numpy() - m2) <= 1e-6 * (0.9 * np.abs(m_mu) + 0.1 * np.abs(g_mu)))
+    assert np.allclose(vv.cpu().numpy(), v2, rtol=1e-6, atol=0)
     got = oracle.theta_from_scene(sc.to_numpy())
     sm = sl["mean"]
     # G = m^/(sqrt(v^)+eps) is O(1): the FP32 step carries ~1e-6 of it
     assert np.all(np.abs(got[sm] - th[sm]) <= 2e-6 * np.maximum(np.abs(th[sm]), 1.0)), np.abs(got[sm] - th[sm]).max()
     assert np.allclose(st.r.cpu().numpy().reshape(-1), rr, rtol=1e-5, atol=2e-6)
+
+
+def test_gaussian_kernel_forward_and_backward_against_oracle():
+    """kernel = 1 (T2D = exp(-h/2)): the forward within 1e-4 per channel and
+    the gradient within the bar of the t kernel (nu gets none)."""
+    from gpu_util import (assert_groups_close, gpu_forward, masked_weights, oracle_views, scene_grads_flat,
+                          sh_basis_bound)
+    require_gpu()
+    scene, cams = inputs.tiny_cube_2k()
+    cfg = frame.make_cfg(kernel=1)
+    fr, sc, cams = gpu_forward(scene, cams, cfg)
+    cfgd = frame.cfg_dict(cfg)
+    assert cfgd["kernel"] == 1
+    s32 = f32_scene(scene)
+    refs = oracle_views(s32, cams, cfgd)
+    ok = refs[0][1]["flags"] == 0
+    img = fr.image(0).reshape(3, -1).cpu().numpy()
+    assert np.abs(img[:, ok] - refs[0][1]["rgb"].reshape(3, -1)[:, ok]).max() <= 1e-4
+    assert np.isinf(fr.records().cpu().numpy()[:, 7]).all()  # records carry nu = inf
+    ws = masked_weights(cams, refs, seed=21)
+    dl = torch.as_tensor(np.concatenate([w.reshape(-1) for w in ws]).astype(np.float32), device=DEV)
+    g = sc.zeros_like()
+    fr.backward(dl, [g])
+    torch.cuda.synchronize()
+    gflat = scene_grads_flat(g)
+    gref, g2d, gabs, g2abs = oracle.backward(s32, cams, cfgd, ws, want_grad2d=True, want_abs=True)
+    sl = oracle.theta_slices(scene["n"], 0)
+    assert np.all(gflat[sl["nu"]] == 0.0) and np.all(gref[sl["nu"]] == 0.0)
+    print(assert_groups_close(gflat, gref, scene["n"], 0, gabs, label="gauss",
+                              extra=sh_basis_bound(scene["n"], 0, g2abs)))
