@@ -37,12 +37,12 @@ __device__ __forceinline__ void project_bwd_component(const sss_frame_plan& P, i
 
   float d_mu[3] = {0, 0, 0}, d_ls[3] = {0, 0, 0}, bw[3] = {0, 0, 0};
   float d_o = 0.0f, d_nu = 0.0f;
-  float d_sh[3 * K];
-#pragma unroll
-  for (int k = 0; k < 3 * K; ++k) d_sh[k] = 0.0f;
   bool touched = false;
+  uint64_t views = 0;  // views (bit q - begin) whose gradient record is non-zero and geometry valid
+  const int q0 = P.scene_job_begin[s];
 
-  for (int q = P.scene_job_begin[s]; q < P.scene_job_begin[s + 1]; ++q) {
+  // geometry: mean (through mean2D and the Jacobian), scale, rotation, o, nu
+  for (int q = q0; q < P.scene_job_begin[s + 1]; ++q) {
     const sss_job_desc& J = P.jobs[P.scene_jobs[q]];
     const uint32_t e = J.entry_base + i;
     const float4* gr = reinterpret_cast<const float4*>(g2d + (size_t)e * 12);
@@ -54,6 +54,7 @@ __device__ __forceinline__ void project_bwd_component(const sss_frame_plan& P, i
     const ViewGeom v = view_geom(c, gs, J.cam, cfg);
     if (!v.valid) continue;
     touched = true;
+    views |= 1ull << (q - q0);
     const float* V = J.cam.viewmat;
     // Covariance chain, in the splat's own frame.  With Gc the conic gradient
     // as a symmetric matrix [[ga, gb/2], [gb/2, gc]]: dL/dSigma2D = -Q Gc Q
@@ -117,38 +118,52 @@ __device__ __forceinline__ void project_bwd_component(const sss_frame_plan& P, i
     d_o += g1.y * (1.0f - v.o * v.o);
     if (!v.nu_limited) d_nu += g1.z;
 
-    // colour
-    float cc[3];
-    cam_centre(J.cam, cc);
-    float dd[3] = {c.mu[0] - cc[0], c.mu[1] - cc[1], c.mu[2] - cc[2]};
-    const float il = 1.0f / sqrtf(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-    const float ux = dd[0] * il, uy = dd[1] * il, uz = dd[2] * il;
-    float Y[K];
-    sh_basis<DEG>(ux, uy, uz, Y);
-    float grgb[3] = {g1.w, g2.x, g2.y};
-    float wk[K];
+  }
+
+  // colour, one channel at a time (its K coefficients and their gradients in
+  // registers): dL/dsh_kc = sum over views of g_c Y_k (0 where the channel
+  // is clamped), and the channel's share of the direction gradient of mu,
+  // which is linear in the weights g_c sh_kc
+  for (int ch = 0; ch < 3; ++ch) {
+    float shc[K], dsh[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) wk[k] = 0.0f;
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
+    for (int k = 0; k < K; ++k) {
+      shc[k] = __ldg(S.sh + (size_t)(3 * k + ch) * n + i);
+      dsh[k] = 0.0f;
+    }
+    for (uint64_t m = views; m; m &= m - 1) {
+      const int q = q0 + __ffsll((long long)m) - 1;
+      const sss_job_desc& J = P.jobs[P.scene_jobs[q]];
+      const uint32_t e = J.entry_base + i;
+      const float grgb = g2d[(size_t)e * 12 + 7 + ch];
+      if (grgb == 0.0f) continue;
+      float cc[3];
+      cam_centre(J.cam, cc);
+      const float dd0 = c.mu[0] - cc[0], dd1 = c.mu[1] - cc[1], dd2 = c.mu[2] - cc[2];
+      const float il = 1.0f / sqrtf(dd0 * dd0 + dd1 * dd1 + dd2 * dd2);
+      const float ux = dd0 * il, uy = dd1 * il, uz = dd2 * il;
+      float Y[K];
+      sh_basis<DEG>(ux, uy, uz, Y);
       float raw = 0.5f;
 #pragma unroll
-      for (int k = 0; k < K; ++k) raw = fmaf(__ldg(S.sh + (size_t)(3 * k + ch) * n + i), Y[k], raw);
+      for (int k = 0; k < K; ++k) raw = fmaf(shc[k], Y[k], raw);
       if (raw < 0.0f) continue;  // clamped channel: no gradient
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        d_sh[3 * k + ch] += grgb[ch] * Y[k];
-        wk[k] += grgb[ch] * __ldg(S.sh + (size_t)(3 * k + ch) * n + i);
+      for (int k = 0; k < K; ++k) dsh[k] = fmaf(grgb, Y[k], dsh[k]);
+      if (DEG > 0) {
+        float wk[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) wk[k] = grgb * shc[k];
+        float gx, gy, gz;
+        sh_grad<DEG>(ux, uy, uz, wk, gx, gy, gz);
+        const float dotg = gx * ux + gy * uy + gz * uz;
+        d_mu[0] += (gx - ux * dotg) * il;
+        d_mu[1] += (gy - uy * dotg) * il;
+        d_mu[2] += (gz - uz * dotg) * il;
       }
     }
-    if (DEG > 0) {
-      float gx, gy, gz;
-      sh_grad<DEG>(ux, uy, uz, wk, gx, gy, gz);
-      const float dotg = gx * ux + gy * uy + gz * uz;
-      d_mu[0] += (gx - ux * dotg) * il;
-      d_mu[1] += (gy - uy * dotg) * il;
-      d_mu[2] += (gz - uz * dotg) * il;
-    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) G.sh[(size_t)(3 * k + ch) * n + i] = dsh[k];
   }
 
   float d_q[4] = {0, 0, 0, 0};
@@ -174,15 +189,13 @@ __device__ __forceinline__ void project_bwd_component(const sss_frame_plan& P, i
   for (int k = 0; k < 4; ++k) G.quat[k * n + i] = d_q[k];
   G.nu[i] = d_nu;
   G.opacity_raw[i] = d_o;
-#pragma unroll
-  for (int k = 0; k < 3 * K; ++k) G.sh[k * n + i] = d_sh[k];
 }
 
 struct GradSet {
   sss_params g[SSS_MAX_SCENES];
 };
 
-__global__ void __launch_bounds__(256) k_project_bwd(const sss_frame_plan P, const void* ws, const GradSet G) {
+__global__ void __launch_bounds__(256, 2) k_project_bwd(const sss_frame_plan P, const void* ws, const GradSet G) {
   const uint32_t gidx = blockIdx.x * blockDim.x + threadIdx.x;
   if (gidx >= P.scene_comp_base[P.n_scenes]) return;
   const int s = scene_of_comp(P, gidx);

@@ -9,6 +9,8 @@
 // permutation, and a Weyl-sequence key schedule -- on counter
 // (component, 0, step_lo, step_hi) under key (seed_lo, seed_hi); the four
 // words give three normals by Box-Muller.
+#include <cmath>
+
 #include "common.cuh"
 
 namespace sss {
@@ -30,6 +32,7 @@ struct StepArgs {
   float reg_o, reg_s;  // regulariser weights of the loss
   float* mu_m;         // optional Adam moments of dL/dmu (Adam gradient in SGHMC)
   float* mu_v;
+  float ln_beta1, ln_beta2;
 };
 
 // Per-thread view of the step: index and bias corrections 1 / (1 - beta^t).
@@ -38,53 +41,85 @@ struct StepNow {
   float inv_bc1, inv_bc2;
 };
 
+// Bias corrections 1 / (1 - beta^t) with 1 - beta^t = -expm1(t ln beta) (no
+// cancellation for beta near 1); ln beta comes from the host in FP64.
 __device__ __forceinline__ StepNow step_now(const StepArgs& a) {
   const uint64_t s = a.step_counter ? *a.step_counter : a.step;
   StepNow t;
   t.lo = (uint32_t)s;
   t.hi = (uint32_t)(s >> 32);
-  const double tt = (double)s + 1.0;
-  t.inv_bc1 = (float)(1.0 / (1.0 - pow((double)a.beta1, tt)));
-  t.inv_bc2 = (float)(1.0 / (1.0 - pow((double)a.beta2, tt)));
+  const float tt = (float)s + 1.0f;
+  t.inv_bc1 = -1.0f / expm1f(tt * a.ln_beta1);
+  t.inv_bc2 = -1.0f / expm1f(tt * a.ln_beta2);
   return t;
 }
 
-// Adam on R rows (stride n) of one component: every load of the group is
-// issued before the first update, so each thread keeps 4R loads in flight.
-// REG adds a regulariser's gradient, a closed form of the parameter p:
-// 1: reg exp(p) (scale term, p = log_scale), 2: reg sign(tanh p)(1 - tanh^2 p)
-// (opacity term, p = opacity_raw).
-template <int R, int REG = 0>
-__device__ __forceinline__ void adam_rows(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                                          float* __restrict__ v, size_t n, float lr, const StepArgs& a,
-                                          const StepNow& t, float reg = 0.0f) {
-  float pp[R], gg[R], mo[R], vo[R];
+// Adam (bias-corrected) on every row of the other groups, one CTA row
+// (blockIdx.y) per parameter row: rows 0-2 log_scale (lr[0], + reg_s exp(p)),
+// 3-6 quaternion (lr[1]), 7 nu (lr[2], then limited to [1, 1e4]), 8
+// opacity_raw (lr[3], + reg_o sign(tanh p)(1 - tanh^2 p)), 9.. SH (lr[4]).
+// Each thread updates kPer components with all their loads in flight.
+constexpr int kPer = 4;
+
+__global__ void __launch_bounds__(256) k_adam(const StepArgs a) {
+  __shared__ StepNow s_t;
+  if (threadIdx.x == 0) s_t = step_now(a);
+  __syncthreads();
+  const StepNow t = s_t;
+  const int row = blockIdx.y;
+  const size_t n = (size_t)a.p.n;
+  float* p;
+  const float* g;
+  float lr;
+  int reg = 0;
+  if (row < 3) {
+    p = a.p.log_scale + row * n, g = a.g.log_scale + row * n, lr = a.lr[0], reg = a.reg_s != 0.0f ? 1 : 0;
+  } else if (row < 7) {
+    p = a.p.quat + (row - 3) * n, g = a.g.quat + (row - 3) * n, lr = a.lr[1];
+  } else if (row == 7) {
+    p = a.p.nu, g = a.g.nu, lr = a.lr[2];
+  } else if (row == 8) {
+    p = a.p.opacity_raw, g = a.g.opacity_raw, lr = a.lr[3], reg = a.reg_o != 0.0f ? 2 : 0;
+  } else {
+    p = a.p.sh + (row - 9) * n, g = a.g.sh + (row - 9) * n, lr = a.lr[4];
+  }
+  float* m = a.m + row * n;
+  float* v = a.v + row * n;
+  const size_t base = (size_t)blockIdx.x * (256 * kPer) + threadIdx.x;
+  float pp[kPer], gg[kPer], mo[kPer], vo[kPer];
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    gg[r] = __ldg(g + r * n);
-    pp[r] = p[r * n];
-    mo[r] = m[r * n];
-    vo[r] = v[r * n];
+  for (int k = 0; k < kPer; ++k) {
+    const size_t i = base + 256 * k;
+    if (i < n) {
+      gg[k] = __ldg(g + i);
+      pp[k] = p[i];
+      mo[k] = m[i];
+      vo[k] = v[i];
+    }
   }
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    if (REG == 1) gg[r] = fmaf(reg, expf(pp[r]), gg[r]);
-    if (REG == 2) {
-      const float o = tanhf(pp[r]);
+  for (int k = 0; k < kPer; ++k) {
+    const size_t i = base + 256 * k;
+    if (i >= n) continue;
+    float gk = gg[k];
+    if (reg == 1) gk = fmaf(a.reg_s, expf(pp[k]), gk);
+    if (reg == 2) {
+      const float o = tanhf(pp[k]);
       const float sg = o > 0.0f ? 1.0f : (o < 0.0f ? -1.0f : 0.0f);
-      gg[r] = fmaf(reg * sg, fmaf(-o, o, 1.0f), gg[r]);
+      gk = fmaf(a.reg_o * sg, fmaf(-o, o, 1.0f), gk);
     }
-    const float mm = fmaf(a.beta1, mo[r], (1.0f - a.beta1) * gg[r]);
-    const float vv = fmaf(a.beta2, vo[r], (1.0f - a.beta2) * gg[r] * gg[r]);
-    m[r * n] = mm;
-    v[r * n] = vv;
-    p[r * n] = pp[r] - lr * (mm * t.inv_bc1) / (sqrtf(vv * t.inv_bc2) + a.adam_eps);
+    const float mm = fmaf(a.beta1, mo[k], (1.0f - a.beta1) * gk);
+    const float vv = fmaf(a.beta2, vo[k], (1.0f - a.beta2) * gk * gk);
+    m[i] = mm;
+    v[i] = vv;
+    float np = pp[k] - lr * (mm * t.inv_bc1) / (sqrtf(vv * t.inv_bc2) + a.adam_eps);
+    if (row == 7) np = fminf(fmaxf(np, 1.0f), 1e4f);
+    p[i] = np;
   }
 }
 
 template <int DEG>
 __device__ __forceinline__ void step_component(const StepArgs& a, uint32_t i, const StepNow& t) {
-  constexpr int K = (DEG + 1) * (DEG + 1);
   const size_t n = (size_t)a.p.n;
   const float o = tanhf(a.p.opacity_raw[i]);
   const float gate = 1.0f / (1.0f + expf(a.k * (fabsf(o) - a.t0)));
@@ -140,25 +175,6 @@ __device__ __forceinline__ void step_component(const StepArgs& a, uint32_t i, co
     else mu += gate * a.eps * fr * rr + gate * a.eps * sq * xi[c];
     a.p.mean[j] = mu;
   }
-  // Adam: log_scale (rows 0-2 of m, v), quat (3-6), nu (7), opacity (8), sh (9..)
-  if (a.reg_s != 0.0f)
-    adam_rows<3, 1>(a.p.log_scale + i, a.g.log_scale + i, a.m + i, a.v + i, n, a.lr[0], a, t, a.reg_s);
-  else
-    adam_rows<3>(a.p.log_scale + i, a.g.log_scale + i, a.m + i, a.v + i, n, a.lr[0], a, t);
-  adam_rows<4>(a.p.quat + i, a.g.quat + i, a.m + 3 * n + i, a.v + 3 * n + i, n, a.lr[1], a, t);
-  adam_rows<1>(a.p.nu + i, a.g.nu + i, a.m + 7 * n + i, a.v + 7 * n + i, n, a.lr[2], a, t);
-  a.p.nu[i] = fminf(fmaxf(a.p.nu[i], 1.0f), 1e4f);
-  if (a.reg_o != 0.0f)
-    adam_rows<1, 2>(a.p.opacity_raw + i, a.g.opacity_raw + i, a.m + 8 * n + i, a.v + 8 * n + i, n, a.lr[3], a, t,
-                    a.reg_o);
-  else
-    adam_rows<1>(a.p.opacity_raw + i, a.g.opacity_raw + i, a.m + 8 * n + i, a.v + 8 * n + i, n, a.lr[3], a, t);
-  constexpr int SH_ROWS = 3 * K;
-  constexpr int CH = SH_ROWS % 8 == 0 ? 8 : (SH_ROWS % 4 == 0 ? 4 : 3);
-#pragma unroll 1
-  for (int c = 0; c < SH_ROWS; c += CH)
-    adam_rows<CH>(a.p.sh + c * n + i, a.g.sh + c * n + i, a.m + (9 + c) * n + i, a.v + (9 + c) * n + i, n, a.lr[4],
-                  a, t);
 }
 
 __global__ void k_step_advance(uint64_t* counter) { *counter += 1; }
@@ -217,7 +233,13 @@ extern "C" int sss_sghmc_step(const sss_params* params, const sss_params* grads,
   if ((sp->mu_adam_m == nullptr) != (sp->mu_adam_v == nullptr)) return SSS_ERR_INVALID_ARG;
   a.mu_m = sp->mu_adam_m;
   a.mu_v = sp->mu_adam_v;
+  a.ln_beta1 = (float)std::log((double)sp->beta1);
+  a.ln_beta2 = (float)std::log((double)sp->beta2);
+  // the means first: the gate and the burn-in covariance read the pre-step
+  // opacity, quaternion and scale, which the Adam rows then update
   sss::k_sghmc<<<sss::ceil_div((size_t)params->n, 256), 256, 0, (cudaStream_t)stream>>>(a);
+  const int rows = 9 + 3 * (params->sh_degree + 1) * (params->sh_degree + 1);
+  sss::k_adam<<<dim3(sss::ceil_div((size_t)params->n, 256 * sss::kPer), rows), 256, 0, (cudaStream_t)stream>>>(a);
   SSS_LAUNCH_CHECK();
   if (sp->step_counter) {
     sss::k_step_advance<<<1, 1, 0, (cudaStream_t)stream>>>(sp->step_counter);

@@ -22,6 +22,8 @@
 // addresses of a digit's run instead of 4-byte scattered stores.  The last
 // pass of the pair sort also records every tile's [start, end) with
 // atomicMin/atomicMax of the run ends it writes (order independent).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace sss {
@@ -450,10 +452,14 @@ extern "C" int sss_bin(const sss_frame_plan* plan, void* ws, sss_stream_t stream
                       32, nb, hist, nullptr, st);
   if (rc != SSS_OK) return rc;
   uint32_t* block_sums = hist;  // reused: nb words
-  k_count_sum<<<nb, kThreads, 0, st>>>(order, ws_ptr<uint32_t>(ws, P.ws_off_ntiles), n, block_sums);
-  k_scan_rows<<<1, kThreads, 0, st>>>(block_sums, (uint32_t)nb, ctrl + kCtrlPairsNeeded);
+  // emission: one kTile slice of the depth order per CTA (many CTAs hide the
+  // latency of the dependent order -> count / rectangle gathers); the block
+  // sums fit in the histogram scratch (256 nb + 256 words)
+  const unsigned nbe = (unsigned)std::min<size_t>(ceil_div(n, kTile), (size_t)kRadix * nb);
+  k_count_sum<<<nbe, kThreads, 0, st>>>(order, ws_ptr<uint32_t>(ws, P.ws_off_ntiles), n, block_sums);
+  k_scan_rows<<<1, kThreads, 0, st>>>(block_sums, nbe, ctrl + kCtrlPairsNeeded);
   k_finish_count<<<1, 1, 0, st>>>(ctrl, P.pair_capacity);
-  k_emit<<<nb, kThreads, 0, st>>>(P, order, ws_ptr<uint32_t>(ws, P.ws_off_ntiles), ws_ptr<uint2>(ws, P.ws_off_rect),
+  k_emit<<<nbe, kThreads, 0, st>>>(P, order, ws_ptr<uint32_t>(ws, P.ws_off_ntiles), ws_ptr<uint2>(ws, P.ws_off_rect),
                                   block_sums, ws_ptr<uint32_t>(ws, P.ws_off_pkey),
                                   ws_ptr<uint32_t>(ws, P.ws_off_pval));
   SSS_LAUNCH_CHECK();

@@ -22,8 +22,9 @@ def test_sghmc_with_the_adam_gradient_against_oracle(burn_in):
     g0 = rng.normal(0, 1e-2, size=sl["sh"].stop).astype(np.float32)
     m_mu = rng.normal(0, 1e-3, size=(3, n)).astype(np.float32)
     v_mu = rng.uniform(1e-6, 1e-4, size=(3, n)).astype(np.float32)
-    params = dict(eps=2e-2, C=0.6, k=100.0, t0=0.005, lr=(5e-3, 1e-3, 1e-2, 5e-2, 2.5e-3), beta1=0.9, beta2=0.999,
-                  adam_eps=1e-8)
+    f32 = lambda x: float(np.float32(x))  # the values the kernel sees
+    params = dict(eps=2e-2, C=0.6, k=100.0, t0=0.005, lr=(5e-3, 1e-3, 1e-2, 5e-2, 2.5e-3), beta1=f32(0.9),
+                  beta2=f32(0.999), adam_eps=f32(1e-8))
     step = 4
     sc = frame.Scene.from_numpy(scene, DEV)
     gsc = frame.Scene.zeros(n, 0, DEV)
@@ -37,7 +38,7 @@ def test_sghmc_with_the_adam_gradient_against_oracle(burn_in):
     frame.sghmc_step(sc, gsc, st, sp)
     torch.cuda.synchronize()
     G, m2, v2 = oracle.adam_preconditioned(g0[sl["mean"]].reshape(3, n).astype(np.float64), m_mu, v_mu, step=step,
-                                           beta1=0.9, beta2=0.999, adam_eps=1e-8)
+                                           beta1=params["beta1"], beta2=params["beta2"], adam_eps=params["adam_eps"])
     gpre = g0.astype(np.float64).copy()
     gpre[sl["mean"]] = G.reshape(-1)
     th, rr, _, _, _ = oracle.sghmc_step(oracle.theta_from_scene(scene), gpre, np.zeros(3 * n),
