@@ -3,11 +3,12 @@
 // 11 x 11 Gaussian window, sigma 1.5, zero padding, C1 = 0.01^2, C2 = 0.03^2,
 // D-SSIM = 1 - mean SSIM over all pixels and channels.
 //
-// Value pass: one CTA per (32 x 16 tile, channel) of an image.  The tile
+// Value pass: one CTA per (32 x 32 tile, channel) of an image.  The tile
 // plus a 5-pixel halo of prediction x and target y is staged in shared
-// memory; a horizontal 11-tap pass over the 26 rows gives the windowed sums
+// memory; a horizontal 11-tap pass over the 42 rows gives the windowed sums
 // of x, y, x^2, y^2, xy, a vertical pass the five window statistics at each
-// pixel, then SSIM and its partials
+// pixel (both passes register-blocked: a thread makes 4 adjacent outputs
+// from 14 loaded values), then SSIM and its partials
 //   a = dS/dmx - 2 mx dS/dsx2 - my dS/dsxy,  b = dS/dsx2,  c = dS/dsxy
 // (written to the scratch maps) and the sums of S and |x - y| (one FP64
 // atomic per CTA).  Gradient pass: the same tiling over the maps gives
@@ -18,7 +19,9 @@
 namespace sss {
 namespace {
 
-constexpr int TX = 32, TY = 16, R = 5, HX = TX + 2 * R, HY = TY + 2 * R, NT = 256;
+constexpr int TX = 32, TY = 32, R = 5, HX = TX + 2 * R, HY = TY + 2 * R, NT = 256;
+constexpr int WB = 4;  // outputs per thread along a pass
+constexpr int NTAP = 2 * R + 1;
 
 struct SsimArgs {
   const float* pred;
@@ -75,37 +78,64 @@ __global__ void __launch_bounds__(NT) k_ssim_value(const sss_frame_plan P, const
   stage(sx, A.pred + plane_off, W, H, x0, y0, cx);
   stage(sy, A.target + plane_off, W, H, x0, y0, cy);
   __syncthreads();
-  for (int i = threadIdx.x; i < HY * TX; i += NT) {
-    const int r = i / TX, q = i - r * TX;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+  // horizontal: item = (row, group of WB columns); windowed sums of x, y,
+  // x^2, y^2, xy for WB adjacent columns from WB + 10 staged values
+  for (int it = threadIdx.x; it < HY * (TX / WB); it += NT) {
+    const int r = it / (TX / WB), q0 = (it - r * (TX / WB)) * WB;
+    float xv[WB + 2 * R], yv[WB + 2 * R];
 #pragma unroll
-    for (int k = 0; k < 2 * R + 1; ++k) {
-      const float xv = sx[r][q + k], yv = sy[r][q + k], wk = A.w[k];
-      s0 = fmaf(wk, xv, s0);
-      s1 = fmaf(wk, yv, s1);
-      s2 = fmaf(wk, xv * xv, s2);
-      s3 = fmaf(wk, yv * yv, s3);
-      s4 = fmaf(wk, xv * yv, s4);
+    for (int k = 0; k < WB + 2 * R; ++k) {
+      xv[k] = sx[r][q0 + k];
+      yv[k] = sy[r][q0 + k];
     }
-    hsum[0][r][q] = s0;
-    hsum[1][r][q] = s1;
-    hsum[2][r][q] = s2;
-    hsum[3][r][q] = s3;
-    hsum[4][r][q] = s4;
+#pragma unroll
+    for (int o = 0; o < WB; ++o) {
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+#pragma unroll
+      for (int k = 0; k < NTAP; ++k) {
+        const float a = xv[o + k], b = yv[o + k], wk = A.w[k];
+        s0 = fmaf(wk, a, s0);
+        s1 = fmaf(wk, b, s1);
+        s2 = fmaf(wk, a * a, s2);
+        s3 = fmaf(wk, b * b, s3);
+        s4 = fmaf(wk, a * b, s4);
+      }
+      hsum[0][r][q0 + o] = s0;
+      hsum[1][r][q0 + o] = s1;
+      hsum[2][r][q0 + o] = s2;
+      hsum[3][r][q0 + o] = s3;
+      hsum[4][r][q0 + o] = s4;
+    }
   }
   __syncthreads();
   double l1 = 0.0, ssum = 0.0;
   constexpr float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
-  for (int i = threadIdx.x; i < TY * TX; i += NT) {
-    const int r = i / TX, q = i - r * TX;
-    const int gx = x0 + q, gy = y0 + r;
-    float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  // vertical: item = (column, group of WB rows)
+  for (int it = threadIdx.x; it < TX * (TY / WB); it += NT) {
+    const int q = it % TX, r0 = (it / TX) * WB;
+    float m5[WB][5];
 #pragma unroll
-    for (int k = 0; k < 2 * R + 1; ++k) {
-      const float wk = A.w[k];
+    for (int o = 0; o < WB; ++o)
 #pragma unroll
-      for (int s = 0; s < 5; ++s) m[s] = fmaf(wk, hsum[s][r + k][q], m[s]);
+      for (int c = 0; c < 5; ++c) m5[o][c] = 0.f;
+#pragma unroll
+    for (int k = 0; k < WB + 2 * R; ++k) {
+      float hv[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) hv[c] = hsum[c][r0 + k][q];
+#pragma unroll
+      for (int o = 0; o < WB; ++o) {
+        const int tap = k - o;
+        if (tap < 0 || tap >= NTAP) continue;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) m5[o][c] = fmaf(A.w[tap], hv[c], m5[o][c]);
+      }
     }
+#pragma unroll
+    for (int ob = 0; ob < WB; ++ob) {
+    const int r = r0 + ob;
+    const int gx = x0 + q, gy = y0 + r;
+    const float* m = m5[ob];
     if (gx >= W || gy >= H) continue;
     const float sx2 = m[2] - m[0] * m[0], sy2 = m[3] - m[1] * m[1], sxy = m[4] - m[0] * m[1];
     const float mx = m[0] + cx, my = m[1] + cy;
@@ -123,6 +153,7 @@ __global__ void __launch_bounds__(NT) k_ssim_value(const sss_frame_plan P, const
     A.maps[6 * (size_t)A.n_pixels + o] = dS_dsxy;
     ssum += (double)S;
     l1 += (double)fabsf(A.pred[o] - A.target[o]);
+    }
   }
   // CTA sums -> one FP64 atomic each
 #pragma unroll
@@ -169,41 +200,53 @@ __global__ void __launch_bounds__(NT) k_ssim_grad(const sss_frame_plan P, const 
 #pragma unroll
   for (int m = 0; m < 3; ++m) stage(sm[m], A.maps + m * 3 * (size_t)A.n_pixels + plane_off, W, H, x0, y0);
   __syncthreads();
-  for (int i = threadIdx.x; i < HY * TX; i += NT) {
-    const int r = i / TX, q = i - r * TX;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  for (int it = threadIdx.x; it < HY * (TX / WB); it += NT) {
+    const int r = it / (TX / WB), q0 = (it - r * (TX / WB)) * WB;
 #pragma unroll
-    for (int k = 0; k < 2 * R + 1; ++k) {
-      const float wk = A.w[k];
-      s0 = fmaf(wk, sm[0][r][q + k], s0);
-      s1 = fmaf(wk, sm[1][r][q + k], s1);
-      s2 = fmaf(wk, sm[2][r][q + k], s2);
+    for (int mi = 0; mi < 3; ++mi) {
+      float mv[WB + 2 * R];
+#pragma unroll
+      for (int k = 0; k < WB + 2 * R; ++k) mv[k] = sm[mi][r][q0 + k];
+#pragma unroll
+      for (int o = 0; o < WB; ++o) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < NTAP; ++k) acc = fmaf(A.w[k], mv[o + k], acc);
+        hsum[mi][r][q0 + o] = acc;
+      }
     }
-    hsum[0][r][q] = s0;
-    hsum[1][r][q] = s1;
-    hsum[2][r][q] = s2;
   }
   __syncthreads();
   const float scale = A.dl_dloss ? *A.dl_dloss * A.inv_count : A.inv_count;
   const float w1 = (1.0f - A.eps) * scale, ws = A.eps * scale;
-  for (int i = threadIdx.x; i < TY * TX; i += NT) {
-    const int r = i / TX, q = i - r * TX;
-    const int gx = x0 + q, gy = y0 + r;
-    if (gx >= W || gy >= H) continue;
-    float ca = 0.f, cb = 0.f, cc = 0.f;
+  for (int it = threadIdx.x; it < TX * (TY / WB); it += NT) {
+    const int q = it % TX, r0 = (it / TX) * WB;
+    float cv[WB][3];
 #pragma unroll
-    for (int k = 0; k < 2 * R + 1; ++k) {
-      const float wk = A.w[k];
-      ca = fmaf(wk, hsum[0][r + k][q], ca);
-      cb = fmaf(wk, hsum[1][r + k][q], cb);
-      cc = fmaf(wk, hsum[2][r + k][q], cc);
+    for (int o = 0; o < WB; ++o) cv[o][0] = cv[o][1] = cv[o][2] = 0.f;
+#pragma unroll
+    for (int k = 0; k < WB + 2 * R; ++k) {
+      const float h0 = hsum[0][r0 + k][q], h1 = hsum[1][r0 + k][q], h2 = hsum[2][r0 + k][q];
+#pragma unroll
+      for (int o = 0; o < WB; ++o) {
+        const int tap = k - o;
+        if (tap < 0 || tap >= NTAP) continue;
+        cv[o][0] = fmaf(A.w[tap], h0, cv[o][0]);
+        cv[o][1] = fmaf(A.w[tap], h1, cv[o][1]);
+        cv[o][2] = fmaf(A.w[tap], h2, cv[o][2]);
+      }
     }
-    const size_t o = plane_off + (size_t)gy * W + gx;
-    const float x = A.pred[o], y = A.target[o];
-    const float dS = fmaf(2.0f * x, cb, fmaf(y, cc, ca));
-    const float d = x - y;
-    const float sg = d > 0.0f ? w1 : (d < 0.0f ? -w1 : 0.0f);
-    A.grad[o] = fmaf(-ws, dS, sg);
+#pragma unroll
+    for (int ob = 0; ob < WB; ++ob) {
+      const int gx = x0 + q, gy = y0 + r0 + ob;
+      if (gx >= W || gy >= H) continue;
+      const size_t o = plane_off + (size_t)gy * W + gx;
+      const float x = A.pred[o], y = A.target[o];
+      const float dS = fmaf(2.0f * x, cv[ob][1], fmaf(y, cv[ob][2], cv[ob][0]));
+      const float d = x - y;
+      const float sg = d > 0.0f ? w1 : (d < 0.0f ? -w1 : 0.0f);
+      A.grad[o] = fmaf(-ws, dS, sg);
+    }
   }
 }
 
