@@ -277,6 +277,44 @@ int radix_sort_pairs(uint32_t* keys0, uint32_t* keys1, uint32_t* vals0, uint32_t
                      const uint32_t* first_keys, const uint32_t* count_dev, uint32_t count_max, int bits, int nb,
                      uint32_t* hist, cudaStream_t st);
 
+// ------------------------------------------------------------ warp staging
+// 16-byte asynchronous global -> shared copy (no registers held in flight).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Per-warp staging of splat records, 32 per batch (slot = lane), double
+// buffered: a warp gathers batch i+1 with cp.async while it evaluates batch
+// i, and no other warp touches its buffers (no CTA barrier).
+struct WarpBuf {
+  float4 a[2][32], b[2][32], c[2][32];
+  uint32_t e[2][32];
+};
+
+// Lane `lane` fills slot `lane` of buffer k with record e, or with an empty
+// slot (h_max < 0, never hit) when !valid; one commit group per call.
+__device__ __forceinline__ void warp_stage(WarpBuf& S, int k, const SplatRec* __restrict__ rec, uint32_t e,
+                                           bool valid, int lane) {
+  if (valid) {
+    const float4* src = reinterpret_cast<const float4*>(rec + e);
+    cp_async16(&S.a[k][lane], src);
+    cp_async16(&S.b[k][lane], src + 1);
+    cp_async16(&S.c[k][lane], src + 2);
+  } else {
+    S.a[k][lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    S.b[k][lane] = make_float4(1.0f, 0.0f, -1.0f, 1.0f);
+    S.c[k][lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  }
+  S.e[k][lane] = valid ? e : 0u;
+  cp_async_commit();
+}
+
 // ------------------------------------------------------------ warp helpers
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 

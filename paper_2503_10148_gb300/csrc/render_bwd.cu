@@ -79,23 +79,22 @@ __device__ __forceinline__ float log1p_minus_u(float u, float log_base) {
   return log_base - u;
 }
 
-template <int PW, int PH, int B, bool PAPER_NU>
-__global__ void __launch_bounds__(256, (PW * PH >= 4 && B >= 256) ? 2 : 4) k_render_bwd(const sss_frame_plan P, void* ws,
-                                                    const float* __restrict__ dl_drgb) {
+template <int PW, int PH, bool PAPER_NU>
+__global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const sss_frame_plan P, void* ws,
+                                                       const float* __restrict__ dl_drgb) {
   constexpr int NPIX = PW * PH;
   constexpr int TW = 16 * PW, TH = 16 * PH;
-  constexpr int NW = B / 32;
-  __shared__ float4 s_buf[2][3 * B];
-  __shared__ uint32_t s_ebuf[2][B];
-  __shared__ uint32_t s_top;
+  __shared__ WarpBuf s_wb[2];
 
-  const uint32_t tile = blockIdx.x;
+  // four CTAs of two warps per tile; warp w of the tile's 2 x 4 layout
+  const uint32_t tile = blockIdx.x >> 2;
+  WarpBuf& S = s_wb[threadIdx.x >> 5];
   const int j = job_of_tile(P, tile);
   const sss_job_desc& J = P.jobs[j];
   const sss_raster_cfg& cfg = P.cfg;
   const uint32_t lt = tile - J.tile_base;
   const int tx = (int)(lt % (uint32_t)J.tiles_x), ty = (int)(lt / (uint32_t)J.tiles_x);
-  const int warp = threadIdx.x >> 5;
+  const int warp = (int)((blockIdx.x & 3u) << 1) | (int)(threadIdx.x >> 5);
   const unsigned lane = threadIdx.x & 31;
   const int bx = tx * TW + (warp & 1) * 8 * PW, by = ty * TH + (warp >> 1) * 4 * PH;
   const int lx = bx + (lane & 7) * PW, ly = by + (lane >> 3) * PH;
@@ -127,171 +126,155 @@ __global__ void __launch_bounds__(256, (PW * PH >= 4 && B >= 256) ? 2 : 4) k_ren
     lane_max = max(lane_max, last[p]);
   }
   const uint32_t warp_max = __reduce_max_sync(0xffffffffu, lane_max);
-  if (threadIdx.x == 0) s_top = 0;
-  __syncthreads();
-  if (lane == 0) atomicMax(&s_top, warp_max);
-  __syncthreads();
-  const uint32_t top = s_top;
 
   const uint2 range = ws_ptr<uint2>(ws, P.ws_off_ranges)[tile];
-  const uint32_t* vals = ws_ptr<uint32_t>(ws, P.ws_off_pval) + (size_t)P.pair_slot * P.pair_capacity;
+  const uint32_t* vals = ws_ptr<uint32_t>(ws, P.ws_off_pval) + (size_t)P.pair_slot * P.pair_capacity + range.x;
   const SplatRec* rec = ws_ptr<SplatRec>(ws, P.ws_off_rec);
   float* g2d = ws_ptr<float>(ws, P.ws_off_grad2d);
   const float tau = cfg.tau, amax = cfg.alpha_max;
 
   // list positions are relative to range.x; pixel p has contributors in
-  // [0, last[p]).  Batches run from the back: batch i covers positions
-  // [lo_i, hi_i) with hi_0 = top, lo_i = max(hi_i - B, 0).
-  const uint32_t n_batches = (top + B - 1) / B;
-  auto lo_of = [&](uint32_t i) { return top > (i + 1) * B ? top - (i + 1) * B : 0u; };
-  auto cnt_of = [&](uint32_t i) { return top - i * B - lo_of(i); };
-  Stager<B> stg;
+  // [0, last[p]).  The warp walks its own contributors back to front in
+  // batches of 32: batch i covers [lo_i, hi_i), hi_0 = warp_max (the
+  // deepest contributor of the warp's pixels), lo_i = max(hi_i - 32, 0);
+  // batch i + 1 is gathered and the entry ids of batch i + 2 are loaded
+  // while batch i is evaluated.
+  const uint32_t n_batches = (warp_max + 31) / 32;
+  auto lo_of = [&](uint32_t i) { return warp_max > (i + 1) * 32 ? warp_max - (i + 1) * 32 : 0u; };
   if (n_batches > 0) {
-    uint32_t e0[Stager<B>::kL];
-    stg.fetch_entries(vals, range.x + lo_of(0), cnt_of(0), e0);
-    stg.load_records(rec, e0);
-    if (n_batches > 1) stg.fetch_entries(vals, range.x + lo_of(1), cnt_of(1), stg.e_next);
-    stg.store(s_buf[0], s_ebuf[0], e0);
-  }
-  __syncthreads();
-  for (uint32_t i = 0; i < n_batches; ++i) {
-    const uint32_t lo = lo_of(i);
-    uint32_t e_after[Stager<B>::kL];
-    if (i + 1 < n_batches) {
-      stg.load_records(rec, stg.e_next);
-      if (i + 2 < n_batches) stg.fetch_entries(vals, range.x + lo_of(i + 2), cnt_of(i + 2), e_after);
+    uint32_t lo = lo_of(0);
+    uint32_t e_next = lo + lane < warp_max ? __ldg(vals + lo + lane) : 0u;
+    warp_stage(S, 0, rec, e_next, lo + lane < warp_max, lane);
+    if (n_batches > 1) {
+      const uint32_t lo1 = lo_of(1);
+      e_next = lo1 + lane < lo ? __ldg(vals + lo1 + lane) : 0u;
     }
-    const float4* s_a = s_buf[i & 1];
-    const float4* s_b = s_a + B;
-    const float4* s_c = s_a + 2 * B;
-    const uint32_t* s_e = s_ebuf[i & 1];
-    if (lo < warp_max) {
-      unsigned mask[NW];
-#pragma unroll
-      for (int k = 0; k < NW; ++k) {
-        const float4 a = s_a[k * 32 + lane], b = s_b[k * 32 + lane];
+    for (uint32_t i = 0; i < n_batches; ++i) {
+      lo = lo_of(i);
+      const int k = (int)(i & 1);
+      if (i + 1 < n_batches) {
+        const uint32_t lo1 = lo_of(i + 1);
+        warp_stage(S, k ^ 1, rec, e_next, lo1 + lane < lo, lane);
+        e_next = 0u;
+        if (i + 2 < n_batches) {
+          const uint32_t lo2 = lo_of(i + 2);
+          if (lo2 + lane < lo1) e_next = __ldg(vals + lo2 + lane);
+        }
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncwarp();
+      unsigned m;
+      {
+        const float4 a = S.a[k][lane], b = S.b[k][lane];
         int ox, oy;
-        rec_origin(s_c[k * 32 + lane].w, ox, oy);
-        const bool hit = b.z >= 0.0f && (lo + k * 32 + lane) < warp_max &&
+        rec_origin(S.c[k][lane].w, ox, oy);
+        const bool hit = b.z >= 0.0f &&
                          ellipse_hits_box(a.x, a.y, a.z, a.w, b.x, fmaf(b.z, 2.0f * kHPad, b.z) + 1e-3f,
                                           (float)(bx - ox) + 0.5f, (float)(bx - ox + 8 * PW) - 0.5f,
                                           (float)(by - oy) + 0.5f, (float)(by - oy + 4 * PH) - 0.5f);
-        mask[k] = __ballot_sync(0xffffffffu, hit);
+        m = __ballot_sync(0xffffffffu, hit);
       }
+      while (m) {
+        const int si = 31 - __clz(m);
+        m &= ~(1u << si);
+        const uint32_t pos = lo + si;
+      const float4 a = S.a[k][si], b = S.b[k][si], c = S.c[k][si];
+      const float cb2 = 2.0f * a.w, hpre = fmaf(b.z, kHPad, b.z);
+      const float nu = b.w, inv_nu = __fdividef(1.0f, nu), o = b.y;
+      int ox, oy;
+      rec_origin(c.w, ox, oy);
+      const float fbx = (float)(lx - ox), fby = (float)(ly - oy);
+      // dT/dh = -(nu+2)/(2 nu) T / (1 + h/nu); -1/2 T for the Gaussian (nu = inf, inv_nu = 0)
+      const float e_over_nu = isinf(nu) ? -0.5f : fmaf(nu, -0.5f, -1.0f) * inv_nu;
+      // all pixels of the lane in straight-line code, masked; nu branch
+      // uniform over the warp
+      PairEval r[NPIX];
+      bool ok[NPIX];
+      float dxs[NPIX], dys[NPIX];
 #pragma unroll
-      for (int k = NW - 1; k >= 0; --k) {
-        unsigned m = mask[k];
-        while (m) {
-          const int bit = 31 - __clz(m);
-          m &= ~(1u << bit);
-          const int si = k * 32 + bit;
-          const uint32_t pos = lo + si;
-          const float4 a = s_a[si], b = s_b[si], c = s_c[si];
-          const float cb2 = 2.0f * a.w, hpre = fmaf(b.z, kHPad, b.z);
-          const float nu = b.w, inv_nu = __fdividef(1.0f, nu), o = b.y;
-          int ox, oy;
-          rec_origin(c.w, ox, oy);
-          const float fbx = (float)(lx - ox), fby = (float)(ly - oy);
-          // dT/dh = -(nu+2)/(2 nu) T / (1 + h/nu); -1/2 T for the Gaussian (nu = inf, inv_nu = 0)
-          const float e_over_nu = isinf(nu) ? -0.5f : fmaf(nu, -0.5f, -1.0f) * inv_nu;
-          // all pixels of the lane in straight-line code, masked; nu branch
-          // uniform over the warp
-          PairEval r[NPIX];
-          bool ok[NPIX];
-          float dxs[NPIX], dys[NPIX];
-#pragma unroll
-          for (int p = 0; p < NPIX; ++p) {
-            dxs[p] = pixel_offset(fbx, p % PW, a.x);
-            dys[p] = pixel_offset(fby, p / PW, a.y);
-          }
-          if (nu <= kFastNuMax) {
-#pragma unroll
-            for (int p = 0; p < NPIX; ++p)
-              ok[p] = eval_pair_fast(dxs[p], dys[p], a.z, cb2, b.x, hpre, o, nu, inv_nu, tau, amax, r[p]);
-          } else if (isinf(nu)) {
-#pragma unroll
-            for (int p = 0; p < NPIX; ++p)
-              ok[p] = eval_pair_gauss(dxs[p], dys[p], a.z, cb2, b.x, hpre, o, tau, amax, r[p]);
-          } else {
-#pragma unroll
-            for (int p = 0; p < NPIX; ++p)
-              ok[p] = eval_pair_slow(dxs[p], dys[p], a.z, cb2, b.x, hpre, o, nu, inv_nu, tau, amax, r[p]);
-          }
-          // per-lane sums: rgb (v7..9), opacity (v5), nu (v6) and the
-          // q-weighted moments of the pixel offsets, q = dL/dh, from which
-          // dL/dmean and dL/dconic follow once per splat (h is quadratic in
-          // the offsets, so its gradients are linear in these moments)
-          float v[10];
-#pragma unroll
-          for (int q = 0; q < 10; ++q) v[q] = 0.0f;
-          float m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f, m5 = 0.0f;
-          bool any = false;
-#pragma unroll
-          for (int p = 0; p < NPIX; ++p) {
-            const bool live = ok[p] && pos < last[p];
-            any = any || live;
-            const float alpha = r[p].alpha;
-            const float Tk = live ? T[p] * __fdividef(1.0f, 1.0f - alpha) : T[p];
-            T[p] = Tk;
-            const float w = live ? alpha * Tk : 0.0f;
-            v[7] = fmaf(w, g[p][0], v[7]);
-            v[8] = fmaf(w, g[p][1], v[8]);
-            v[9] = fmaf(w, g[p][2], v[9]);
-            // dL/dalpha = T_k dL/dC . (rgb - B) with B the colour behind; only
-            // its projection on dL/dC is needed: Sg = dL/dC . B, and
-            // B <- alpha rgb + (1 - alpha) B gives Sg <- Sg + alpha (g.rgb - Sg)
-            const float gdiff = fmaf(g[p][0], c.x, fmaf(g[p][1], c.y, g[p][2] * c.z)) - Sg[p];
-            Sg[p] = live ? fmaf(alpha, gdiff, Sg[p]) : Sg[p];
-            const float dl_da = (live && !r[p].clamped) ? gdiff * Tk : 0.0f;
-            v[5] = fmaf(dl_da, r[p].t2d, v[5]);
-            const float dl_dt = dl_da * o;
-            const float inv_base = __fdividef(1.0f, fmaf(r[p].h, inv_nu, 1.0f));
-            const float qh = dl_dt * e_over_nu * r[p].t2d * inv_base;  // dL/dh
-            const float u = r[p].h * inv_nu * inv_base;  // x / (1 + x)
-            // paper form: (nu+2) x / (2 nu (1+x)) = u/2 + u/nu; exact: u/nu - g/2
-            const float dnu = PAPER_NU ? fmaf(0.5f, u, u * inv_nu)
-                                       : fmaf(-0.5f, log1p_minus_u(u, r[p].log_base), u * inv_nu);
-            v[6] = fmaf(dl_dt * r[p].t2d, dnu, v[6]);
-            const float qdx = qh * dxs[p], qdy = qh * dys[p];
-            m1 += qdx;
-            m2 += qdy;
-            m3 = fmaf(qdx, dxs[p], m3);
-            m4 = fmaf(qdx, dys[p], m4);
-            m5 = fmaf(qdy, dys[p], m5);
-          }
-          // dh/dmean = -2 (a dx + b dy, b dx + c dy); dh/dconic = (dx^2, 2 dx dy, dy^2)
-          v[0] = -2.0f * fmaf(a.z, m1, a.w * m2);
-          v[1] = -2.0f * fmaf(a.w, m1, b.x * m2);
-          v[2] = m3;
-          v[3] = 2.0f * m4;
-          v[4] = m5;
-          if (__any_sync(0xffffffffu, any)) {
-            int slot;
-            const float tot = warp_reduce_scatter10(v, lane, &slot);
-            if (slot >= 0) atomicAdd(g2d + (size_t)s_e[si] * 12 + slot, tot);
-          }
-        }
+      for (int p = 0; p < NPIX; ++p) {
+        dxs[p] = pixel_offset(fbx, p % PW, a.x);
+        dys[p] = pixel_offset(fby, p / PW, a.y);
       }
-    }
-    if (i + 1 < n_batches) {
-      stg.store(s_buf[(i + 1) & 1], s_ebuf[(i + 1) & 1], stg.e_next);
+      if (nu <= kFastNuMax) {
 #pragma unroll
-      for (int l = 0; l < Stager<B>::kL; ++l) stg.e_next[l] = e_after[l];
+        for (int p = 0; p < NPIX; ++p)
+          ok[p] = eval_pair_fast(dxs[p], dys[p], a.z, cb2, b.x, hpre, o, nu, inv_nu, tau, amax, r[p]);
+      } else if (isinf(nu)) {
+#pragma unroll
+        for (int p = 0; p < NPIX; ++p)
+          ok[p] = eval_pair_gauss(dxs[p], dys[p], a.z, cb2, b.x, hpre, o, tau, amax, r[p]);
+      } else {
+#pragma unroll
+        for (int p = 0; p < NPIX; ++p)
+          ok[p] = eval_pair_slow(dxs[p], dys[p], a.z, cb2, b.x, hpre, o, nu, inv_nu, tau, amax, r[p]);
+      }
+      // per-lane sums: rgb (v7..9), opacity (v5), nu (v6) and the
+      // q-weighted moments of the pixel offsets, q = dL/dh, from which
+      // dL/dmean and dL/dconic follow once per splat (h is quadratic in
+      // the offsets, so its gradients are linear in these moments)
+      float v[10];
+#pragma unroll
+      for (int q = 0; q < 10; ++q) v[q] = 0.0f;
+      float m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f, m5 = 0.0f;
+      bool any = false;
+#pragma unroll
+      for (int p = 0; p < NPIX; ++p) {
+        const bool live = ok[p] && pos < last[p];
+        any = any || live;
+        const float alpha = r[p].alpha;
+        const float Tk = live ? T[p] * __fdividef(1.0f, 1.0f - alpha) : T[p];
+        T[p] = Tk;
+        const float w = live ? alpha * Tk : 0.0f;
+        v[7] = fmaf(w, g[p][0], v[7]);
+        v[8] = fmaf(w, g[p][1], v[8]);
+        v[9] = fmaf(w, g[p][2], v[9]);
+        // dL/dalpha = T_k dL/dC . (rgb - B) with B the colour behind; only
+        // its projection on dL/dC is needed: Sg = dL/dC . B, and
+        // B <- alpha rgb + (1 - alpha) B gives Sg <- Sg + alpha (g.rgb - Sg)
+        const float gdiff = fmaf(g[p][0], c.x, fmaf(g[p][1], c.y, g[p][2] * c.z)) - Sg[p];
+        Sg[p] = live ? fmaf(alpha, gdiff, Sg[p]) : Sg[p];
+        const float dl_da = (live && !r[p].clamped) ? gdiff * Tk : 0.0f;
+        v[5] = fmaf(dl_da, r[p].t2d, v[5]);
+        const float dl_dt = dl_da * o;
+        const float inv_base = __fdividef(1.0f, fmaf(r[p].h, inv_nu, 1.0f));
+        const float qh = dl_dt * e_over_nu * r[p].t2d * inv_base;  // dL/dh
+        const float u = r[p].h * inv_nu * inv_base;  // x / (1 + x)
+        // paper form: (nu+2) x / (2 nu (1+x)) = u/2 + u/nu; exact: u/nu - g/2
+        const float dnu = PAPER_NU ? fmaf(0.5f, u, u * inv_nu)
+                                   : fmaf(-0.5f, log1p_minus_u(u, r[p].log_base), u * inv_nu);
+        v[6] = fmaf(dl_dt * r[p].t2d, dnu, v[6]);
+        const float qdx = qh * dxs[p], qdy = qh * dys[p];
+        m1 += qdx;
+        m2 += qdy;
+        m3 = fmaf(qdx, dxs[p], m3);
+        m4 = fmaf(qdx, dys[p], m4);
+        m5 = fmaf(qdy, dys[p], m5);
+      }
+      // dh/dmean = -2 (a dx + b dy, b dx + c dy); dh/dconic = (dx^2, 2 dx dy, dy^2)
+      v[0] = -2.0f * fmaf(a.z, m1, a.w * m2);
+      v[1] = -2.0f * fmaf(a.w, m1, b.x * m2);
+      v[2] = m3;
+      v[3] = 2.0f * m4;
+      v[4] = m5;
+      if (__any_sync(0xffffffffu, any)) {
+        int slot;
+        const float tot = warp_reduce_scatter10(v, lane, &slot);
+        if (slot >= 0) atomicAdd(g2d + (size_t)S.e[k][si] * 12 + slot, tot);
+      }
+      }
+      __syncwarp();  // every lane is done with buffer k before it is refilled
     }
-    __syncthreads();
+    cp_async_wait<0>();
   }
 }
 
 template <int PW, int PH, bool PAPER_NU>
 int launch_batch(const sss_frame_plan& P, void* ws, const float* g, cudaStream_t st) {
-  const unsigned grid = P.n_tiles;
-  switch (P.cfg.batch) {
-    case 32: k_render_bwd<PW, PH, 32, PAPER_NU><<<grid, 256, 0, st>>>(P, ws, g); break;
-    case 64: k_render_bwd<PW, PH, 64, PAPER_NU><<<grid, 256, 0, st>>>(P, ws, g); break;
-    case 128: k_render_bwd<PW, PH, 128, PAPER_NU><<<grid, 256, 0, st>>>(P, ws, g); break;
-    case 256: k_render_bwd<PW, PH, 256, PAPER_NU><<<grid, 256, 0, st>>>(P, ws, g); break;
-    default: return SSS_ERR_UNSUPPORTED;
-  }
+  // 32 records per warp and batch whatever cfg.batch says (checked by the plan)
+  k_render_bwd<PW, PH, PAPER_NU><<<4 * P.n_tiles, 64, 0, st>>>(P, ws, g);
   SSS_LAUNCH_CHECK();
   return SSS_OK;
 }

@@ -16,20 +16,21 @@
 namespace sss {
 namespace {
 
-template <int PW, int PH, int B>
-__global__ void __launch_bounds__(256) k_render_fwd(const sss_frame_plan P, void* ws, float* __restrict__ out_rgb) {
+template <int PW, int PH>
+__global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, void* ws, float* __restrict__ out_rgb) {
   constexpr int NPIX = PW * PH;
   constexpr int TW = 16 * PW, TH = 16 * PH;
-  constexpr int NW = B / 32;
-  __shared__ float4 s_buf[2][3 * B];
+  __shared__ WarpBuf s_wb[2];
 
-  const uint32_t tile = blockIdx.x;
+  // four CTAs of two warps per tile; warp w of the tile's 2 x 4 layout
+  const uint32_t tile = blockIdx.x >> 2;
+  const int warp = (int)((blockIdx.x & 3u) << 1) | (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+  WarpBuf& S = s_wb[threadIdx.x >> 5];
   const int j = job_of_tile(P, tile);
   const sss_job_desc& J = P.jobs[j];
   const sss_raster_cfg& cfg = P.cfg;
   const uint32_t lt = tile - J.tile_base;
   const int tx = (int)(lt % (uint32_t)J.tiles_x), ty = (int)(lt / (uint32_t)J.tiles_x);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int bx = tx * TW + (warp & 1) * 8 * PW, by = ty * TH + (warp >> 1) * 4 * PH;
   const int lx = bx + (lane & 7) * PW, ly = by + (lane >> 3) * PH;
   const int W = J.cam.width, H = J.cam.height;
@@ -51,111 +52,96 @@ __global__ void __launch_bounds__(256) k_render_fwd(const sss_frame_plan P, void
   bool warp_done = __all_sync(0xffffffffu, lane_done);
 
   const uint2 range = ws_ptr<uint2>(ws, P.ws_off_ranges)[tile];
-  const uint32_t* vals = ws_ptr<uint32_t>(ws, P.ws_off_pval) + (size_t)P.pair_slot * P.pair_capacity;
+  const uint32_t* vals = ws_ptr<uint32_t>(ws, P.ws_off_pval) + (size_t)P.pair_slot * P.pair_capacity + range.x;
   const SplatRec* rec = ws_ptr<SplatRec>(ws, P.ws_off_rec);
   const float tau = cfg.tau, amax = cfg.alpha_max, tmin = cfg.t_min;
   uint32_t n_eval = 0, n_contrib = 0;  // pair counters for the roofline
 
   const uint32_t n_list = range.y - range.x;
-  const uint32_t n_batches = (n_list + B - 1) / B;
-  Stager<B> stg;
-  if (n_batches > 0) {
-    uint32_t e0[Stager<B>::kL];
-    stg.fetch_entries(vals, range.x, min((uint32_t)B, n_list), e0);
-    stg.load_records(rec, e0);
-    if (n_batches > 1) stg.fetch_entries(vals, range.x + B, min((uint32_t)B, n_list - B), stg.e_next);
-    stg.store(s_buf[0], nullptr, e0);
-  }
-  __syncthreads();
-  for (uint32_t i = 0; i < n_batches; ++i) {
-    const uint32_t b0 = range.x + i * B;
-    // records of batch i+1 and entry ids of batch i+2 go in flight now
-    uint32_t e_after[Stager<B>::kL];
-    if (i + 1 < n_batches) {
-      stg.load_records(rec, stg.e_next);
-      if (i + 2 < n_batches) stg.fetch_entries(vals, b0 + 2 * B, min((uint32_t)B, range.y - (b0 + 2 * B)), e_after);
-    }
-    const float4* s_a = s_buf[i & 1];
-    const float4* s_b = s_a + B;
-    const float4* s_c = s_a + 2 * B;
-    if (!warp_done) {
-      unsigned mask[NW];
-#pragma unroll
-      for (int k = 0; k < NW; ++k) {
-        const float4 a = s_a[k * 32 + lane], b = s_b[k * 32 + lane];
+  const uint32_t n_batches = (n_list + 31) / 32;
+  if (!warp_done && n_batches > 0) {
+    // batch i = list positions [32 i, 32 i + 32); batch i + 1 is gathered and
+    // the entry ids of batch i + 2 are loaded while batch i is evaluated
+    uint32_t e_next = lane < n_list ? __ldg(vals + lane) : 0u;
+    warp_stage(S, 0, rec, e_next, lane < n_list, lane);
+    if (n_batches > 1) e_next = 32 + lane < n_list ? __ldg(vals + 32 + lane) : 0u;
+    for (uint32_t i = 0; i < n_batches && !warp_done; ++i) {
+      const uint32_t p0 = i * 32;
+      const int k = (int)(i & 1);
+      if (i + 1 < n_batches) {
+        warp_stage(S, k ^ 1, rec, e_next, p0 + 32 + lane < n_list, lane);
+        const uint32_t q = p0 + 64 + lane;
+        e_next = (i + 2 < n_batches && q < n_list) ? __ldg(vals + q) : 0u;
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncwarp();
+      unsigned m;
+      {
+        const float4 a = S.a[k][lane], b = S.b[k][lane];
         int ox, oy;
-        rec_origin(s_c[k * 32 + lane].w, ox, oy);
+        rec_origin(S.c[k][lane].w, ox, oy);
         const bool hit = b.z >= 0.0f &&
                          ellipse_hits_box(a.x, a.y, a.z, a.w, b.x, fmaf(b.z, 2.0f * kHPad, b.z) + 1e-3f,
                                           (float)(bx - ox) + 0.5f, (float)(bx - ox + 8 * PW) - 0.5f,
                                           (float)(by - oy) + 0.5f, (float)(by - oy + 4 * PH) - 0.5f);
-        mask[k] = __ballot_sync(0xffffffffu, hit);
+        m = __ballot_sync(0xffffffffu, hit);
+      }
+      while (m && !warp_done) {
+        const int si = __ffs(m) - 1;
+        m &= m - 1;
+      const float4 a = S.a[k][si], b = S.b[k][si], c = S.c[k][si];
+      const float cb2 = 2.0f * a.w, hpre = fmaf(b.z, kHPad, b.z), inv_nu = __fdividef(1.0f, b.w);
+      int ox, oy;
+      rec_origin(c.w, ox, oy);
+      const float fbx = (float)(lx - ox), fby = (float)(ly - oy);
+      const uint32_t pos1 = p0 + si + 1;
+      // every pixel of the lane through the same straight-line code (no
+      // branches between pixels, so their chains interleave); the nu
+      // branch is uniform over the warp
+      PairEval r[NPIX];
+      bool ok[NPIX];
+      if (b.w <= kFastNuMax) {
+#pragma unroll
+        for (int p = 0; p < NPIX; ++p)
+          ok[p] = eval_pair_fast(pixel_offset(fbx, p % PW, a.x), pixel_offset(fby, p / PW, a.y), a.z, cb2,
+                                 b.x, hpre, b.y, b.w, inv_nu, tau, amax, r[p]);
+      } else if (isinf(b.w)) {
+#pragma unroll
+        for (int p = 0; p < NPIX; ++p)
+          ok[p] = eval_pair_gauss(pixel_offset(fbx, p % PW, a.x), pixel_offset(fby, p / PW, a.y), a.z, cb2,
+                                  b.x, hpre, b.y, tau, amax, r[p]);
+      } else {
+#pragma unroll
+        for (int p = 0; p < NPIX; ++p)
+          ok[p] = eval_pair(pixel_offset(fbx, p % PW, a.x), pixel_offset(fby, p / PW, a.y), a.z, cb2, b.x,
+                            hpre, b.y, b.w, inv_nu, tau, amax, r[p]);
       }
 #pragma unroll
-      for (int k = 0; k < NW; ++k) {
-        unsigned m = mask[k];
-        while (m && !warp_done) {
-          const int bit = __ffs(m) - 1;
-          m &= m - 1;
-          const int si = k * 32 + bit;
-          const float4 a = s_a[si], b = s_b[si], c = s_c[si];
-          const float cb2 = 2.0f * a.w, hpre = fmaf(b.z, kHPad, b.z), inv_nu = __fdividef(1.0f, b.w);
-          int ox, oy;
-          rec_origin(c.w, ox, oy);
-          const float fbx = (float)(lx - ox), fby = (float)(ly - oy);
-          const uint32_t pos1 = b0 + si - range.x + 1;
-          // every pixel of the lane through the same straight-line code (no
-          // branches between pixels, so their chains interleave); the nu
-          // branch is uniform over the warp
-          PairEval r[NPIX];
-          bool ok[NPIX];
-          if (b.w <= kFastNuMax) {
-#pragma unroll
-            for (int p = 0; p < NPIX; ++p)
-              ok[p] = eval_pair_fast(pixel_offset(fbx, p % PW, a.x), pixel_offset(fby, p / PW, a.y), a.z, cb2,
-                                     b.x, hpre, b.y, b.w, inv_nu, tau, amax, r[p]);
-          } else if (isinf(b.w)) {
-#pragma unroll
-            for (int p = 0; p < NPIX; ++p)
-              ok[p] = eval_pair_gauss(pixel_offset(fbx, p % PW, a.x), pixel_offset(fby, p / PW, a.y), a.z, cb2,
-                                      b.x, hpre, b.y, tau, amax, r[p]);
-          } else {
-#pragma unroll
-            for (int p = 0; p < NPIX; ++p)
-              ok[p] = eval_pair(pixel_offset(fbx, p % PW, a.x), pixel_offset(fby, p / PW, a.y), a.z, cb2, b.x,
-                                hpre, b.y, b.w, inv_nu, tau, amax, r[p]);
-          }
-#pragma unroll
-          for (int p = 0; p < NPIX; ++p) {
-            n_eval += done[p] ? 0u : 1u;
-            const bool live = ok[p] && !done[p];
-            const float Tn = T[p] * (1.0f - r[p].alpha);
-            const bool term = live && Tn < tmin;  // stops before this splat
-            const bool add = live && !term;
-            const float w = add ? r[p].alpha * T[p] : 0.0f;
-            C[p][0] = fmaf(w, c.x, C[p][0]);
-            C[p][1] = fmaf(w, c.y, C[p][1]);
-            C[p][2] = fmaf(w, c.z, C[p][2]);
-            T[p] = add ? Tn : T[p];
-            last[p] = add ? pos1 : last[p];
-            done[p] = done[p] || term;
-            n_contrib += add ? 1u : 0u;
-          }
-          bool ld = true;
-#pragma unroll
-          for (int p = 0; p < NPIX; ++p) ld = ld && done[p];
-          warp_done = __all_sync(0xffffffffu, ld);
-        }
+      for (int p = 0; p < NPIX; ++p) {
+        n_eval += done[p] ? 0u : 1u;
+        const bool live = ok[p] && !done[p];
+        const float Tn = T[p] * (1.0f - r[p].alpha);
+        const bool term = live && Tn < tmin;  // stops before this splat
+        const bool add = live && !term;
+        const float w = add ? r[p].alpha * T[p] : 0.0f;
+        C[p][0] = fmaf(w, c.x, C[p][0]);
+        C[p][1] = fmaf(w, c.y, C[p][1]);
+        C[p][2] = fmaf(w, c.z, C[p][2]);
+        T[p] = add ? Tn : T[p];
+        last[p] = add ? pos1 : last[p];
+        done[p] = done[p] || term;
+        n_contrib += add ? 1u : 0u;
       }
-    }
-    if (i + 1 < n_batches) {
-      stg.store(s_buf[(i + 1) & 1], nullptr, stg.e_next);
+      bool ld = true;
 #pragma unroll
-      for (int l = 0; l < Stager<B>::kL; ++l) stg.e_next[l] = e_after[l];
+      for (int p = 0; p < NPIX; ++p) ld = ld && done[p];
+      warp_done = __all_sync(0xffffffffu, ld);
+      }
+      __syncwarp();  // every lane is done with buffer k before it is refilled
     }
-    // one barrier per batch: the next buffer is complete and every warp is
-    // done with this one; also the CTA-wide early exit
-    if (__syncthreads_count(!warp_done) == 0) break;
+    cp_async_wait<0>();  // no copy into this warp's buffers outlives the loop
   }
 
   {
@@ -186,14 +172,9 @@ __global__ void __launch_bounds__(256) k_render_fwd(const sss_frame_plan P, void
 
 template <int PW, int PH>
 int launch_batch(const sss_frame_plan& P, void* ws, float* out, cudaStream_t st) {
-  const unsigned grid = P.n_tiles;
-  switch (P.cfg.batch) {
-    case 32: k_render_fwd<PW, PH, 32><<<grid, 256, 0, st>>>(P, ws, out); break;
-    case 64: k_render_fwd<PW, PH, 64><<<grid, 256, 0, st>>>(P, ws, out); break;
-    case 128: k_render_fwd<PW, PH, 128><<<grid, 256, 0, st>>>(P, ws, out); break;
-    case 256: k_render_fwd<PW, PH, 256><<<grid, 256, 0, st>>>(P, ws, out); break;
-    default: return SSS_ERR_UNSUPPORTED;
-  }
+  // the staging batch is 32 records per warp whatever cfg.batch says (the
+  // plan has already checked it is one of the accepted values)
+  k_render_fwd<PW, PH><<<4 * P.n_tiles, 64, 0, st>>>(P, ws, out);
   SSS_LAUNCH_CHECK();
   return SSS_OK;
 }
