@@ -107,8 +107,9 @@ typedef struct sss_camera {
 /* ------------------------------------------------------ raster options */
 typedef struct sss_raster_cfg {
   int32_t tile_w, tile_h; /* 16x16, 32x16, 16x32 or 32x32 pixels             */
-  int32_t batch;          /* splats staged in shared memory per round: 32,
-                             64, 128 or 256                                   */
+  int32_t batch;          /* records each warp stages in shared memory per
+                             round (double buffered, cp.async); 32, the only
+                             value built, one record per lane              */
   int32_t nu_grad_mode;   /* 0: exact dT/dnu (default); 1: the SM's printed
                              form, which omits -1/2 ln(1 + h/nu) T2D          */
   float tau;              /* alpha threshold, 1/255: a splat contributes to a

@@ -1,10 +1,12 @@
-"""Autotuner for the rasterizer's launch shape: tile size and staging batch.
+"""Autotuner for the rasterizer's launch shape: the tile size.
 
 For a workload it times the whole captured train step (``train.TrainStep``)
-for every (tile_w, tile_h, batch) candidate and keeps the fastest.  Tile size
+for every (tile_w, tile_h) candidate and keeps the fastest.  Tile size
 trades pair count (bigger tiles: fewer pairs to sort, fewer splat records
-gathered) against per-warp culling efficiency; the staging batch trades
-shared memory and barrier count against wasted staging past termination.
+gathered) against per-warp culling efficiency (each warp of a tile covers
+an eighth of it and skips the records whose ellipse misses its block).
+The render kernels stage 32 records per warp and round, one per lane, so
+the staging batch is fixed and not a candidate.
 
 Results are stored per workload name in ``tuned.json`` next to this file;
 ``cached(name)`` returns the stored choice or None.
@@ -18,7 +20,6 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "tuned.json")
 
 TILES = ((16, 16), (32, 16), (16, 32), (32, 32))
-BATCHES = (32, 64, 128, 256)
 
 
 def cached(name: str) -> dict | None:
@@ -42,21 +43,24 @@ def store(name: str, choice: dict, path: str = CACHE):
 
 
 def tune(name: str, scene, cams, targets, candidates=None, steps: int = 5, device="cuda", log=print,
-         path: str = CACHE) -> dict:
-    """Times each candidate's captured step and stores the fastest."""
+         path: str = CACHE, step_kw: dict | None = None) -> dict:
+    """Times each candidate's captured step and stores the fastest.
+    ``step_kw`` are the ``train.TrainStep`` options of the step to tune
+    (loss, regularisers, restart)."""
     import torch
 
     from . import frame as F
     from . import train
 
-    candidates = candidates or [(tw, th, b) for (tw, th) in TILES for b in BATCHES]
+    candidates = candidates or list(TILES)
     snapshot = {f: scene.t[f].clone() for f in F.FIELDS}
     results = []
-    for tw, th, b in candidates:
-        for f in F.FIELDS:  # every candidate starts from the same parameters
-            scene.t[f].copy_(snapshot[f])
-        cfg = F.make_cfg(tile_w=tw, tile_h=th, batch=b)
-        ts = train.TrainStep(scene, cams, targets, cfg=cfg, device=device)
+    for tw, th in candidates:
+        with torch.no_grad():  # every candidate starts from the same parameters
+            for f in F.FIELDS:
+                scene.t[f].copy_(snapshot[f])
+        cfg = F.make_cfg(tile_w=tw, tile_h=th)
+        ts = train.TrainStep(scene, cams, targets, cfg=cfg, device=device, **(step_kw or {}))
         ts.calibrate()
         ts.capture()
         ts.replay()
@@ -69,14 +73,15 @@ def tune(name: str, scene, cams, targets, candidates=None, steps: int = 5, devic
         torch.cuda.synchronize(device)
         ms = e0.elapsed_time(e1) / steps
         ts.check()
-        results.append((ms, tw, th, b))
-        log(f"autotune {name}: tile {tw}x{th} batch {b}: {ms:.3f} ms/step")
+        results.append((ms, tw, th))
+        log(f"autotune {name}: tile {tw}x{th}: {ms:.3f} ms/step")
         del ts
         torch.cuda.empty_cache()
-    for f in F.FIELDS:
-        scene.t[f].copy_(snapshot[f])
-    ms, tw, th, b = min(results)
-    choice = {"tile_w": tw, "tile_h": th, "batch": b, "ms_per_step": round(ms, 3),
-              "candidates": {f"{a}x{c}/{d}": round(m, 3) for m, a, c, d in results}}
+    with torch.no_grad():
+        for f in F.FIELDS:
+            scene.t[f].copy_(snapshot[f])
+    ms, tw, th = min(results)
+    choice = {"tile_w": tw, "tile_h": th, "ms_per_step": round(ms, 3),
+              "candidates": {f"{a}x{c}": round(m, 3) for m, a, c in results}}
     store(name, choice, path)
     return choice

@@ -10,7 +10,7 @@ namespace {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 bool tile_ok(int w, int h) { return (w == 16 || w == 32) && (h == 16 || h == 32); }
-bool batch_ok(int b) { return b == 32 || b == 64 || b == 128 || b == 256; }
+bool batch_ok(int b) { return b == 32; }
 
 }  // namespace
 
@@ -23,7 +23,7 @@ void sss_default_cfg(sss_raster_cfg* cfg) {
   std::memset(cfg, 0, sizeof(*cfg));
   cfg->tile_w = 16;
   cfg->tile_h = 16;
-  cfg->batch = 128;
+  cfg->batch = 32;
   cfg->nu_grad_mode = 0;
   cfg->tau = 1.0f / 255.0f;
   cfg->t_min = 1e-4f;

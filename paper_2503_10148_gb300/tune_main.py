@@ -25,7 +25,11 @@ def main():
     scene = F.Scene.from_numpy(scene_np, dev)
     targets = torch.as_tensor(np.concatenate([t.reshape(-1) for t in inputs.target_images(cams, seed=3)]),
                               device=dev)
-    choice = autotune.tune(args.workload, scene, cams, targets, steps=args.steps, device=dev, path=args.out)
+    # the step bench.py times: 0.8 L1 + 0.2 D-SSIM, opacity and scale
+    # regularisers, every step from the configured scene
+    step_kw = dict(loss="full", eps_dssim=0.2, reg_opacity=0.01, reg_scale=0.01, restart=True)
+    choice = autotune.tune(args.workload, scene, cams, targets, steps=args.steps, device=dev, path=args.out,
+                           step_kw=step_kw)
     print(choice)
 
 

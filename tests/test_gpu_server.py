@@ -23,7 +23,7 @@ def test_batched_frame_equals_single_frames(scenes):
     reqs = server.poisson_requests(3, rate=50.0, duration=1.0, seed=7,
                                    resolutions=((64, 48), (200, 120), (256, 256), (97, 131)))[:12]
     assert len({r.scene for r in reqs}) == 3 and len({r.pixels for r in reqs}) > 2
-    cfg = frame.make_cfg(tile_w=32, tile_h=32, batch=64)
+    cfg = frame.make_cfg(tile_w=32, tile_h=32)
     used = sorted({r.scene for r in reqs})
     fr = frame.Frame([scenes[s] for s in used], [r.cam for r in reqs], [used.index(r.scene) for r in reqs], cfg=cfg,
                      device=DEV)
@@ -37,7 +37,7 @@ def test_batched_frame_equals_single_frames(scenes):
 
 
 def test_server_completes_every_request(scenes):
-    cfg = frame.make_cfg(tile_w=32, tile_h=32, batch=64)
+    cfg = frame.make_cfg(tile_w=32, tile_h=32)
     reqs = server.poisson_requests(3, rate=80.0, duration=1.5, seed=8,
                                    resolutions=((128, 128), (320, 240), (640, 360)))
     srv = server.RenderServer(scenes, cfg, hbm_budget_bytes=1 << 30, device=DEV)
@@ -53,7 +53,7 @@ def test_server_batches_a_burst_within_its_budget(scenes):
     """Requests that all arrive at once are rendered in fewer frames than
     requests, each frame within the arena (admission by HBM budget)."""
     import dataclasses
-    cfg = frame.make_cfg(tile_w=32, tile_h=32, batch=64)
+    cfg = frame.make_cfg(tile_w=32, tile_h=32)
     reqs = server.poisson_requests(3, rate=200.0, duration=0.5, seed=9,
                                    resolutions=((128, 128), (320, 240), (640, 360)))
     burst = [dataclasses.replace(r, arrival=0.0) for r in reqs]
