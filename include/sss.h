@@ -130,6 +130,10 @@ typedef struct sss_raster_cfg {
                              nu -> infinity, T2D = exp(-h/2) with extent
                              h <= 2 ln(|o|/tau) and no nu gradient (the
                              paper's "SGHMC + 3DGS" ablation kernel)          */
+  int32_t count_pairs;    /* 0 (default): no counting; 1: the forward also
+                             counts evaluated and contributing (splat,
+                             pixel) pairs into ctrl[4..7] (a diagnostic for
+                             work figures; costs a few % of the forward)     */
 } sss_raster_cfg;
 
 /* Fills *cfg with the defaults quoted above. */
@@ -197,8 +201,8 @@ typedef struct sss_frame_plan {
   size_t ws_off_ctrl;    /* uint32[16]: [0] pairs needed, [1] pairs sorted,
                             [2] status bits, [3] entries, [4..5] uint64
                             contributing (splat, pixel) pairs and [6..7]
-                            uint64 evaluated pairs of the last forward;
-                            reset by sss_bin                                */
+                            uint64 evaluated pairs of the forwards run with
+                            cfg.count_pairs = 1; reset by sss_bin          */
   int32_t sort_blocks;   /* persistent CTAs used by the sorts and scans     */
   uint32_t pair_slot;    /* which half of pkey/pval holds the sorted pairs  */
 } sss_frame_plan;

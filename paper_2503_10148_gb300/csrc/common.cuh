@@ -10,7 +10,7 @@ namespace sss {
 
 constexpr int kNumSMs = 152;          // GB300: 2 dies x 76 SMs
 constexpr float kFastNuMax = 64.0f;   // above this nu the log/exp pair runs on
-                                      // the accurate path (see eval_pair)
+                                      // the accurate path (eval_pair_slow)
 
 // ------------------------------------------------------------ workspace
 template <typename T>
@@ -90,10 +90,13 @@ __device__ __forceinline__ float mufu_ex2(float x) {
 
 // One (splat, pixel) evaluation shared by the forward and backward kernels so
 // that both take identical FP32 decisions.  Returns whether the pair
-// contributes (h within the padded extent and |alpha| >= tau); the fields of
-// r are computed either way (finite for any finite offsets, alpha already
-// clamped to [-alpha_max, alpha_max]), so callers can evaluate all their
-// pixels in straight-line code and mask.  Fast path: two MUFU ops (lg2,
+// contributes (|alpha| = |o| T2D >= tau; the tile lists hold only pairs the
+// screen extent h <= h_max may reach, and beyond h_max |alpha| < tau, so no
+// separate h test is needed); the fields of r are computed either way
+// (finite for any finite offsets, alpha already clamped to
+// [-alpha_max, alpha_max]), so callers can evaluate all their pixels in
+// straight-line code and mask.  The opacity comes split per splat as
+// |o| and sign(o): |o| T2D is |o T2D| exactly, and the clamp is one min.  Fast path: two MUFU ops (lg2,
 // ex2).  For nu > kFastNuMax the exponent -(nu+2)/2 is large enough that the
 // absolute error of lg2.approx would show, so eval_pair_slow uses
 // log1pf/expf; callers pick the path per splat (uniform over a warp).
@@ -108,49 +111,41 @@ __device__ __forceinline__ float conic_h(float dx, float dy, float ca, float cb2
   return fmaf(dx, t, cc * dy * dy);
 }
 
-__device__ __forceinline__ bool finish_pair(float h, float t2d, float lb, float o, float hmax_pre, float tau,
+__device__ __forceinline__ bool finish_pair(float h, float t2d, float lb, float oabs, float osgn, float tau,
                                             float amax, PairEval& r) {
-  const float alpha = o * t2d;
-  const bool ok = (h <= hmax_pre) && (fabsf(alpha) >= tau);
+  const float aabs = oabs * t2d;
   r.h = h;
   r.t2d = t2d;
-  r.alpha = fminf(fmaxf(alpha, -amax), amax);
+  r.alpha = osgn * fminf(aabs, amax);
   r.log_base = lb;
-  r.clamped = fabsf(alpha) > amax;
-  return ok;
+  r.clamped = aabs > amax;
+  return aabs >= tau;
 }
 
-__device__ __forceinline__ bool eval_pair_fast(float dx, float dy, float ca, float cb2, float cc, float hmax_pre,
-                                               float o, float nu, float inv_nu, float tau, float amax,
+__device__ __forceinline__ bool eval_pair_fast(float dx, float dy, float ca, float cb2, float cc, float oabs,
+                                               float osgn, float nu, float inv_nu, float tau, float amax,
                                                PairEval& r) {
   const float h = conic_h(dx, dy, ca, cb2, cc);
   const float e = fmaf(nu, -0.5f, -1.0f);  // -(nu + 2) / 2
   const float l2 = mufu_lg2(fmaf(h, inv_nu, 1.0f));
-  return finish_pair(h, mufu_ex2(e * l2), l2 * 0.69314718055994531f, o, hmax_pre, tau, amax, r);
+  return finish_pair(h, mufu_ex2(e * l2), l2 * 0.69314718055994531f, oabs, osgn, tau, amax, r);
 }
 
-__device__ __forceinline__ bool eval_pair_slow(float dx, float dy, float ca, float cb2, float cc, float hmax_pre,
-                                               float o, float nu, float inv_nu, float tau, float amax,
+__device__ __forceinline__ bool eval_pair_slow(float dx, float dy, float ca, float cb2, float cc, float oabs,
+                                               float osgn, float nu, float inv_nu, float tau, float amax,
                                                PairEval& r) {
   const float h = conic_h(dx, dy, ca, cb2, cc);
   const float e = fmaf(nu, -0.5f, -1.0f);
   const float lb = log1pf(h * inv_nu);
-  return finish_pair(h, expf(e * lb), lb, o, hmax_pre, tau, amax, r);
+  return finish_pair(h, expf(e * lb), lb, oabs, osgn, tau, amax, r);
 }
 
 // Gaussian kernel (the nu -> infinity limit; records carry nu = +inf):
 // T2D = exp(-h/2) = 2^(-h log2(e) / 2), one MUFU op.
-__device__ __forceinline__ bool eval_pair_gauss(float dx, float dy, float ca, float cb2, float cc, float hmax_pre,
-                                                float o, float tau, float amax, PairEval& r) {
+__device__ __forceinline__ bool eval_pair_gauss(float dx, float dy, float ca, float cb2, float cc, float oabs,
+                                                float osgn, float tau, float amax, PairEval& r) {
   const float h = conic_h(dx, dy, ca, cb2, cc);
-  return finish_pair(h, mufu_ex2(h * -0.72134752044448170f), 0.0f, o, hmax_pre, tau, amax, r);
-}
-
-__device__ __forceinline__ bool eval_pair(float dx, float dy, float ca, float cb2, float cc, float hmax_pre,
-                                          float o, float nu, float inv_nu, float tau, float amax, PairEval& r) {
-  if (isinf(nu)) return eval_pair_gauss(dx, dy, ca, cb2, cc, hmax_pre, o, tau, amax, r);
-  return nu <= kFastNuMax ? eval_pair_fast(dx, dy, ca, cb2, cc, hmax_pre, o, nu, inv_nu, tau, amax, r)
-                          : eval_pair_slow(dx, dy, ca, cb2, cc, hmax_pre, o, nu, inv_nu, tau, amax, r);
+  return finish_pair(h, mufu_ex2(h * -0.72134752044448170f), 0.0f, oabs, osgn, tau, amax, r);
 }
 
 // Offset of a pixel centre from the splat mean along one axis: fb is the
@@ -186,10 +181,12 @@ __device__ __forceinline__ bool ellipse_hits_box(float mx, float my, float ca, f
   return hmin <= hmax_test;
 }
 
-// Margin of the per-pixel prefilter over h_max (relative).  Pairs with
-// h <= h_max (1 + kHPad) are evaluated exactly; the |alpha| >= tau test then
-// decides.  Pairs beyond it have |alpha| below tau by far more than the FP32
-// error of alpha.
+// Relative margin over h_max of the per-warp cull, which skips a splat when
+// its ellipse h <= h_max (1 + 2 kHPad) + 1e-3 misses the warp's block of
+// pixel centres.  Pixels beyond it have |alpha| below tau by far more than
+// the FP32 error of alpha (near |o| = tau, where h_max -> 0, the absolute
+// 1e-3 covers it), so the cull never drops a pair the |alpha| >= tau test
+// would keep.
 constexpr float kHPad = 1e-3f;
 
 __device__ __forceinline__ void rec_origin(float w, int& ox, int& oy) {
@@ -197,56 +194,6 @@ __device__ __forceinline__ void rec_origin(float w, int& ox, int& oy) {
   ox = (int)(o & 0xffffu);
   oy = (int)(o >> 16);
 }
-
-// ------------------------------------------------------------ staging
-// Double-buffered staging of B splat records (three float4 each) into shared
-// memory by all 256 threads of a CTA.  Thread t owns the (record, float4)
-// slots q = t + 256 l, l < kL: record q % B, component q / B.  The kernels
-// software-pipeline it: while batch i is processed from one buffer, the
-// records of batch i+1 are in registers (loads in flight) and the entry
-// indices of batch i+2 are being fetched, so the gather latency is not paid
-// at the CTA barrier.
-template <int B>
-struct Stager {
-  static constexpr int kL = (3 * B + 255) / 256;
-  uint32_t e_next[kL];  // entries of the batch whose records are loaded next
-  float4 v[kL];         // records in flight
-
-  // entry ids of list positions [base, base + cnt) owned by this thread
-  __device__ __forceinline__ void fetch_entries(const uint32_t* __restrict__ vals, uint32_t base, uint32_t cnt,
-                                                uint32_t (&e)[kL]) const {
-#pragma unroll
-    for (int l = 0; l < kL; ++l) {
-      const int q = threadIdx.x + 256 * l;
-      const uint32_t r = (uint32_t)(q % B);
-      e[l] = (q < 3 * B && r < cnt) ? __ldg(vals + base + r) : 0xffffffffu;
-    }
-  }
-  __device__ __forceinline__ void load_records(const SplatRec* __restrict__ rec, const uint32_t (&e)[kL]) {
-#pragma unroll
-    for (int l = 0; l < kL; ++l) {
-      const int q = threadIdx.x + 256 * l;
-      const int comp = q / B;
-      if (q < 3 * B && e[l] != 0xffffffffu) {
-        v[l] = __ldg(reinterpret_cast<const float4*>(rec + e[l]) + comp);
-      } else {
-        // empty slot: h_max < 0 never hits
-        v[l] = comp == 1 ? make_float4(1.0f, 0.0f, -1.0f, 1.0f) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      }
-    }
-  }
-  // s: [3][B] float4 of one buffer; s_e: optional [B] entry ids
-  __device__ __forceinline__ void store(float4* s, uint32_t* s_e, const uint32_t (&e)[kL]) const {
-#pragma unroll
-    for (int l = 0; l < kL; ++l) {
-      const int q = threadIdx.x + 256 * l;
-      if (q < 3 * B) {
-        s[q] = v[l];
-        if (s_e && q < B) s_e[q] = e[l];
-      }
-    }
-  }
-};
 
 // ------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64

@@ -51,6 +51,7 @@ int sss_plan_frame(const sss_params* scenes, int n_scenes, const sss_camera* cam
   if (!tile_ok(cfg->tile_w, cfg->tile_h) || !batch_ok(cfg->batch)) return SSS_ERR_UNSUPPORTED;
   if (cfg->nu_grad_mode != 0 && cfg->nu_grad_mode != 1) return SSS_ERR_INVALID_ARG;
   if (cfg->kernel != 0 && cfg->kernel != 1) return SSS_ERR_INVALID_ARG;
+  if (cfg->count_pairs != 0 && cfg->count_pairs != 1) return SSS_ERR_INVALID_ARG;
   if (!(cfg->tau > 0.0f && cfg->tau < cfg->alpha_max && cfg->alpha_max < 1.0f && cfg->t_min >= 0.0f &&
         cfg->t_min < 1.0f && cfg->lowpass >= 0.0f))
     return SSS_ERR_INVALID_ARG;

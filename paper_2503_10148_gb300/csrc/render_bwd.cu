@@ -19,14 +19,17 @@
 //   dh/dmean2D = -2 conic d,  dh/d(a, b, c) = (dx^2, 2 dx dy, dy^2).
 // The factor of dT2D/dnu, f = -1/2 ln(1 + x) + (nu+2) x / (2 nu (1 + x)) with
 // x = h/nu, is O(x^2) while its two terms are O(x): evaluated as written it
-// cancels.  With u = x / (1 + x) it equals u/nu - g/2, g = ln(1 + x) - u =
-// sum_{k>=2} u^k / k (from -ln(1 - u)), a sum of positive terms; for
-// u < 1/4 the series to k = 13 is used (truncation < 1e-9 of g), above that the
-// direct difference (cancellation at most 8x).
-// Records are staged as in the forward (double buffered, next batch loaded
-// while this one is processed).  A lane first sums its pixels; the warp then
-// reduces the 10 sums with a reduce-scatter (12 shuffles instead of 10 x 5)
-// and 10 lanes add the totals to the splat's record with one RED each.
+// cancels.  With u = x / (1 + x) it equals u/nu - g/2, g = ln(1 + x) - u.
+// With s = u / (2 - u) = x / (2 + x), ln(1 + x) = 2 atanh(s) and 2 s - u =
+// u s, so g = u s + 2 (s^3/3 + s^5/5 + ...), a sum of positive terms; for
+// u < 1/4 (s < 1/7) the series to s^9 is used (truncation below 3e-9 of g),
+// above that the direct difference (cancellation at most 8x).
+// Each warp walks its own contributors back to front, 32 records per round
+// staged as in the forward.  Per splat a lane first sums its pixels (the
+// factors common to the splat, o and dT2D/dh's (nu+2)/(2 nu), are applied to
+// the sums once); the warp then reduces the 10 sums with a reduce-scatter
+// (12 shuffles instead of 10 x 5) and 10 lanes add the totals to the
+// splat's record with one RED each.
 #include "common.cuh"
 
 namespace sss {
@@ -62,19 +65,11 @@ __device__ __forceinline__ float warp_reduce_scatter10(const float (&v)[10], uns
 
 __device__ __forceinline__ float log1p_minus_u(float u, float log_base) {
   if (u < 0.25f) {
-    float p = 1.0f / 13.0f;
-    p = fmaf(u, p, 1.0f / 12.0f);
-    p = fmaf(u, p, 1.0f / 11.0f);
-    p = fmaf(u, p, 1.0f / 10.0f);
-    p = fmaf(u, p, 1.0f / 9.0f);
-    p = fmaf(u, p, 1.0f / 8.0f);
-    p = fmaf(u, p, 1.0f / 7.0f);
-    p = fmaf(u, p, 1.0f / 6.0f);
-    p = fmaf(u, p, 1.0f / 5.0f);
-    p = fmaf(u, p, 1.0f / 4.0f);
-    p = fmaf(u, p, 1.0f / 3.0f);
-    p = fmaf(u, p, 0.5f);
-    return u * u * p;
+    const float sv = __fdividef(u, 2.0f - u), s2 = sv * sv;
+    float p = fmaf(s2, 2.0f / 9.0f, 2.0f / 7.0f);
+    p = fmaf(s2, p, 2.0f / 5.0f);
+    p = fmaf(s2, p, 2.0f / 3.0f);
+    return fmaf(s2 * sv, p, u * sv);
   }
   return log_base - u;
 }
@@ -181,84 +176,112 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
         m &= ~(1u << si);
         const uint32_t pos = lo + si;
       const float4 a = S.a[k][si], b = S.b[k][si], c = S.c[k][si];
-      const float cb2 = 2.0f * a.w, hpre = fmaf(b.z, kHPad, b.z);
+      const float cb2 = 2.0f * a.w;
       const float nu = b.w, inv_nu = __fdividef(1.0f, nu), o = b.y;
+      const float oabs = fabsf(o), osgn = copysignf(1.0f, o);
       int ox, oy;
       rec_origin(c.w, ox, oy);
       const float fbx = (float)(lx - ox), fby = (float)(ly - oy);
-      // dT/dh = -(nu+2)/(2 nu) T / (1 + h/nu); -1/2 T for the Gaussian (nu = inf, inv_nu = 0)
-      const float e_over_nu = isinf(nu) ? -0.5f : fmaf(nu, -0.5f, -1.0f) * inv_nu;
       // all pixels of the lane in straight-line code, masked; nu branch
       // uniform over the warp
       PairEval r[NPIX];
       bool ok[NPIX];
-      float dxs[NPIX], dys[NPIX];
+      float dxs[PW], dys[PH];
 #pragma unroll
-      for (int p = 0; p < NPIX; ++p) {
-        dxs[p] = pixel_offset(fbx, p % PW, a.x);
-        dys[p] = pixel_offset(fby, p / PW, a.y);
-      }
+      for (int i = 0; i < PW; ++i) dxs[i] = pixel_offset(fbx, i, a.x);
+#pragma unroll
+      for (int j = 0; j < PH; ++j) dys[j] = pixel_offset(fby, j, a.y);
       if (nu <= kFastNuMax) {
 #pragma unroll
         for (int p = 0; p < NPIX; ++p)
-          ok[p] = eval_pair_fast(dxs[p], dys[p], a.z, cb2, b.x, hpre, o, nu, inv_nu, tau, amax, r[p]);
+          ok[p] = eval_pair_fast(dxs[p % PW], dys[p / PW], a.z, cb2, b.x, oabs, osgn, nu, inv_nu, tau, amax, r[p]);
       } else if (isinf(nu)) {
 #pragma unroll
         for (int p = 0; p < NPIX; ++p)
-          ok[p] = eval_pair_gauss(dxs[p], dys[p], a.z, cb2, b.x, hpre, o, tau, amax, r[p]);
+          ok[p] = eval_pair_gauss(dxs[p % PW], dys[p / PW], a.z, cb2, b.x, oabs, osgn, tau, amax, r[p]);
       } else {
 #pragma unroll
         for (int p = 0; p < NPIX; ++p)
-          ok[p] = eval_pair_slow(dxs[p], dys[p], a.z, cb2, b.x, hpre, o, nu, inv_nu, tau, amax, r[p]);
+          ok[p] = eval_pair_slow(dxs[p % PW], dys[p / PW], a.z, cb2, b.x, oabs, osgn, nu, inv_nu, tau, amax, r[p]);
       }
-      // per-lane sums: rgb (v7..9), opacity (v5), nu (v6) and the
-      // q-weighted moments of the pixel offsets, q = dL/dh, from which
-      // dL/dmean and dL/dconic follow once per splat (h is quadratic in
-      // the offsets, so its gradients are linear in these moments)
+      // per-lane sums: rgb (v7..9), st = dL/dalpha T2D (v5 = dL/do), st
+      // times the nu factor (v6 / o) and, per pixel, q = st / (1 + h/nu),
+      // with dL/dh = o (dT2D/dh / T2D) (1 + h/nu) q; dL/dmean and dL/dconic
+      // follow from q-weighted moments of the pixel offsets (h is quadratic
+      // in the offsets, so its gradients are linear in these moments)
       float v[10];
-#pragma unroll
-      for (int q = 0; q < 10; ++q) v[q] = 0.0f;
-      float m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f, m5 = 0.0f;
+      float s5 = 0.0f, s6 = 0.0f, r7 = 0.0f, r8 = 0.0f, r9 = 0.0f;
+      float q[NPIX];
       bool any = false;
 #pragma unroll
       for (int p = 0; p < NPIX; ++p) {
         const bool live = ok[p] && pos < last[p];
         any = any || live;
-        const float alpha = r[p].alpha;
-        const float Tk = live ? T[p] * __fdividef(1.0f, 1.0f - alpha) : T[p];
+        const float al = live ? r[p].alpha : 0.0f;
+        const float Tk = live ? T[p] * __fdividef(1.0f, 1.0f - al) : T[p];
         T[p] = Tk;
-        const float w = live ? alpha * Tk : 0.0f;
-        v[7] = fmaf(w, g[p][0], v[7]);
-        v[8] = fmaf(w, g[p][1], v[8]);
-        v[9] = fmaf(w, g[p][2], v[9]);
+        const float w = al * Tk;  // 0 unless live
+        r7 = fmaf(w, g[p][0], r7);
+        r8 = fmaf(w, g[p][1], r8);
+        r9 = fmaf(w, g[p][2], r9);
         // dL/dalpha = T_k dL/dC . (rgb - B) with B the colour behind; only
         // its projection on dL/dC is needed: Sg = dL/dC . B, and
         // B <- alpha rgb + (1 - alpha) B gives Sg <- Sg + alpha (g.rgb - Sg)
         const float gdiff = fmaf(g[p][0], c.x, fmaf(g[p][1], c.y, g[p][2] * c.z)) - Sg[p];
-        Sg[p] = live ? fmaf(alpha, gdiff, Sg[p]) : Sg[p];
+        Sg[p] = fmaf(al, gdiff, Sg[p]);
         const float dl_da = (live && !r[p].clamped) ? gdiff * Tk : 0.0f;
-        v[5] = fmaf(dl_da, r[p].t2d, v[5]);
-        const float dl_dt = dl_da * o;
+        const float st = dl_da * r[p].t2d;
+        s5 += st;
         const float inv_base = __fdividef(1.0f, fmaf(r[p].h, inv_nu, 1.0f));
-        const float qh = dl_dt * e_over_nu * r[p].t2d * inv_base;  // dL/dh
+        q[p] = st * inv_base;
         const float u = r[p].h * inv_nu * inv_base;  // x / (1 + x)
         // paper form: (nu+2) x / (2 nu (1+x)) = u/2 + u/nu; exact: u/nu - g/2
         const float dnu = PAPER_NU ? fmaf(0.5f, u, u * inv_nu)
                                    : fmaf(-0.5f, log1p_minus_u(u, r[p].log_base), u * inv_nu);
-        v[6] = fmaf(dl_dt * r[p].t2d, dnu, v[6]);
-        const float qdx = qh * dxs[p], qdy = qh * dys[p];
-        m1 += qdx;
-        m2 += qdy;
-        m3 = fmaf(qdx, dxs[p], m3);
-        m4 = fmaf(qdx, dys[p], m4);
-        m5 = fmaf(qdy, dys[p], m5);
+        s6 = fmaf(st, dnu, s6);
       }
+      // moments of q over the lane's PW x PH pixels from column and row sums
+      float cq[PW], cqy[PW], rq[PH];
+#pragma unroll
+      for (int i = 0; i < PW; ++i) cq[i] = cqy[i] = 0.0f;
+#pragma unroll
+      for (int j = 0; j < PH; ++j) rq[j] = 0.0f;
+#pragma unroll
+      for (int p = 0; p < NPIX; ++p) {
+        cq[p % PW] += q[p];
+        cqy[p % PW] = fmaf(q[p], dys[p / PW], cqy[p % PW]);
+        rq[p / PW] += q[p];
+      }
+      float m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f, m5 = 0.0f;
+#pragma unroll
+      for (int i = 0; i < PW; ++i) {
+        const float dq = dxs[i] * cq[i];
+        m1 += dq;
+        m3 = fmaf(dq, dxs[i], m3);
+        m4 = fmaf(dxs[i], cqy[i], m4);
+      }
+#pragma unroll
+      for (int j = 0; j < PH; ++j) {
+        const float dq = dys[j] * rq[j];
+        m2 += dq;
+        m5 = fmaf(dq, dys[j], m5);
+      }
+      // dT2D/dh / T2D = -(nu+2)/(2 nu) / (1 + h/nu); -1/2 for the Gaussian
+      // (nu = inf, inv_nu = 0)
+      const float kq = o * (isinf(nu) ? -0.5f : fmaf(nu, -0.5f, -1.0f) * inv_nu);
+      m1 *= kq;
+      m2 *= kq;
       // dh/dmean = -2 (a dx + b dy, b dx + c dy); dh/dconic = (dx^2, 2 dx dy, dy^2)
       v[0] = -2.0f * fmaf(a.z, m1, a.w * m2);
       v[1] = -2.0f * fmaf(a.w, m1, b.x * m2);
-      v[2] = m3;
-      v[3] = 2.0f * m4;
-      v[4] = m5;
+      v[2] = kq * m3;
+      v[3] = 2.0f * kq * m4;
+      v[4] = kq * m5;
+      v[5] = s5;
+      v[6] = o * s6;
+      v[7] = r7;
+      v[8] = r8;
+      v[9] = r9;
       if (__any_sync(0xffffffffu, any)) {
         int slot;
         const float tot = warp_reduce_scatter10(v, lane, &slot);

@@ -16,7 +16,7 @@
 namespace sss {
 namespace {
 
-template <int PW, int PH>
+template <int PW, int PH, bool COUNT>
 __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, void* ws, float* __restrict__ out_rgb) {
   constexpr int NPIX = PW * PH;
   constexpr int TW = 16 * PW, TH = 16 * PH;
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
   const uint32_t* vals = ws_ptr<uint32_t>(ws, P.ws_off_pval) + (size_t)P.pair_slot * P.pair_capacity + range.x;
   const SplatRec* rec = ws_ptr<SplatRec>(ws, P.ws_off_rec);
   const float tau = cfg.tau, amax = cfg.alpha_max, tmin = cfg.t_min;
-  uint32_t n_eval = 0, n_contrib = 0;  // pair counters for the roofline
+  uint32_t n_eval = 0, n_contrib = 0;  // pair counters (COUNT only)
 
   const uint32_t n_list = range.y - range.x;
   const uint32_t n_batches = (n_list + 31) / 32;
@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
         const int si = __ffs(m) - 1;
         m &= m - 1;
       const float4 a = S.a[k][si], b = S.b[k][si], c = S.c[k][si];
-      const float cb2 = 2.0f * a.w, hpre = fmaf(b.z, kHPad, b.z), inv_nu = __fdividef(1.0f, b.w);
+      const float cb2 = 2.0f * a.w, inv_nu = __fdividef(1.0f, b.w);
+      const float oabs = fabsf(b.y), osgn = copysignf(1.0f, b.y);
       int ox, oy;
       rec_origin(c.w, ox, oy);
       const float fbx = (float)(lx - ox), fby = (float)(ly - oy);
@@ -106,21 +107,21 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
 #pragma unroll
         for (int p = 0; p < NPIX; ++p)
           ok[p] = eval_pair_fast(pixel_offset(fbx, p % PW, a.x), pixel_offset(fby, p / PW, a.y), a.z, cb2,
-                                 b.x, hpre, b.y, b.w, inv_nu, tau, amax, r[p]);
+                                 b.x, oabs, osgn, b.w, inv_nu, tau, amax, r[p]);
       } else if (isinf(b.w)) {
 #pragma unroll
         for (int p = 0; p < NPIX; ++p)
           ok[p] = eval_pair_gauss(pixel_offset(fbx, p % PW, a.x), pixel_offset(fby, p / PW, a.y), a.z, cb2,
-                                  b.x, hpre, b.y, tau, amax, r[p]);
+                                  b.x, oabs, osgn, tau, amax, r[p]);
       } else {
 #pragma unroll
         for (int p = 0; p < NPIX; ++p)
-          ok[p] = eval_pair(pixel_offset(fbx, p % PW, a.x), pixel_offset(fby, p / PW, a.y), a.z, cb2, b.x,
-                            hpre, b.y, b.w, inv_nu, tau, amax, r[p]);
+          ok[p] = eval_pair_slow(pixel_offset(fbx, p % PW, a.x), pixel_offset(fby, p / PW, a.y), a.z, cb2,
+                                 b.x, oabs, osgn, b.w, inv_nu, tau, amax, r[p]);
       }
 #pragma unroll
       for (int p = 0; p < NPIX; ++p) {
-        n_eval += done[p] ? 0u : 1u;
+        if (COUNT) n_eval += done[p] ? 0u : 1u;
         const bool live = ok[p] && !done[p];
         const float Tn = T[p] * (1.0f - r[p].alpha);
         const bool term = live && Tn < tmin;  // stops before this splat
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
         T[p] = add ? Tn : T[p];
         last[p] = add ? pos1 : last[p];
         done[p] = done[p] || term;
-        n_contrib += add ? 1u : 0u;
+        if (COUNT) n_contrib += add ? 1u : 0u;
       }
       bool ld = true;
 #pragma unroll
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
     cp_async_wait<0>();  // no copy into this warp's buffers outlives the loop
   }
 
-  {
+  if (COUNT) {
     const uint32_t ne = __reduce_add_sync(0xffffffffu, n_eval), nc = __reduce_add_sync(0xffffffffu, n_contrib);
     if ((threadIdx.x & 31) == 0 && ne) {
       unsigned long long* ctr = reinterpret_cast<unsigned long long*>(ws_ptr<uint32_t>(ws, P.ws_off_ctrl) + 4);
@@ -172,9 +173,11 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
 
 template <int PW, int PH>
 int launch_batch(const sss_frame_plan& P, void* ws, float* out, cudaStream_t st) {
-  // the staging batch is 32 records per warp whatever cfg.batch says (the
-  // plan has already checked it is one of the accepted values)
-  k_render_fwd<PW, PH><<<4 * P.n_tiles, 64, 0, st>>>(P, ws, out);
+  // the staging batch is 32 records per warp (the only value the plan accepts)
+  if (P.cfg.count_pairs)
+    k_render_fwd<PW, PH, true><<<4 * P.n_tiles, 64, 0, st>>>(P, ws, out);
+  else
+    k_render_fwd<PW, PH, false><<<4 * P.n_tiles, 64, 0, st>>>(P, ws, out);
   SSS_LAUNCH_CHECK();
   return SSS_OK;
 }

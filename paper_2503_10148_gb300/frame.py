@@ -206,6 +206,17 @@ class Frame:
         self.render_fwd(stream, out)
         return self.rgb if out is None else out
 
+    def count_pairs(self, stream=None) -> tuple[int, int]:
+        """One forward with pair counting on (``cfg.count_pairs``); returns
+        the frame's contributing and evaluated (splat, pixel) pairs."""
+        self.plan.cfg.count_pairs = 1
+        try:
+            self.forward(stream, grow=False)
+        finally:
+            self.plan.cfg.count_pairs = 0
+        ctrl = self.ws_view(self.plan.ws_off_ctrl, torch.int64, 4).cpu()
+        return int(ctrl[2]), int(ctrl[3])
+
     def backward(self, dl_drgb: torch.Tensor, grads, stream=None):
         self.render_bwd(dl_drgb, stream)
         self.project_bwd(grads, stream)

@@ -214,6 +214,30 @@ def test_forward_last_contributor_matches_oracle():
     assert np.array_equal(comp[ok], ref["last"][ok])
 
 
+def test_pair_counters_match_oracle():
+    """cfg.count_pairs: the forward counts contributing (splat, pixel) pairs
+    (the oracle's n_contrib summed over pixels; flagged pixels, whose FP32
+    decisions may differ near tau or t_min, get a slack) and evaluated pairs
+    (at least the contributing ones); a forward without counting adds
+    nothing."""
+    scene, cams = inputs.tiny_cube_2k()
+    fr, _, cams = gpu_forward(scene, cams)
+    cfgd = frame.cfg_dict(fr.cfg)
+    nc, ne = fr.count_pairs()
+    want, slack = 0, 0
+    for cam in cams:
+        ref = oracle.render(oracle.project(f32_scene(scene), cam, cfgd), cam, cfgd)
+        want += int(ref["n_contrib"].sum())
+        fl = ref["flags"] != 0
+        slack += int(ref["n_contrib"][fl].sum()) + 4 * int(fl.sum())
+    assert abs(nc - want) <= slack, (nc, want, slack)
+    assert want > 0 and ne >= nc
+    fr.forward(grow=False)
+    torch.cuda.synchronize()
+    ctrl = fr.ws_view(fr.plan.ws_off_ctrl, torch.int64, 4).cpu()
+    assert (int(ctrl[2]), int(ctrl[3])) == (0, 0)
+
+
 def test_forward_shell_8views_800_sampled():
     """Shell workload at full size (100k components, 8 x 800x800, SH degree 3),
     2,000 sampled pixels per view computed one by one by the oracle."""
