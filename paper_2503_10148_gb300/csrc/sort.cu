@@ -57,14 +57,15 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-// Lanes of the warp whose 8-bit digit equals this lane's, among the lanes
-// in `valid` (a match.any built from eight ballots: two lanes match when
-// they agree on every bit).  Ballots are plain vote instructions, where
+// Lanes of the warp whose DB-bit digit equals this lane's, among the lanes
+// in `valid` (a match.any built from DB ballots: two lanes match when they
+// agree on every bit).  Ballots are plain vote instructions, where
 // match.any goes through the MIO pipe and its latency dominated the passes.
+template <int DB>
 __device__ __forceinline__ unsigned digit_peers(uint32_t d, unsigned valid) {
   unsigned peers = valid;
 #pragma unroll
-  for (int b = 0; b < 8; ++b) {
+  for (int b = 0; b < DB; ++b) {
     const bool bit = (d >> b) & 1u;
     const unsigned m = __ballot_sync(0xffffffffu, bit);
     peers &= bit ? m : ~m;
@@ -97,12 +98,12 @@ __device__ __forceinline__ uint32_t block_scan_incl(uint32_t v, uint32_t* s_w, u
   return before + x;
 }
 
-// Per-CTA digit histogram of its slice -> hist[digit * nb + cta].  Each warp
-// counts into its own sub-histogram (the leader of each group of equal
-// digits adds the group's size: distinct addresses, no atomics), and the
-// eight are summed at the end.
+// Per-CTA digit histogram of its slice -> hist[digit * nb + cta].  A
+// histogram needs no order, so each warp counts into its own sub-histogram
+// with shared-memory atomics (the eight are summed at the end).
 __global__ void __launch_bounds__(kThreads) k_upsweep(const uint32_t* __restrict__ keys, const uint32_t* count_dev,
-                                                      uint32_t count_max, int shift, uint32_t* __restrict__ hist) {
+                                                      uint32_t count_max, int shift, uint32_t mask,
+                                                      uint32_t* __restrict__ hist) {
   __shared__ uint32_t sh[kWarps][kRadix];
   const unsigned warp = threadIdx.x >> 5;
 #pragma unroll
@@ -110,20 +111,17 @@ __global__ void __launch_bounds__(kThreads) k_upsweep(const uint32_t* __restrict
   __syncthreads();
   uint32_t begin, end;
   slice(load_count(count_dev, count_max), gridDim.x, blockIdx.x, begin, end);
-  const unsigned lt = lanemask_lt();
+  uint32_t* my = sh[warp];
   for (uint32_t t0 = begin; t0 < end; t0 += kTile) {
     uint32_t d[kItems];
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
       const uint32_t i = t0 + it * kThreads + threadIdx.x;
-      d[it] = i < end ? (__ldg(keys + i) >> shift) & 0xffu : 0u;
+      d[it] = i < end ? (__ldg(keys + i) >> shift) & mask : 0xffffffffu;
     }
 #pragma unroll
-    for (int it = 0; it < kItems; ++it) {
-      const bool ok = t0 + it * kThreads + threadIdx.x < end;
-      const unsigned peers = digit_peers(d[it], __ballot_sync(0xffffffffu, ok));
-      if (ok && (peers & lt) == 0u) sh[warp][d[it]] += (uint32_t)__popc(peers);
-    }
+    for (int it = 0; it < kItems; ++it)
+      if (d[it] != 0xffffffffu) atomicAdd(my + d[it], 1u);
   }
   __syncthreads();
   uint32_t tot = 0;
@@ -181,11 +179,13 @@ struct DownsweepSmem {
 // written by consecutive threads.  vals_in == nullptr means the identity
 // payload (element index).  With `ranges`, runs of equal keys report their
 // global ends (keys are the tile ids and this is the last pass).
+template <int DB>
 __global__ void __launch_bounds__(kThreads, 3)
     k_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const uint32_t* count_dev,
                 uint32_t count_max, int shift, const uint32_t* __restrict__ hist_scan,
                 const uint32_t* __restrict__ totals, uint2* __restrict__ ranges) {
+  constexpr uint32_t kDMask = (1u << DB) - 1u;  // digit bits of this pass
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DownsweepSmem& S = *reinterpret_cast<DownsweepSmem*>(smem_raw);
   uint32_t begin, end;
@@ -221,8 +221,8 @@ __global__ void __launch_bounds__(kThreads, 3)
     for (int it = 0; it < kItems; ++it) {
       const uint32_t i = wloc + it * 32 + lane;
       const bool ok = i < n_here;
-      const uint32_t d = ok ? (S.kin[i] >> shift) & 0xffu : 0u;
-      const unsigned peers = digit_peers(d, __ballot_sync(0xffffffffu, ok));
+      const uint32_t d = ok ? (S.kin[i] >> shift) & kDMask : 0u;
+      const unsigned peers = digit_peers<DB>(d, __ballot_sync(0xffffffffu, ok));
       const uint32_t c = ok ? S.warp_cnt[warp][d] : 0u;
       rk[it] = c + __popc(peers & lt);
       __syncwarp();
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 3)
       const uint32_t i = wloc + it * 32 + lane;
       if (i < n_here) {
         const uint32_t k = S.kin[i];
-        const uint32_t loc = S.warp_cnt[warp][(k >> shift) & 0xffu] + rk[it];
+        const uint32_t loc = S.warp_cnt[warp][(k >> shift) & kDMask] + rk[it];
         S.key[loc] = k;
         S.val[loc] = S.vin[i];
       }
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 3)
       const uint32_t i = j * kThreads + threadIdx.x;
       if (i < n_here) {
         const uint32_t k = S.key[i];
-        const uint32_t g = S.base[(k >> shift) & 0xffu] + i;
+        const uint32_t g = S.base[(k >> shift) & kDMask] + i;
         keys_out[g] = k;
         vals_out[g] = S.val[i];
         if (ranges) {
@@ -274,14 +274,23 @@ __global__ void __launch_bounds__(kThreads, 3)
   }
 }
 
+template <int DB>
+int downsweep_optin_one() {
+  return cudaFuncSetAttribute(k_downsweep<DB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(DownsweepSmem)) == cudaSuccess
+             ? SSS_OK
+             : SSS_ERR_CUDA;
+}
+
 // Opt-in to the dynamic shared memory of k_downsweep, once per device.
 int downsweep_smem_optin() {
   static int done[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SSS_ERR_CUDA;
   if (!done[dev]) {
-    if (cudaFuncSetAttribute(k_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(DownsweepSmem)) != cudaSuccess) {
+    if (downsweep_optin_one<1>() || downsweep_optin_one<2>() || downsweep_optin_one<3>() ||
+        downsweep_optin_one<4>() || downsweep_optin_one<5>() || downsweep_optin_one<6>() ||
+        downsweep_optin_one<7>() || downsweep_optin_one<8>()) {
       (void)cudaGetLastError();
       return SSS_ERR_CUDA;
     }
@@ -290,11 +299,20 @@ int downsweep_smem_optin() {
   return SSS_OK;
 }
 
+template <int DB>
+void launch_downsweep(int nb, cudaStream_t st, const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
+                      uint32_t* vout, const uint32_t* count_dev, uint32_t count_max, int shift, const uint32_t* hist,
+                      const uint32_t* totals, uint2* ranges) {
+  k_downsweep<DB><<<nb, kThreads, sizeof(DownsweepSmem), st>>>(kin, vin, kout, vout, count_dev, count_max, shift, hist,
+                                                               totals, ranges);
+}
+
 // Stable LSD sort of `count` (key, val) pairs over bits [0, bits), ping-pong
 // between slot 0 and slot 1; the result lands in slot (passes & 1).  `hist`
-// holds [256][nb] counts followed by 256 digit totals.  With `ranges`, the
-// last pass records the [start, end) of every key (which must be < the ranges
-// array's length).
+// holds [256][nb] counts followed by 256 digit totals.  Passes take 8 bits,
+// the last one the remaining 1..8 (the ballot match of the downsweep costs
+// one vote per digit bit).  With `ranges`, the last pass records the
+// [start, end) of every key (which must be < the ranges array's length).
 int radix_sort(uint32_t* keys0, uint32_t* keys1, uint32_t* vals0, uint32_t* vals1, const uint32_t* first_vals,
                const uint32_t* first_keys, const uint32_t* count_dev, uint32_t count_max, int bits, int nb,
                uint32_t* hist, uint2* ranges, cudaStream_t st) {
@@ -303,14 +321,24 @@ int radix_sort(uint32_t* keys0, uint32_t* keys1, uint32_t* vals0, uint32_t* vals
   if (int rc = downsweep_smem_optin()) return rc;
   for (int p = 0; p < passes; ++p) {
     const int shift = 8 * p;
+    const int db = std::min(8, bits - shift);
     const uint32_t* kin = (p == 0 && first_keys) ? first_keys : ((p & 1) ? keys1 : keys0);
     const uint32_t* vin = (p == 0) ? first_vals : ((p & 1) ? vals1 : vals0);
     uint32_t* kout = (p & 1) ? keys0 : keys1;
     uint32_t* vout = (p & 1) ? vals0 : vals1;
-    k_upsweep<<<nb, kThreads, 0, st>>>(kin, count_dev, count_max, shift, hist);
+    uint2* rg = p + 1 == passes ? ranges : nullptr;
+    k_upsweep<<<nb, kThreads, 0, st>>>(kin, count_dev, count_max, shift, (1u << db) - 1u, hist);
     k_scan_rows<<<kRadix, kThreads, 0, st>>>(hist, (uint32_t)nb, totals);
-    k_downsweep<<<nb, kThreads, sizeof(DownsweepSmem), st>>>(kin, vin, kout, vout, count_dev, count_max, shift, hist, totals,
-                                         p + 1 == passes ? ranges : nullptr);
+    switch (db) {
+      case 1: launch_downsweep<1>(nb, st, kin, vin, kout, vout, count_dev, count_max, shift, hist, totals, rg); break;
+      case 2: launch_downsweep<2>(nb, st, kin, vin, kout, vout, count_dev, count_max, shift, hist, totals, rg); break;
+      case 3: launch_downsweep<3>(nb, st, kin, vin, kout, vout, count_dev, count_max, shift, hist, totals, rg); break;
+      case 4: launch_downsweep<4>(nb, st, kin, vin, kout, vout, count_dev, count_max, shift, hist, totals, rg); break;
+      case 5: launch_downsweep<5>(nb, st, kin, vin, kout, vout, count_dev, count_max, shift, hist, totals, rg); break;
+      case 6: launch_downsweep<6>(nb, st, kin, vin, kout, vout, count_dev, count_max, shift, hist, totals, rg); break;
+      case 7: launch_downsweep<7>(nb, st, kin, vin, kout, vout, count_dev, count_max, shift, hist, totals, rg); break;
+      default: launch_downsweep<8>(nb, st, kin, vin, kout, vout, count_dev, count_max, shift, hist, totals, rg); break;
+    }
     SSS_LAUNCH_CHECK();
   }
   return SSS_OK;
