@@ -187,8 +187,9 @@ typedef struct sss_frame_plan {
   size_t ws_off_dkey;    /* uint32[n_entries]: FP32 depth-key bits          */
   size_t ws_off_ntiles;  /* uint32[n_entries]: tiles touched                */
   size_t ws_off_rect;    /* uint2[n_entries]: tile rect (x0|x1<<16, y0|y1<<16) */
-  size_t ws_off_order;   /* uint32[2][n_entries]: depth-sorted entries      */
-  size_t ws_off_okey;    /* uint32[2][n_entries]: sort keys (ping-pong)     */
+  size_t ws_off_order;   /* uint32[2][n4]: depth-sorted entries (slot 0),
+                            n4 = n_entries rounded up to a multiple of 4    */
+  size_t ws_off_okey;    /* uint32[2][n4]: sort keys (ping-pong)            */
   size_t ws_off_pkey;    /* uint32[2][pair_capacity]: tile key per pair     */
   size_t ws_off_pval;    /* uint32[2][pair_capacity]: entry per pair        */
   size_t ws_off_ranges;  /* uint2[n_tiles]: [start, end) per tile           */
@@ -209,7 +210,9 @@ typedef struct sss_frame_plan {
 
 /* Host only.  Builds a plan for n_jobs jobs.  scenes[s] holds device
  * pointers (not dereferenced here); job_scene[j] in [0, n_scenes).
- * pair_capacity bounds the (tile, splat) pairs of one frame.
+ * pair_capacity bounds the (tile, splat) pairs of one frame; the plan
+ * rounds it up to a multiple of 4 (plan->pair_capacity), so that both pair
+ * slots start 16-byte aligned; at most 2^31 - 4.
  * Errors: SSS_ERR_INVALID_ARG for counts outside the limits, sh_degree not in
  * 0..3, non-positive image sizes, a job referring to a missing scene, totals
  * above 2^31; SSS_ERR_UNSUPPORTED for a tile size or batch not built. */

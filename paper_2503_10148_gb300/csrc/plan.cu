@@ -55,7 +55,8 @@ int sss_plan_frame(const sss_params* scenes, int n_scenes, const sss_camera* cam
   if (!(cfg->tau > 0.0f && cfg->tau < cfg->alpha_max && cfg->alpha_max < 1.0f && cfg->t_min >= 0.0f &&
         cfg->t_min < 1.0f && cfg->lowpass >= 0.0f))
     return SSS_ERR_INVALID_ARG;
-  if (pair_capacity == 0 || pair_capacity > 0x7fffffffu) return SSS_ERR_INVALID_ARG;
+  if (pair_capacity == 0 || pair_capacity > 0x7ffffffcu) return SSS_ERR_INVALID_ARG;
+  pair_capacity = (pair_capacity + 3u) & ~3u;  // 16-byte aligned pair slots
 
   std::memset(plan, 0, sizeof(*plan));
   plan->n_jobs = n_jobs;
@@ -125,8 +126,10 @@ int sss_plan_frame(const sss_params* scenes, int n_scenes, const sss_camera* cam
   plan->ws_off_dkey = take(4 * entries);
   plan->ws_off_ntiles = take(4 * entries);
   plan->ws_off_rect = take(8 * entries);
-  plan->ws_off_order = take(2 * 4 * entries);
-  plan->ws_off_okey = take(2 * 4 * entries);
+  // two slots each; slot 1 starts 16-byte aligned (the sort copies chunks
+  // with 16-byte transfers when both of its inputs are aligned)
+  plan->ws_off_order = take(2 * 4 * ((entries + 3) & ~3ull));
+  plan->ws_off_okey = take(2 * 4 * ((entries + 3) & ~3ull));
   plan->ws_off_pkey = take(2 * 4 * (size_t)pair_capacity);
   plan->ws_off_pval = take(2 * 4 * (size_t)pair_capacity);
   plan->ws_off_ranges = take(8 * tiles);

@@ -200,33 +200,71 @@ __global__ void __launch_bounds__(kThreads, 3)
     uint32_t tot;
     next = block_scan_incl(v, S.w, tot) - v + hist_scan[dme * gridDim.x + blockIdx.x];
   }
-  for (uint32_t t0 = begin; t0 < end; t0 += kTile) {
-    const uint32_t n_here = min(end - t0, (uint32_t)kTile);
+  // chunk loads are asynchronous: chunk c + 1 is requested once chunk c has
+  // been ranked and moved to the digit-ordered buffers, so it arrives while
+  // chunk c is written out
+  // 16-byte copies when both input arrays are 16-byte aligned (chunk starts
+  // are multiples of kTile elements), else 4-byte copies
+  const bool vec = ((reinterpret_cast<uintptr_t>(keys_in) | reinterpret_cast<uintptr_t>(vals_in)) & 15u) == 0;
+  auto request = [&](uint32_t t0) {
+    const uint32_t n = min(end - t0, (uint32_t)kTile);
+    if (vec) {
 #pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-      const uint32_t i = j * kThreads + threadIdx.x;
-      if (i < n_here) {
-        cp_async4(&S.kin[i], keys_in + t0 + i);
-        if (vals_in) cp_async4(&S.vin[i], vals_in + t0 + i);
-        else S.vin[i] = t0 + i;
+      for (int j = 0; j < kItems / 4; ++j) {
+        const uint32_t i = 4 * (j * kThreads + threadIdx.x);
+        if (i + 4 <= n) {
+          cp_async16(&S.kin[i], keys_in + t0 + i);
+          if (vals_in) cp_async16(&S.vin[i], vals_in + t0 + i);
+        } else {
+          for (uint32_t e = i; e < n; ++e) {
+            cp_async4(&S.kin[e], keys_in + t0 + e);
+            if (vals_in) cp_async4(&S.vin[e], vals_in + t0 + e);
+          }
+        }
+        if (!vals_in) {
+#pragma unroll
+          for (uint32_t r = 0; r < 4; ++r)
+            if (i + r < n) S.vin[i + r] = t0 + i + r;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < kItems; ++j) {
+        const uint32_t i = j * kThreads + threadIdx.x;
+        if (i < n) {
+          cp_async4(&S.kin[i], keys_in + t0 + i);
+          if (vals_in) cp_async4(&S.vin[i], vals_in + t0 + i);
+          else S.vin[i] = t0 + i;
+        }
       }
     }
 #pragma unroll
     for (int k = 0; k < kRadix / 32; ++k) S.warp_cnt[warp][k * 32 + lane] = 0;
+  };
+  request(begin);
+  for (uint32_t t0 = begin; t0 < end; t0 += kTile) {
+    const uint32_t n_here = min(end - t0, (uint32_t)kTile);
     cp_async_wait_all();
     __syncthreads();
     const uint32_t wloc = warp * kWarpSpan;  // chunk position of this warp's first element
-    uint32_t rk[kItems];
+    // ranking: the 16 rounds' digit matches first (independent, so their
+    // votes interleave), then the chain through the warp's digit counters
+    uint32_t dg[kItems], rk[kItems];
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
       const uint32_t i = wloc + it * 32 + lane;
       const bool ok = i < n_here;
-      const uint32_t d = ok ? (S.kin[i] >> shift) & kDMask : 0u;
-      const unsigned peers = digit_peers<DB>(d, __ballot_sync(0xffffffffu, ok));
-      const uint32_t c = ok ? S.warp_cnt[warp][d] : 0u;
+      dg[it] = ok ? (S.kin[i] >> shift) & kDMask : 0u;
+      rk[it] = digit_peers<DB>(dg[it], __ballot_sync(0xffffffffu, ok));  // peers for now
+    }
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+      const bool ok = wloc + it * 32 + lane < n_here;
+      const unsigned peers = rk[it];
+      const uint32_t c = ok ? S.warp_cnt[warp][dg[it]] : 0u;
       rk[it] = c + __popc(peers & lt);
       __syncwarp();
-      if (ok && (peers & lt) == 0u) S.warp_cnt[warp][d] = c + __popc(peers);
+      if (ok && (peers & lt) == 0u) S.warp_cnt[warp][dg[it]] = c + __popc(peers);
       __syncwarp();
     }
     __syncthreads();
@@ -256,6 +294,8 @@ __global__ void __launch_bounds__(kThreads, 3)
       }
     }
     __syncthreads();
+    // the input buffers and counters are free: request the next chunk
+    if (t0 + kTile < end) request(t0 + kTile);
 #pragma unroll 4
     for (int j = 0; j < kItems; ++j) {
       const uint32_t i = j * kThreads + threadIdx.x;
@@ -270,8 +310,10 @@ __global__ void __launch_bounds__(kThreads, 3)
         }
       }
     }
-    __syncthreads();
+    // S.key, S.val and S.base are rewritten only after the next chunk's
+    // first barrier, which every thread reaches after its write-out
   }
+  cp_async_wait_all();
 }
 
 template <int DB>
@@ -476,7 +518,8 @@ extern "C" int sss_bin(const sss_frame_plan* plan, void* ws, sss_stream_t stream
   uint32_t* okey = ws_ptr<uint32_t>(ws, P.ws_off_okey);
   uint32_t* hist = ws_ptr<uint32_t>(ws, P.ws_off_hist);
   // depth digits: 4 passes over the n entries, sorted result in slot 0
-  int rc = radix_sort(okey, okey + n, order, order + n, nullptr, ws_ptr<uint32_t>(ws, P.ws_off_dkey), nullptr, n,
+  const uint32_t n4 = (n + 3) & ~3u;  // slot stride (16-byte aligned slot 1)
+  int rc = radix_sort(okey, okey + n4, order, order + n4, nullptr, ws_ptr<uint32_t>(ws, P.ws_off_dkey), nullptr, n,
                       32, nb, hist, nullptr, st);
   if (rc != SSS_OK) return rc;
   uint32_t* block_sums = hist;  // reused: nb words
