@@ -1,7 +1,11 @@
 // a7: SGHMC on the means, Adam on every other group (Sec. 3.4 Eq.
-// sigmoidUpdate, SM Eq. SGHMC), one thread per component.  Pure streaming:
-// per component at SH degree 3 it reads parameters, gradients and moments and
-// writes parameters and moments back (about 1.6 KB), so it runs at HBM speed.
+// sigmoidUpdate, SM Eq. SGHMC).  Two launches: k_sghmc updates the means
+// (one thread per component: the noise, the gate and the momentum), k_adam
+// every other parameter row (a 2D grid of (row, block of 1024 components),
+// four components per thread with their loads in flight).  Pure streaming:
+// per component at SH degree 3 they read parameters, gradients and moments
+// and write parameters and moments back (about 1.6 KB), so they run at HBM
+// speed.
 //
 // Noise: Philox4x32-10 (Salmon et al., SC'11) -- ten rounds of two 32x32->64
 // multiplications by the published multipliers on counter words 0 and 2,
