@@ -5,7 +5,7 @@
 //
 // Value pass: one CTA per (32 x 32 tile, channel) of an image.  The tile
 // plus a 5-pixel halo of prediction x and target y is staged in shared
-// memory; a horizontal 11-tap pass over the 42 rows gives the windowed sums
+// memory (asynchronous copies, zero-filled outside the image); a horizontal 11-tap pass over the 42 rows gives the windowed sums
 // of x, y, x^2, y^2, xy, a vertical pass the five window statistics at each
 // pixel (both passes register-blocked: a thread makes 4 adjacent outputs
 // from 14 loaded values), then SSIM and its partials
@@ -47,14 +47,30 @@ __device__ __forceinline__ int job_of_ssim_tile(const sss_frame_plan& P, const S
 }
 
 // Stage rows [y0 - R, y0 + TY + R) x cols [x0 - R, x0 + TX + R) of one
-// channel plane (zero outside the image) into s, minus `shift`.
-__device__ __forceinline__ void stage(float (*s)[HX], const float* plane, int W, int H, int x0, int y0,
-                                      float shift = 0.0f) {
-  for (int i = threadIdx.x; i < HY * HX; i += NT) {
-    const int r = i / HX, q = i - r * HX;
-    const int gy = y0 - R + r, gx = x0 - R + q;
-    s[r][q] = ((gx >= 0 && gx < W && gy >= 0 && gy < H) ? plane[(size_t)gy * W + gx] : 0.0f) - shift;
+// channel plane into s with asynchronous 4-byte copies (all in flight at
+// once; pixels outside the image are zero-filled by the copy): warp w takes
+// rows w, w + 8, ..., its lanes the columns.  The caller waits
+// (stage_wait) and synchronises the CTA.
+__device__ __forceinline__ void stage(float (*s)[HX], const float* plane, int W, int H, int x0, int y0) {
+  const int lane = threadIdx.x & 31;
+  for (int r = threadIdx.x >> 5; r < HY; r += NT / 32) {
+    const int gy = y0 - R + r;
+    const bool row_in = gy >= 0 && gy < H;
+    const float* row = plane + (size_t)(row_in ? gy : 0) * W;
+#pragma unroll
+    for (int q = lane; q < HX; q += 32) {
+      const int gx = x0 - R + q;
+      const bool in = row_in && gx >= 0 && gx < W;
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(&s[r][q]);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(in ? row + gx : plane),
+                   "r"(in ? 4 : 0)
+                   : "memory");
+    }
   }
+}
+__device__ __forceinline__ void stage_wait() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 __global__ void __launch_bounds__(NT) k_ssim_value(const sss_frame_plan P, const SsimArgs A) {
@@ -72,12 +88,14 @@ __global__ void __launch_bounds__(NT) k_ssim_value(const sss_frame_plan P, const
   const size_t plane_off = 3 * (size_t)J.pix_base + (size_t)ch * W * H;
   // Window statistics of x - cx, y - cy with cx, cy the tile's first pixel:
   // the variances E[(x-c)^2] - E[x-c]^2 then carry no cancellation in flat
-  // regions (out-of-image pixels stage as -c, i.e. zero padding is kept;
-  // the window weights sum to 1, so the statistics are shift-invariant).
-  const float cx = A.pred[plane_off + (size_t)y0 * W + x0], cy = A.target[plane_off + (size_t)y0 * W + x0];
-  stage(sx, A.pred + plane_off, W, H, x0, y0, cx);
-  stage(sy, A.target + plane_off, W, H, x0, y0, cy);
+  // regions (out-of-image pixels stage as 0 and enter as -c, i.e. zero
+  // padding is kept; the window weights sum to 1, so the statistics are
+  // shift-invariant).  The shift is applied as the staged values are read.
+  stage(sx, A.pred + plane_off, W, H, x0, y0);
+  stage(sy, A.target + plane_off, W, H, x0, y0);
+  stage_wait();
   __syncthreads();
+  const float cx = sx[R][R], cy = sy[R][R];  // the tile's first pixel (inside the image)
   // horizontal: item = (row, group of WB columns); windowed sums of x, y,
   // x^2, y^2, xy for WB adjacent columns from WB + 10 staged values
   for (int it = threadIdx.x; it < HY * (TX / WB); it += NT) {
@@ -85,8 +103,8 @@ __global__ void __launch_bounds__(NT) k_ssim_value(const sss_frame_plan P, const
     float xv[WB + 2 * R], yv[WB + 2 * R];
 #pragma unroll
     for (int k = 0; k < WB + 2 * R; ++k) {
-      xv[k] = sx[r][q0 + k];
-      yv[k] = sy[r][q0 + k];
+      xv[k] = sx[r][q0 + k] - cx;
+      yv[k] = sy[r][q0 + k] - cy;
     }
 #pragma unroll
     for (int o = 0; o < WB; ++o) {
@@ -108,7 +126,10 @@ __global__ void __launch_bounds__(NT) k_ssim_value(const sss_frame_plan P, const
     }
   }
   __syncthreads();
-  double l1 = 0.0, ssum = 0.0;
+  // per-thread partials in FP32 (a thread makes TX TY / NT = 4 outputs), then
+  // FP64 over the CTA and the frame (FP64 runs at a small fraction of the
+  // FP32 rate on this part)
+  float l1f = 0.0f, ssf = 0.0f;
   constexpr float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
   // vertical: item = (column, group of WB rows)
   for (int it = threadIdx.x; it < TX * (TY / WB); it += NT) {
@@ -143,19 +164,21 @@ __global__ void __launch_bounds__(NT) k_ssim_value(const sss_frame_plan P, const
     const float B1 = fmaf(mx, mx, fmaf(my, my, C1)), B2 = sx2 + sy2 + C2;
     const float D = 1.0f / (B1 * B2);
     const float S = A1 * A2 * D;
-    // product forms: no division by A1 or A2 (either can vanish)
-    const float dS_dmx = 2.0f * my * A2 * D - 2.0f * mx * S / B1;
-    const float dS_dsx2 = -S / B2;
+    // product forms: no division by A1 or A2 (either can vanish); 1/B1 and
+    // 1/B2 as B2 D and B1 D (one reciprocal per pixel)
+    const float dS_dmx = 2.0f * my * A2 * D - 2.0f * mx * S * (B2 * D);
+    const float dS_dsx2 = -S * (B1 * D);
     const float dS_dsxy = 2.0f * A1 * D;
     const size_t o = plane_off + (size_t)gy * W + gx;
     A.maps[o] = dS_dmx - 2.0f * mx * dS_dsx2 - my * dS_dsxy;
     A.maps[3 * (size_t)A.n_pixels + o] = dS_dsx2;
     A.maps[6 * (size_t)A.n_pixels + o] = dS_dsxy;
-    ssum += (double)S;
-    l1 += (double)fabsf(A.pred[o] - A.target[o]);
+    ssf += S;
+    l1f += fabsf(sx[r + R][q + R] - sy[r + R][q + R]);
     }
   }
   // CTA sums -> one FP64 atomic each
+  double l1 = (double)l1f, ssum = (double)ssf;
 #pragma unroll
   for (int off = 16; off; off >>= 1) {
     l1 += __shfl_xor_sync(0xffffffffu, l1, off);
@@ -199,6 +222,7 @@ __global__ void __launch_bounds__(NT) k_ssim_grad(const sss_frame_plan P, const 
   const size_t plane_off = 3 * (size_t)J.pix_base + (size_t)ch * W * H;
 #pragma unroll
   for (int m = 0; m < 3; ++m) stage(sm[m], A.maps + m * 3 * (size_t)A.n_pixels + plane_off, W, H, x0, y0);
+  stage_wait();
   __syncthreads();
   for (int it = threadIdx.x; it < HY * (TX / WB); it += NT) {
     const int r = it / (TX / WB), q0 = (it - r * (TX / WB)) * WB;
@@ -221,6 +245,17 @@ __global__ void __launch_bounds__(NT) k_ssim_grad(const sss_frame_plan P, const 
   const float w1 = (1.0f - A.eps) * scale, ws = A.eps * scale;
   for (int it = threadIdx.x; it < TX * (TY / WB); it += NT) {
     const int q = it % TX, r0 = (it / TX) * WB;
+    // this item's prediction and target values, requested before the
+    // windowed sums so that their latency overlaps them
+    float xs[WB], ys[WB];
+#pragma unroll
+    for (int ob = 0; ob < WB; ++ob) {
+      const int gx = x0 + q, gy = y0 + r0 + ob;
+      const bool in = gx < W && gy < H;
+      const size_t o = plane_off + (size_t)(in ? gy : y0) * W + (in ? gx : x0);
+      xs[ob] = A.pred[o];
+      ys[ob] = A.target[o];
+    }
     float cv[WB][3];
 #pragma unroll
     for (int o = 0; o < WB; ++o) cv[o][0] = cv[o][1] = cv[o][2] = 0.f;
@@ -241,7 +276,7 @@ __global__ void __launch_bounds__(NT) k_ssim_grad(const sss_frame_plan P, const 
       const int gx = x0 + q, gy = y0 + r0 + ob;
       if (gx >= W || gy >= H) continue;
       const size_t o = plane_off + (size_t)gy * W + gx;
-      const float x = A.pred[o], y = A.target[o];
+      const float x = xs[ob], y = ys[ob];
       const float dS = fmaf(2.0f * x, cv[ob][1], fmaf(y, cv[ob][2], cv[ob][0]));
       const float d = x - y;
       const float sg = d > 0.0f ? w1 : (d < 0.0f ? -w1 : 0.0f);
