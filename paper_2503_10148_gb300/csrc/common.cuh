@@ -88,6 +88,112 @@ __device__ __forceinline__ float mufu_ex2(float x) {
   return y;
 }
 
+// ------------------------------------------------------------ packed FP32
+// Blackwell issues two FP32 additions, subtractions, multiplications or FMAs
+// as one instruction (add/sub/mul/fma.rn.f32x2), each element rounded
+// exactly as the scalar operation.  The per-pixel code of the render kernels
+// is written once over a value type V -- float (one pixel) or F2 (two pixels
+// of a lane) -- with masks MaskT<V> = bool or B2.  The scalar operations use
+// the _rn intrinsics, which the compiler does not contract into FMAs, so a
+// pixel gets bit-identical values whether it is evaluated alone or in a
+// pair, in the forward and in the backward.
+struct F2 {
+  float x, y;
+};
+struct B2 {
+  bool x, y;
+};
+
+#define SSS_PACKED_OP(name, ins)                                                                         \
+  __device__ __forceinline__ F2 name(F2 a, F2 b) {                                                      \
+    F2 d;                                                                                                \
+    asm("{.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t" ins               \
+        " pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"                                                     \
+        : "=f"(d.x), "=f"(d.y)                                                                           \
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                                       \
+    return d;                                                                                            \
+  }
+SSS_PACKED_OP(vadd, "add.rn.f32x2")
+SSS_PACKED_OP(vsub, "sub.rn.f32x2")
+SSS_PACKED_OP(vmul, "mul.rn.f32x2")
+#undef SSS_PACKED_OP
+
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) {
+  F2 d;
+  asm("{.reg .b64 pa, pb, pc, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\tmov.b64 pc, {%6, %7};\n\t"
+      "fma.rn.f32x2 pd, pa, pb, pc;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+template <class V>
+struct MaskOf;
+template <>
+struct MaskOf<float> {
+  using T = bool;
+};
+template <>
+struct MaskOf<F2> {
+  using T = B2;
+};
+template <class V>
+using MaskT = typename MaskOf<V>::T;
+
+template <class V>
+__device__ __forceinline__ V vsplat(float v);
+template <>
+__device__ __forceinline__ float vsplat<float>(float v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ F2 vsplat<F2>(float v) {
+  return F2{v, v};
+}
+
+// element-wise helpers (MUFU, min, comparisons, selection, mask logic)
+__device__ __forceinline__ float vlg2(float a) { return mufu_lg2(a); }
+__device__ __forceinline__ F2 vlg2(F2 a) { return F2{mufu_lg2(a.x), mufu_lg2(a.y)}; }
+__device__ __forceinline__ float vex2(float a) { return mufu_ex2(a); }
+__device__ __forceinline__ F2 vex2(F2 a) { return F2{mufu_ex2(a.x), mufu_ex2(a.y)}; }
+__device__ __forceinline__ float vrcp(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ F2 vrcp(F2 a) { return F2{__fdividef(1.0f, a.x), __fdividef(1.0f, a.y)}; }
+__device__ __forceinline__ float vlog1p(float a) { return log1pf(a); }
+__device__ __forceinline__ F2 vlog1p(F2 a) { return F2{log1pf(a.x), log1pf(a.y)}; }
+__device__ __forceinline__ float vexp(float a) { return expf(a); }
+__device__ __forceinline__ F2 vexp(F2 a) { return F2{expf(a.x), expf(a.y)}; }
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ F2 vmin(F2 a, float b) { return F2{fminf(a.x, b), fminf(a.y, b)}; }
+__device__ __forceinline__ bool vge(float a, float b) { return a >= b; }
+__device__ __forceinline__ B2 vge(F2 a, float b) { return B2{a.x >= b, a.y >= b}; }
+__device__ __forceinline__ bool vgt(float a, float b) { return a > b; }
+__device__ __forceinline__ B2 vgt(F2 a, float b) { return B2{a.x > b, a.y > b}; }
+__device__ __forceinline__ bool vlt(float a, float b) { return a < b; }
+__device__ __forceinline__ B2 vlt(F2 a, float b) { return B2{a.x < b, a.y < b}; }
+__device__ __forceinline__ float vsel(bool m, float a, float b) { return m ? a : b; }
+__device__ __forceinline__ F2 vsel(B2 m, F2 a, F2 b) { return F2{m.x ? a.x : b.x, m.y ? a.y : b.y}; }
+__device__ __forceinline__ bool mand(bool a, bool b) { return a && b; }
+__device__ __forceinline__ B2 mand(B2 a, B2 b) { return B2{a.x && b.x, a.y && b.y}; }
+__device__ __forceinline__ bool mandn(bool a, bool b) { return a && !b; }  // a and not b
+__device__ __forceinline__ B2 mandn(B2 a, B2 b) { return B2{a.x && !b.x, a.y && !b.y}; }
+__device__ __forceinline__ bool mor(bool a, bool b) { return a || b; }
+__device__ __forceinline__ B2 mor(B2 a, B2 b) { return B2{a.x || b.x, a.y || b.y}; }
+__device__ __forceinline__ bool many(bool a) { return a; }
+__device__ __forceinline__ bool many(B2 a) { return a.x || a.y; }
+__device__ __forceinline__ bool mall(bool a) { return a; }
+__device__ __forceinline__ bool mall(B2 a) { return a.x && a.y; }
+__device__ __forceinline__ float vsum(float a) { return a; }
+__device__ __forceinline__ float vsum(F2 a) { return a.x + a.y; }
+// element k (0 or 1) of a value or mask
+__device__ __forceinline__ float vget(float a, int) { return a; }
+__device__ __forceinline__ float vget(F2 a, int k) { return k ? a.y : a.x; }
+__device__ __forceinline__ bool mget(bool a, int) { return a; }
+__device__ __forceinline__ bool mget(B2 a, int k) { return k ? a.y : a.x; }
+
 // One (splat, pixel) evaluation shared by the forward and backward kernels so
 // that both take identical FP32 decisions.  Returns whether the pair
 // contributes (|alpha| = |o| T2D >= tau; the tile lists hold only pairs the
@@ -95,58 +201,72 @@ __device__ __forceinline__ float mufu_ex2(float x) {
 // separate h test is needed); the fields of r are computed either way
 // (finite for any finite offsets, alpha already clamped to
 // [-alpha_max, alpha_max]), so callers can evaluate all their pixels in
-// straight-line code and mask.  The opacity comes split per splat as
-// |o| and sign(o): |o| T2D is |o T2D| exactly, and the clamp is one min.  Fast path: two MUFU ops (lg2,
-// ex2).  For nu > kFastNuMax the exponent -(nu+2)/2 is large enough that the
-// absolute error of lg2.approx would show, so eval_pair_slow uses
-// log1pf/expf; callers pick the path per splat (uniform over a warp).
+// straight-line code and mask.  The opacity comes split per splat as |o| and
+// sign(o): |o| T2D is |o T2D| exactly, and the clamp is one min.  Fast path:
+// two MUFU ops (lg2, ex2).  For nu > kFastNuMax the exponent -(nu+2)/2 is
+// large enough that the absolute error of lg2.approx would show, so
+// eval_pair_slow uses log1pf/expf; callers pick the path per splat (uniform
+// over a warp).
+template <class V>
 struct PairEval {
-  float h, t2d, alpha, log_base;  // log_base = ln(1 + h/nu)
-  bool clamped;
+  V h, t2d, alpha, log_base;  // log_base = ln(1 + h/nu)
+  MaskT<V> clamped;
 };
 
-__device__ __forceinline__ float conic_h(float dx, float dy, float ca, float cb2, float cc) {
-  float t = ca * dx;
-  t = fmaf(cb2, dy, t);
-  return fmaf(dx, t, cc * dy * dy);
+// h = dx (a dx + 2 b dy) + c dy^2
+template <class V>
+__device__ __forceinline__ V conic_h(V dx, V dy, float ca, float cb2, float cc) {
+  const V t = vfma(vsplat<V>(ca), dx, vmul(vsplat<V>(cb2), dy));
+  return vfma(dx, t, vmul(vmul(vsplat<V>(cc), dy), dy));
 }
 
-__device__ __forceinline__ bool finish_pair(float h, float t2d, float lb, float oabs, float osgn, float tau,
-                                            float amax, PairEval& r) {
-  const float aabs = oabs * t2d;
+template <class V>
+__device__ __forceinline__ MaskT<V> finish_pair(V h, V t2d, V lb, float oabs, float osgn, float tau, float amax,
+                                                PairEval<V>& r) {
+  const V aabs = vmul(vsplat<V>(oabs), t2d);
   r.h = h;
   r.t2d = t2d;
-  r.alpha = osgn * fminf(aabs, amax);
+  r.alpha = vmul(vsplat<V>(osgn), vmin(aabs, amax));
   r.log_base = lb;
-  r.clamped = aabs > amax;
-  return aabs >= tau;
+  r.clamped = vgt(aabs, amax);
+  return vge(aabs, tau);
 }
 
-__device__ __forceinline__ bool eval_pair_fast(float dx, float dy, float ca, float cb2, float cc, float oabs,
-                                               float osgn, float nu, float inv_nu, float tau, float amax,
-                                               PairEval& r) {
-  const float h = conic_h(dx, dy, ca, cb2, cc);
+template <class V>
+__device__ __forceinline__ MaskT<V> eval_pair_fast(V dx, V dy, float ca, float cb2, float cc, float oabs, float osgn,
+                                                   float nu, float inv_nu, float tau, float amax, PairEval<V>& r) {
+  const V h = conic_h(dx, dy, ca, cb2, cc);
   const float e = fmaf(nu, -0.5f, -1.0f);  // -(nu + 2) / 2
-  const float l2 = mufu_lg2(fmaf(h, inv_nu, 1.0f));
-  return finish_pair(h, mufu_ex2(e * l2), l2 * 0.69314718055994531f, oabs, osgn, tau, amax, r);
+  const V l2 = vlg2(vfma(h, vsplat<V>(inv_nu), vsplat<V>(1.0f)));
+  return finish_pair(h, vex2(vmul(vsplat<V>(e), l2)), vmul(l2, vsplat<V>(0.69314718055994531f)), oabs, osgn, tau,
+                     amax, r);
 }
 
-__device__ __forceinline__ bool eval_pair_slow(float dx, float dy, float ca, float cb2, float cc, float oabs,
-                                               float osgn, float nu, float inv_nu, float tau, float amax,
-                                               PairEval& r) {
-  const float h = conic_h(dx, dy, ca, cb2, cc);
+template <class V>
+__device__ __forceinline__ MaskT<V> eval_pair_slow(V dx, V dy, float ca, float cb2, float cc, float oabs, float osgn,
+                                                   float nu, float inv_nu, float tau, float amax, PairEval<V>& r) {
+  const V h = conic_h(dx, dy, ca, cb2, cc);
   const float e = fmaf(nu, -0.5f, -1.0f);
-  const float lb = log1pf(h * inv_nu);
-  return finish_pair(h, expf(e * lb), lb, oabs, osgn, tau, amax, r);
+  const V lb = vlog1p(vmul(h, vsplat<V>(inv_nu)));
+  return finish_pair(h, vexp(vmul(vsplat<V>(e), lb)), lb, oabs, osgn, tau, amax, r);
 }
 
 // Gaussian kernel (the nu -> infinity limit; records carry nu = +inf):
 // T2D = exp(-h/2) = 2^(-h log2(e) / 2), one MUFU op.
-__device__ __forceinline__ bool eval_pair_gauss(float dx, float dy, float ca, float cb2, float cc, float oabs,
-                                                float osgn, float tau, float amax, PairEval& r) {
-  const float h = conic_h(dx, dy, ca, cb2, cc);
-  return finish_pair(h, mufu_ex2(h * -0.72134752044448170f), 0.0f, oabs, osgn, tau, amax, r);
+template <class V>
+__device__ __forceinline__ MaskT<V> eval_pair_gauss(V dx, V dy, float ca, float cb2, float cc, float oabs,
+                                                    float osgn, float tau, float amax, PairEval<V>& r) {
+  const V h = conic_h(dx, dy, ca, cb2, cc);
+  return finish_pair(h, vex2(vmul(h, vsplat<V>(-0.72134752044448170f))), vsplat<V>(0.0f), oabs, osgn, tau, amax,
+                     r);
 }
+
+// Pixels per value of a lane: pairs when the lane's pixel count is even.
+template <int NPIX>
+struct LaneVec {
+  static constexpr int L = (NPIX % 2 == 0) ? 2 : 1;
+  static constexpr int NV = NPIX / L;
+};
 
 // Offset of a pixel centre from the splat mean along one axis: fb is the
 // lane's first pixel minus the record origin (an exact small integer as a

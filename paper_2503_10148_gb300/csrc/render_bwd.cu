@@ -25,11 +25,14 @@
 // u < 1/4 (s < 1/7) the series to s^9 is used (truncation below 3e-9 of g),
 // above that the direct difference (cancellation at most 8x).
 // Each warp walks its own contributors back to front, 32 records per round
-// staged as in the forward.  Per splat a lane first sums its pixels (the
+// staged as in the forward, and evaluates a lane's pixels two at a time
+// with packed FP32 instructions where it has an even number of them.  Per splat a lane first sums its pixels (the
 // factors common to the splat, o and dT2D/dh's (nu+2)/(2 nu), are applied to
 // the sums once); the warp then reduces the 10 sums with a reduce-scatter
 // (12 shuffles instead of 10 x 5) and 10 lanes add the totals to the
 // splat's record with one RED each.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace sss {
@@ -73,12 +76,24 @@ __device__ __forceinline__ float log1p_minus_u(float u, float log_base) {
   }
   return log_base - u;
 }
+// two pixels: the series in packed form for both, then a per-element choice
+__device__ __forceinline__ F2 log1p_minus_u(F2 u, F2 log_base) {
+  const F2 sv = vmul(u, vrcp(vsub(vsplat<F2>(2.0f), u))), s2 = vmul(sv, sv);
+  F2 p = vfma(s2, vsplat<F2>(2.0f / 9.0f), vsplat<F2>(2.0f / 7.0f));
+  p = vfma(s2, p, vsplat<F2>(2.0f / 5.0f));
+  p = vfma(s2, p, vsplat<F2>(2.0f / 3.0f));
+  const F2 series = vfma(vmul(s2, sv), p, vmul(u, sv));
+  return vsel(vlt(u, 0.25f), series, vsub(log_base, u));
+}
 
 template <int PW, int PH, bool PAPER_NU>
 __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const sss_frame_plan P, void* ws,
-                                                       const float* __restrict__ dl_drgb) {
+                                                                           const float* __restrict__ dl_drgb) {
   constexpr int NPIX = PW * PH;
   constexpr int TW = 16 * PW, TH = 16 * PH;
+  constexpr int L = LaneVec<NPIX>::L, NV = LaneVec<NPIX>::NV;
+  using V = typename std::conditional<L == 2, F2, float>::type;
+  using M = MaskT<V>;
   __shared__ WarpBuf s_wb[2];
 
   // four CTAs of two warps per tile; warp w of the tile's 2 x 4 layout
@@ -99,26 +114,46 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
   const float* Tf = ws_ptr<float>(ws, P.ws_off_T);
   const uint32_t* Lf = ws_ptr<uint32_t>(ws, P.ws_off_last);
   const float* gimg = dl_drgb + 3 * (size_t)J.pix_base;
-  float T[NPIX], Sg[NPIX], g[NPIX][3];  // Sg = dL/dC . (colour behind)
+  // pixel p = L v + k of the lane is value v, element k
+  V T[NV], Sg[NV], g[NV][3];  // Sg = dL/dC . (colour behind)
   uint32_t last[NPIX];
   uint32_t lane_max = 0;
 #pragma unroll
-  for (int p = 0; p < NPIX; ++p) {
-    const int x = lx + p % PW, y = ly + p / PW;
-    if (x < W && y < H) {
-      const size_t o = (size_t)y * W + x;
-      T[p] = Tf[J.pix_base + o];
-      last[p] = Lf[J.pix_base + o];
-      g[p][0] = gimg[o];
-      g[p][1] = gimg[hw + o];
-      g[p][2] = gimg[2 * hw + o];
-    } else {
-      T[p] = 1.0f;
-      last[p] = 0u;
-      g[p][0] = g[p][1] = g[p][2] = 0.0f;
+  for (int v = 0; v < NV; ++v) {
+    float t[2], gg[2][3];
+#pragma unroll
+    for (int kk = 0; kk < L; ++kk) {
+      const int p = L * v + kk;
+      const int x = lx + p % PW, y = ly + p / PW;
+      if (x < W && y < H) {
+        const size_t o = (size_t)y * W + x;
+        t[kk] = Tf[J.pix_base + o];
+        last[p] = Lf[J.pix_base + o];
+        gg[kk][0] = gimg[o];
+        gg[kk][1] = gimg[hw + o];
+        gg[kk][2] = gimg[2 * hw + o];
+      } else {
+        t[kk] = 1.0f;
+        last[p] = 0u;
+        gg[kk][0] = gg[kk][1] = gg[kk][2] = 0.0f;
+      }
+      lane_max = max(lane_max, last[p]);
     }
-    Sg[p] = fmaf(g[p][0], cfg.bg[0], fmaf(g[p][1], cfg.bg[1], g[p][2] * cfg.bg[2]));
-    lane_max = max(lane_max, last[p]);
+    float sg[2];
+#pragma unroll
+    for (int kk = 0; kk < L; ++kk)
+      sg[kk] = fmaf(gg[kk][0], cfg.bg[0], fmaf(gg[kk][1], cfg.bg[1], gg[kk][2] * cfg.bg[2]));
+    if constexpr (L == 2) {
+      T[v] = F2{t[0], t[1]};
+      Sg[v] = F2{sg[0], sg[1]};
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) g[v][ch] = F2{gg[0][ch], gg[1][ch]};
+    } else {
+      T[v] = t[0];
+      Sg[v] = sg[0];
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) g[v][ch] = gg[0][ch];
+    }
   }
   const uint32_t warp_max = __reduce_max_sync(0xffffffffu, lane_max);
 
@@ -175,118 +210,134 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
         const int si = 31 - __clz(m);
         m &= ~(1u << si);
         const uint32_t pos = lo + si;
-      const float4 a = S.a[k][si], b = S.b[k][si], c = S.c[k][si];
-      const float cb2 = 2.0f * a.w;
-      const float nu = b.w, inv_nu = __fdividef(1.0f, nu), o = b.y;
-      const float oabs = fabsf(o), osgn = copysignf(1.0f, o);
-      int ox, oy;
-      rec_origin(c.w, ox, oy);
-      const float fbx = (float)(lx - ox), fby = (float)(ly - oy);
-      // all pixels of the lane in straight-line code, masked; nu branch
-      // uniform over the warp
-      PairEval r[NPIX];
-      bool ok[NPIX];
-      float dxs[PW], dys[PH];
+        const float4 a = S.a[k][si], b = S.b[k][si], c = S.c[k][si];
+        const float cb2 = 2.0f * a.w;
+        const float nu = b.w, inv_nu = __fdividef(1.0f, nu), o = b.y;
+        const float oabs = fabsf(o), osgn = copysignf(1.0f, o);
+        int ox, oy;
+        rec_origin(c.w, ox, oy);
+        const float fbx = (float)(lx - ox), fby = (float)(ly - oy);
+        float dxs[PW], dys[PH];
 #pragma unroll
-      for (int i = 0; i < PW; ++i) dxs[i] = pixel_offset(fbx, i, a.x);
+        for (int ii = 0; ii < PW; ++ii) dxs[ii] = pixel_offset(fbx, ii, a.x);
 #pragma unroll
-      for (int j = 0; j < PH; ++j) dys[j] = pixel_offset(fby, j, a.y);
-      if (nu <= kFastNuMax) {
+        for (int jj = 0; jj < PH; ++jj) dys[jj] = pixel_offset(fby, jj, a.y);
+        V dx[NV], dy[NV];
 #pragma unroll
-        for (int p = 0; p < NPIX; ++p)
-          ok[p] = eval_pair_fast(dxs[p % PW], dys[p / PW], a.z, cb2, b.x, oabs, osgn, nu, inv_nu, tau, amax, r[p]);
-      } else if (isinf(nu)) {
+        for (int v = 0; v < NV; ++v) {
+          if constexpr (L == 2) {
+            dx[v] = F2{dxs[(L * v) % PW], dxs[(L * v + 1) % PW]};
+            dy[v] = F2{dys[(L * v) / PW], dys[(L * v + 1) / PW]};
+          } else {
+            dx[v] = dxs[v % PW];
+            dy[v] = dys[v / PW];
+          }
+        }
+        // all pixels of the lane in straight-line code, masked; nu branch
+        // uniform over the warp
+        PairEval<V> r[NV];
+        M ok[NV];
+        if (nu <= kFastNuMax) {
 #pragma unroll
-        for (int p = 0; p < NPIX; ++p)
-          ok[p] = eval_pair_gauss(dxs[p % PW], dys[p / PW], a.z, cb2, b.x, oabs, osgn, tau, amax, r[p]);
-      } else {
+          for (int v = 0; v < NV; ++v)
+            ok[v] = eval_pair_fast(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, nu, inv_nu, tau, amax, r[v]);
+        } else if (isinf(nu)) {
 #pragma unroll
-        for (int p = 0; p < NPIX; ++p)
-          ok[p] = eval_pair_slow(dxs[p % PW], dys[p / PW], a.z, cb2, b.x, oabs, osgn, nu, inv_nu, tau, amax, r[p]);
-      }
-      // per-lane sums: rgb (v7..9), st = dL/dalpha T2D (v5 = dL/do), st
-      // times the nu factor (v6 / o) and, per pixel, q = st / (1 + h/nu),
-      // with dL/dh = o (dT2D/dh / T2D) (1 + h/nu) q; dL/dmean and dL/dconic
-      // follow from q-weighted moments of the pixel offsets (h is quadratic
-      // in the offsets, so its gradients are linear in these moments)
-      float v[10];
-      float s5 = 0.0f, s6 = 0.0f, r7 = 0.0f, r8 = 0.0f, r9 = 0.0f;
-      float q[NPIX];
-      bool any = false;
+          for (int v = 0; v < NV; ++v)
+            ok[v] = eval_pair_gauss(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, tau, amax, r[v]);
+        } else {
 #pragma unroll
-      for (int p = 0; p < NPIX; ++p) {
-        const bool live = ok[p] && pos < last[p];
-        any = any || live;
-        const float al = live ? r[p].alpha : 0.0f;
-        const float Tk = live ? T[p] * __fdividef(1.0f, 1.0f - al) : T[p];
-        T[p] = Tk;
-        const float w = al * Tk;  // 0 unless live
-        r7 = fmaf(w, g[p][0], r7);
-        r8 = fmaf(w, g[p][1], r8);
-        r9 = fmaf(w, g[p][2], r9);
-        // dL/dalpha = T_k dL/dC . (rgb - B) with B the colour behind; only
-        // its projection on dL/dC is needed: Sg = dL/dC . B, and
-        // B <- alpha rgb + (1 - alpha) B gives Sg <- Sg + alpha (g.rgb - Sg)
-        const float gdiff = fmaf(g[p][0], c.x, fmaf(g[p][1], c.y, g[p][2] * c.z)) - Sg[p];
-        Sg[p] = fmaf(al, gdiff, Sg[p]);
-        const float dl_da = (live && !r[p].clamped) ? gdiff * Tk : 0.0f;
-        const float st = dl_da * r[p].t2d;
-        s5 += st;
-        const float inv_base = __fdividef(1.0f, fmaf(r[p].h, inv_nu, 1.0f));
-        q[p] = st * inv_base;
-        const float u = r[p].h * inv_nu * inv_base;  // x / (1 + x)
-        // paper form: (nu+2) x / (2 nu (1+x)) = u/2 + u/nu; exact: u/nu - g/2
-        const float dnu = PAPER_NU ? fmaf(0.5f, u, u * inv_nu)
-                                   : fmaf(-0.5f, log1p_minus_u(u, r[p].log_base), u * inv_nu);
-        s6 = fmaf(st, dnu, s6);
-      }
-      // moments of q over the lane's PW x PH pixels from column and row sums
-      float cq[PW], cqy[PW], rq[PH];
+          for (int v = 0; v < NV; ++v)
+            ok[v] = eval_pair_slow(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, nu, inv_nu, tau, amax, r[v]);
+        }
+        // per-lane sums: rgb (v7..9), st = dL/dalpha T2D (v5 = dL/do), st
+        // times the nu factor (v6 / o) and, per pixel, q = st / (1 + h/nu),
+        // with dL/dh = o (dT2D/dh / T2D) (1 + h/nu) q; dL/dmean and dL/dconic
+        // follow from q-weighted moments of the pixel offsets (h is quadratic
+        // in the offsets, so its gradients are linear in these moments)
+        const V one = vsplat<V>(1.0f), zero = vsplat<V>(0.0f), ivn = vsplat<V>(inv_nu);
+        const V cr = vsplat<V>(c.x), cg = vsplat<V>(c.y), cbl = vsplat<V>(c.z);
+        V s5 = zero, s6 = zero, r7 = zero, r8 = zero, r9 = zero, q[NV];
+        bool any = false;
 #pragma unroll
-      for (int i = 0; i < PW; ++i) cq[i] = cqy[i] = 0.0f;
+        for (int v = 0; v < NV; ++v) {
+          M before;  // the splat is in front of the pixel's last contributor
+          if constexpr (L == 2) before = B2{pos < last[L * v], pos < last[L * v + 1]};
+          else before = pos < last[v];
+          const M live = mand(ok[v], before);
+          any = any || many(live);
+          const V al = vsel(live, r[v].alpha, zero);
+          const V Tk = vsel(live, vmul(T[v], vrcp(vsub(one, al))), T[v]);
+          T[v] = Tk;
+          const V w = vmul(al, Tk);  // 0 unless live
+          r7 = vfma(w, g[v][0], r7);
+          r8 = vfma(w, g[v][1], r8);
+          r9 = vfma(w, g[v][2], r9);
+          // dL/dalpha = T_k dL/dC . (rgb - B) with B the colour behind; only
+          // its projection on dL/dC is needed: Sg = dL/dC . B, and
+          // B <- alpha rgb + (1 - alpha) B gives Sg <- Sg + alpha (g.rgb - Sg)
+          const V gdiff = vsub(vfma(g[v][0], cr, vfma(g[v][1], cg, vmul(g[v][2], cbl))), Sg[v]);
+          Sg[v] = vfma(al, gdiff, Sg[v]);
+          const V dl_da = vsel(mandn(live, r[v].clamped), vmul(gdiff, Tk), zero);
+          const V st = vmul(dl_da, r[v].t2d);
+          s5 = vadd(s5, st);
+          const V inv_base = vrcp(vfma(r[v].h, ivn, one));
+          q[v] = vmul(st, inv_base);
+          const V u = vmul(vmul(r[v].h, ivn), inv_base);  // x / (1 + x)
+          // paper form: (nu+2) x / (2 nu (1+x)) = u/2 + u/nu; exact: u/nu - g/2
+          const V dnu = PAPER_NU ? vfma(vsplat<V>(0.5f), u, vmul(u, ivn))
+                                 : vfma(vsplat<V>(-0.5f), log1p_minus_u(u, r[v].log_base), vmul(u, ivn));
+          s6 = vfma(st, dnu, s6);
+        }
+        // moments of q over the lane's PW x PH pixels from column and row sums
+        float cq[PW], cqy[PW], rq[PH];
 #pragma unroll
-      for (int j = 0; j < PH; ++j) rq[j] = 0.0f;
+        for (int ii = 0; ii < PW; ++ii) cq[ii] = cqy[ii] = 0.0f;
 #pragma unroll
-      for (int p = 0; p < NPIX; ++p) {
-        cq[p % PW] += q[p];
-        cqy[p % PW] = fmaf(q[p], dys[p / PW], cqy[p % PW]);
-        rq[p / PW] += q[p];
-      }
-      float m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f, m5 = 0.0f;
+        for (int jj = 0; jj < PH; ++jj) rq[jj] = 0.0f;
 #pragma unroll
-      for (int i = 0; i < PW; ++i) {
-        const float dq = dxs[i] * cq[i];
-        m1 += dq;
-        m3 = fmaf(dq, dxs[i], m3);
-        m4 = fmaf(dxs[i], cqy[i], m4);
-      }
+        for (int p = 0; p < NPIX; ++p) {
+          const float qp = vget(q[p / L], p % L);
+          cq[p % PW] += qp;
+          cqy[p % PW] = fmaf(qp, dys[p / PW], cqy[p % PW]);
+          rq[p / PW] += qp;
+        }
+        float m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f, m5 = 0.0f;
 #pragma unroll
-      for (int j = 0; j < PH; ++j) {
-        const float dq = dys[j] * rq[j];
-        m2 += dq;
-        m5 = fmaf(dq, dys[j], m5);
-      }
-      // dT2D/dh / T2D = -(nu+2)/(2 nu) / (1 + h/nu); -1/2 for the Gaussian
-      // (nu = inf, inv_nu = 0)
-      const float kq = o * (isinf(nu) ? -0.5f : fmaf(nu, -0.5f, -1.0f) * inv_nu);
-      m1 *= kq;
-      m2 *= kq;
-      // dh/dmean = -2 (a dx + b dy, b dx + c dy); dh/dconic = (dx^2, 2 dx dy, dy^2)
-      v[0] = -2.0f * fmaf(a.z, m1, a.w * m2);
-      v[1] = -2.0f * fmaf(a.w, m1, b.x * m2);
-      v[2] = kq * m3;
-      v[3] = 2.0f * kq * m4;
-      v[4] = kq * m5;
-      v[5] = s5;
-      v[6] = o * s6;
-      v[7] = r7;
-      v[8] = r8;
-      v[9] = r9;
-      if (__any_sync(0xffffffffu, any)) {
-        int slot;
-        const float tot = warp_reduce_scatter10(v, lane, &slot);
-        if (slot >= 0) atomicAdd(g2d + (size_t)S.e[k][si] * 12 + slot, tot);
-      }
+        for (int ii = 0; ii < PW; ++ii) {
+          const float dq = dxs[ii] * cq[ii];
+          m1 += dq;
+          m3 = fmaf(dq, dxs[ii], m3);
+          m4 = fmaf(dxs[ii], cqy[ii], m4);
+        }
+#pragma unroll
+        for (int jj = 0; jj < PH; ++jj) {
+          const float dq = dys[jj] * rq[jj];
+          m2 += dq;
+          m5 = fmaf(dq, dys[jj], m5);
+        }
+        // dT2D/dh / T2D = -(nu+2)/(2 nu) / (1 + h/nu); -1/2 for the Gaussian
+        // (nu = inf, inv_nu = 0)
+        const float kq = o * (isinf(nu) ? -0.5f : fmaf(nu, -0.5f, -1.0f) * inv_nu);
+        m1 *= kq;
+        m2 *= kq;
+        // dh/dmean = -2 (a dx + b dy, b dx + c dy); dh/dconic = (dx^2, 2 dx dy, dy^2)
+        float vv[10];
+        vv[0] = -2.0f * fmaf(a.z, m1, a.w * m2);
+        vv[1] = -2.0f * fmaf(a.w, m1, b.x * m2);
+        vv[2] = kq * m3;
+        vv[3] = 2.0f * kq * m4;
+        vv[4] = kq * m5;
+        vv[5] = vsum(s5);
+        vv[6] = o * vsum(s6);
+        vv[7] = vsum(r7);
+        vv[8] = vsum(r8);
+        vv[9] = vsum(r9);
+        if (__any_sync(0xffffffffu, any)) {
+          int slot;
+          const float tot = warp_reduce_scatter10(vv, lane, &slot);
+          if (slot >= 0) atomicAdd(g2d + (size_t)S.e[k][si] * 12 + slot, tot);
+        }
       }
       __syncwarp();  // every lane is done with buffer k before it is refilled
     }

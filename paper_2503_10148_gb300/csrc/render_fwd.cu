@@ -1,16 +1,20 @@
 // a4: per-pixel front-to-back compositing with signed alpha
 // (Sec. 3.4 Eq. SSS_color; signed opacity Sec. 3.3).
 //
-// One CTA of 256 threads per image tile of (16 PW) x (16 PH) pixels.  Warps
-// are laid out 2 x 4 over the tile; warp w owns an (8 PW) x (4 PH) box and
-// lane l a PW x PH block of pixels inside it.  The tile's splat list is
-// staged in shared memory B splats at a time (48-byte records gathered by
-// entry index, double buffered: the next batch is loaded while this one is
-// processed).  Each warp then tests the B staged splats against its own
-// box in parallel (one splat per lane, exact ellipse/box test) and walks
-// only the survivors, in list (= depth) order, so pairs whose ellipse misses
-// the warp's 32 PW PH pixels cost nothing.  A warp stops evaluating when all
-// its pixels are done; the CTA stops staging when all warps are done.
+// An image tile of (16 PW) x (16 PH) pixels is covered by eight warps laid
+// out 2 x 4, run as four CTAs of two warps; warp w owns an (8 PW) x (4 PH)
+// box and lane l a PW x PH block of pixels inside it.  Warps are
+// independent (no CTA barrier): each walks the tile's list in rounds of 32
+// records, one 48-byte record per lane gathered by entry index with
+// cp.async into the warp's own double buffer (the next round is in flight
+// while this one is evaluated).  The warp tests the 32 staged splats against
+// its box in parallel (exact ellipse/box test) and walks only the
+// survivors, in list (= depth) order, so pairs whose ellipse misses the
+// warp's 32 PW PH pixels cost nothing; it stops when all its pixels are
+// done.  A lane's pixels are evaluated two at a time with packed FP32
+// instructions where it has an even number of them.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace sss {
@@ -20,6 +24,9 @@ template <int PW, int PH, bool COUNT>
 __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, void* ws, float* __restrict__ out_rgb) {
   constexpr int NPIX = PW * PH;
   constexpr int TW = 16 * PW, TH = 16 * PH;
+  constexpr int L = LaneVec<NPIX>::L, NV = LaneVec<NPIX>::NV;
+  using V = typename std::conditional<L == 2, F2, float>::type;
+  using M = MaskT<V>;
   __shared__ WarpBuf s_wb[2];
 
   // four CTAs of two warps per tile; warp w of the tile's 2 x 4 layout
@@ -35,20 +42,27 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
   const int lx = bx + (lane & 7) * PW, ly = by + (lane >> 3) * PH;
   const int W = J.cam.width, H = J.cam.height;
 
-  float T[NPIX], C[NPIX][3];
+  // pixel p = L v + k of the lane is value v, element k
+  V T[NV], C[NV][3];
+  M done[NV];
   uint32_t last[NPIX];
-  bool done[NPIX];
 #pragma unroll
-  for (int p = 0; p < NPIX; ++p) {
-    const int x = lx + p % PW, y = ly + p / PW;
-    done[p] = !(x < W && y < H);
-    T[p] = 1.0f;
-    C[p][0] = C[p][1] = C[p][2] = 0.0f;
-    last[p] = 0u;
+  for (int v = 0; v < NV; ++v) {
+    bool d[2] = {false, false};
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+      const int p = L * v + k;
+      d[k] = !(lx + p % PW < W && ly + p / PW < H);
+      last[p] = 0u;
+    }
+    if constexpr (L == 2) done[v] = B2{d[0], d[1]};
+    else done[v] = d[0];
+    T[v] = vsplat<V>(1.0f);
+    C[v][0] = C[v][1] = C[v][2] = vsplat<V>(0.0f);
   }
   bool lane_done = true;
 #pragma unroll
-  for (int p = 0; p < NPIX; ++p) lane_done = lane_done && done[p];
+  for (int v = 0; v < NV; ++v) lane_done = lane_done && mall(done[v]);
   bool warp_done = __all_sync(0xffffffffu, lane_done);
 
   const uint2 range = ws_ptr<uint2>(ws, P.ws_off_ranges)[tile];
@@ -91,54 +105,69 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
       while (m && !warp_done) {
         const int si = __ffs(m) - 1;
         m &= m - 1;
-      const float4 a = S.a[k][si], b = S.b[k][si], c = S.c[k][si];
-      const float cb2 = 2.0f * a.w, inv_nu = __fdividef(1.0f, b.w);
-      const float oabs = fabsf(b.y), osgn = copysignf(1.0f, b.y);
-      int ox, oy;
-      rec_origin(c.w, ox, oy);
-      const float fbx = (float)(lx - ox), fby = (float)(ly - oy);
-      const uint32_t pos1 = p0 + si + 1;
-      // every pixel of the lane through the same straight-line code (no
-      // branches between pixels, so their chains interleave); the nu
-      // branch is uniform over the warp
-      PairEval r[NPIX];
-      bool ok[NPIX];
-      if (b.w <= kFastNuMax) {
+        const float4 a = S.a[k][si], b = S.b[k][si], c = S.c[k][si];
+        const float cb2 = 2.0f * a.w, inv_nu = __fdividef(1.0f, b.w);
+        const float oabs = fabsf(b.y), osgn = copysignf(1.0f, b.y);
+        int ox, oy;
+        rec_origin(c.w, ox, oy);
+        const float fbx = (float)(lx - ox), fby = (float)(ly - oy);
+        const uint32_t pos1 = p0 + si + 1;
+        V dx[NV], dy[NV];
 #pragma unroll
-        for (int p = 0; p < NPIX; ++p)
-          ok[p] = eval_pair_fast(pixel_offset(fbx, p % PW, a.x), pixel_offset(fby, p / PW, a.y), a.z, cb2,
-                                 b.x, oabs, osgn, b.w, inv_nu, tau, amax, r[p]);
-      } else if (isinf(b.w)) {
+        for (int v = 0; v < NV; ++v) {
+          if constexpr (L == 2) {
+            dx[v] = F2{pixel_offset(fbx, (L * v) % PW, a.x), pixel_offset(fbx, (L * v + 1) % PW, a.x)};
+            dy[v] = F2{pixel_offset(fby, (L * v) / PW, a.y), pixel_offset(fby, (L * v + 1) / PW, a.y)};
+          } else {
+            dx[v] = pixel_offset(fbx, v % PW, a.x);
+            dy[v] = pixel_offset(fby, v / PW, a.y);
+          }
+        }
+        // every pixel of the lane through the same straight-line code (no
+        // branches between pixels, so their chains interleave); the nu
+        // branch is uniform over the warp
+        PairEval<V> r[NV];
+        M ok[NV];
+        if (b.w <= kFastNuMax) {
 #pragma unroll
-        for (int p = 0; p < NPIX; ++p)
-          ok[p] = eval_pair_gauss(pixel_offset(fbx, p % PW, a.x), pixel_offset(fby, p / PW, a.y), a.z, cb2,
-                                  b.x, oabs, osgn, tau, amax, r[p]);
-      } else {
+          for (int v = 0; v < NV; ++v)
+            ok[v] = eval_pair_fast(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, b.w, inv_nu, tau, amax, r[v]);
+        } else if (isinf(b.w)) {
 #pragma unroll
-        for (int p = 0; p < NPIX; ++p)
-          ok[p] = eval_pair_slow(pixel_offset(fbx, p % PW, a.x), pixel_offset(fby, p / PW, a.y), a.z, cb2,
-                                 b.x, oabs, osgn, b.w, inv_nu, tau, amax, r[p]);
-      }
+          for (int v = 0; v < NV; ++v)
+            ok[v] = eval_pair_gauss(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, tau, amax, r[v]);
+        } else {
 #pragma unroll
-      for (int p = 0; p < NPIX; ++p) {
-        if (COUNT) n_eval += done[p] ? 0u : 1u;
-        const bool live = ok[p] && !done[p];
-        const float Tn = T[p] * (1.0f - r[p].alpha);
-        const bool term = live && Tn < tmin;  // stops before this splat
-        const bool add = live && !term;
-        const float w = add ? r[p].alpha * T[p] : 0.0f;
-        C[p][0] = fmaf(w, c.x, C[p][0]);
-        C[p][1] = fmaf(w, c.y, C[p][1]);
-        C[p][2] = fmaf(w, c.z, C[p][2]);
-        T[p] = add ? Tn : T[p];
-        last[p] = add ? pos1 : last[p];
-        done[p] = done[p] || term;
-        if (COUNT) n_contrib += add ? 1u : 0u;
-      }
-      bool ld = true;
+          for (int v = 0; v < NV; ++v)
+            ok[v] = eval_pair_slow(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, b.w, inv_nu, tau, amax, r[v]);
+        }
+        const V one = vsplat<V>(1.0f), zero = vsplat<V>(0.0f);
+        const V cr = vsplat<V>(c.x), cg = vsplat<V>(c.y), cbl = vsplat<V>(c.z);
+        bool ld = true;
 #pragma unroll
-      for (int p = 0; p < NPIX; ++p) ld = ld && done[p];
-      warp_done = __all_sync(0xffffffffu, ld);
+        for (int v = 0; v < NV; ++v) {
+          if (COUNT) {
+#pragma unroll
+            for (int kk = 0; kk < L; ++kk) n_eval += mget(done[v], kk) ? 0u : 1u;
+          }
+          const M live = mandn(ok[v], done[v]);
+          const V Tn = vmul(T[v], vsub(one, r[v].alpha));
+          const M term = mand(live, vlt(Tn, tmin));  // stops before this splat
+          const M add = mandn(live, term);
+          const V w = vsel(add, vmul(r[v].alpha, T[v]), zero);
+          C[v][0] = vfma(w, cr, C[v][0]);
+          C[v][1] = vfma(w, cg, C[v][1]);
+          C[v][2] = vfma(w, cbl, C[v][2]);
+          T[v] = vsel(add, Tn, T[v]);
+#pragma unroll
+          for (int kk = 0; kk < L; ++kk) {
+            last[L * v + kk] = mget(add, kk) ? pos1 : last[L * v + kk];
+            if (COUNT) n_contrib += mget(add, kk) ? 1u : 0u;
+          }
+          done[v] = mor(done[v], term);
+          ld = ld && mall(done[v]);
+        }
+        warp_done = __all_sync(0xffffffffu, ld);
       }
       __syncwarp();  // every lane is done with buffer k before it is refilled
     }
@@ -161,11 +190,13 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
   for (int p = 0; p < NPIX; ++p) {
     const int x = lx + p % PW, y = ly + p / PW;
     if (x < W && y < H) {
+      const int v = p / L, kk = p % L;
       const size_t o = (size_t)y * W + x;
-      img[o] = fmaf(T[p], cfg.bg[0], C[p][0]);
-      img[hw + o] = fmaf(T[p], cfg.bg[1], C[p][1]);
-      img[2 * hw + o] = fmaf(T[p], cfg.bg[2], C[p][2]);
-      Tout[J.pix_base + o] = T[p];
+      const float Tp = vget(T[v], kk);
+      img[o] = fmaf(Tp, cfg.bg[0], vget(C[v][0], kk));
+      img[hw + o] = fmaf(Tp, cfg.bg[1], vget(C[v][1], kk));
+      img[2 * hw + o] = fmaf(Tp, cfg.bg[2], vget(C[v][2], kk));
+      Tout[J.pix_base + o] = Tp;
       Lout[J.pix_base + o] = last[p];
     }
   }
