@@ -267,7 +267,9 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
           const M live = mand(ok[v], before);
           any = any || many(live);
           const V al = vsel(live, r[v].alpha, zero);
-          const V Tk = vsel(live, vmul(T[v], vrcp(vsub(one, al))), T[v]);
+          // T_k = T_{k+1} / (1 - alpha); with al = 0 off the live pixels the
+          // MUFU reciprocal of 1 is exactly 1, so T is kept bit for bit
+          const V Tk = vmul(T[v], vrcp(vsub(one, al)));
           T[v] = Tk;
           const V w = vmul(al, Tk);  // 0 unless live
           r7 = vfma(w, g[v][0], r7);
@@ -290,6 +292,20 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
           s6 = vfma(st, dnu, s6);
         }
         // moments of q over the lane's PW x PH pixels from column and row sums
+        float m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f, m5 = 0.0f;
+        if constexpr (PW == 2 && PH == 2) {
+          // value v is row v: columns packed as (col 0, col 1)
+          const F2 cq = vadd(q[0], q[1]);                    // per-column sums
+          const F2 cqy = vfma(q[1], dy[1], vmul(q[0], dy[0]));  // per-column sums of q dy
+          const F2 dq = vmul(dx[0], cq);
+          m1 = vsum(dq);
+          m3 = vsum(vmul(dq, dx[0]));
+          m4 = vsum(vmul(dx[0], cqy));
+          const F2 dyr = F2{dys[0], dys[1]}, rq = F2{vsum(q[0]), vsum(q[1])};  // per-row sums
+          const F2 dr = vmul(dyr, rq);
+          m2 = vsum(dr);
+          m5 = vsum(vmul(dr, dyr));
+        } else {
         float cq[PW], cqy[PW], rq[PH];
 #pragma unroll
         for (int ii = 0; ii < PW; ++ii) cq[ii] = cqy[ii] = 0.0f;
@@ -302,7 +318,6 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
           cqy[p % PW] = fmaf(qp, dys[p / PW], cqy[p % PW]);
           rq[p / PW] += qp;
         }
-        float m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f, m5 = 0.0f;
 #pragma unroll
         for (int ii = 0; ii < PW; ++ii) {
           const float dq = dxs[ii] * cq[ii];
@@ -315,6 +330,7 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
           const float dq = dys[jj] * rq[jj];
           m2 += dq;
           m5 = fmaf(dq, dys[jj], m5);
+        }
         }
         // dT2D/dh / T2D = -(nu+2)/(2 nu) / (1 + h/nu); -1/2 for the Gaussian
         // (nu = inf, inv_nu = 0)

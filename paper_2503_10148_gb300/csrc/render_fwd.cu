@@ -154,11 +154,15 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
           const V Tn = vmul(T[v], vsub(one, r[v].alpha));
           const M term = mand(live, vlt(Tn, tmin));  // stops before this splat
           const M add = mandn(live, term);
-          const V w = vsel(add, vmul(r[v].alpha, T[v]), zero);
+          // alpha where the splat is composited, else 0: T (1 - 0) = T exactly,
+          // so one select serves the weight and the transmittance update
+          // (the ALU pipe is the busier one here)
+          const V ae = vsel(add, r[v].alpha, zero);
+          const V w = vmul(ae, T[v]);
           C[v][0] = vfma(w, cr, C[v][0]);
           C[v][1] = vfma(w, cg, C[v][1]);
           C[v][2] = vfma(w, cbl, C[v][2]);
-          T[v] = vsel(add, Tn, T[v]);
+          T[v] = vmul(T[v], vsub(one, ae));
 #pragma unroll
           for (int kk = 0; kk < L; ++kk) {
             last[L * v + kk] = mget(add, kk) ? pos1 : last[L * v + kk];
