@@ -97,21 +97,29 @@ __device__ __forceinline__ float mufu_ex2(float x) {
 // the _rn intrinsics, which the compiler does not contract into FMAs, so a
 // pixel gets bit-identical values whether it is evaluated alone or in a
 // pair, in the forward and in the backward.
+// F2 holds its two floats in one 64-bit register (lo = element 0), the
+// operand form of the packed instructions; elements are unpacked only for
+// element-wise work.
 struct F2 {
-  float x, y;
+  unsigned long long v;
 };
 struct B2 {
   bool x, y;
 };
+__device__ __forceinline__ F2 f2(float x, float y) {
+  F2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ void f2u(F2 a, float& x, float& y) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
+}
 
-#define SSS_PACKED_OP(name, ins)                                                                         \
-  __device__ __forceinline__ F2 name(F2 a, F2 b) {                                                      \
-    F2 d;                                                                                                \
-    asm("{.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t" ins               \
-        " pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"                                                     \
-        : "=f"(d.x), "=f"(d.y)                                                                           \
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                                       \
-    return d;                                                                                            \
+#define SSS_PACKED_OP(name, ins)                                                   \
+  __device__ __forceinline__ F2 name(F2 a, F2 b) {                                \
+    F2 d;                                                                          \
+    asm(ins " %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));                      \
+    return d;                                                                      \
   }
 SSS_PACKED_OP(vadd, "add.rn.f32x2")
 SSS_PACKED_OP(vsub, "sub.rn.f32x2")
@@ -120,10 +128,7 @@ SSS_PACKED_OP(vmul, "mul.rn.f32x2")
 
 __device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) {
   F2 d;
-  asm("{.reg .b64 pa, pb, pc, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\tmov.b64 pc, {%6, %7};\n\t"
-      "fma.rn.f32x2 pd, pa, pb, pc;\n\tmov.b64 {%0, %1}, pd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
   return d;
 }
 __device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
@@ -152,30 +157,71 @@ __device__ __forceinline__ float vsplat<float>(float v) {
 }
 template <>
 __device__ __forceinline__ F2 vsplat<F2>(float v) {
-  return F2{v, v};
+  return f2(v, v);
 }
 
 // element-wise helpers (MUFU, min, comparisons, selection, mask logic)
 __device__ __forceinline__ float vlg2(float a) { return mufu_lg2(a); }
-__device__ __forceinline__ F2 vlg2(F2 a) { return F2{mufu_lg2(a.x), mufu_lg2(a.y)}; }
+__device__ __forceinline__ F2 vlg2(F2 a) {
+  float x, y;
+  f2u(a, x, y);
+  return f2(mufu_lg2(x), mufu_lg2(y));
+}
 __device__ __forceinline__ float vex2(float a) { return mufu_ex2(a); }
-__device__ __forceinline__ F2 vex2(F2 a) { return F2{mufu_ex2(a.x), mufu_ex2(a.y)}; }
+__device__ __forceinline__ F2 vex2(F2 a) {
+  float x, y;
+  f2u(a, x, y);
+  return f2(mufu_ex2(x), mufu_ex2(y));
+}
 __device__ __forceinline__ float vrcp(float a) { return __fdividef(1.0f, a); }
-__device__ __forceinline__ F2 vrcp(F2 a) { return F2{__fdividef(1.0f, a.x), __fdividef(1.0f, a.y)}; }
+__device__ __forceinline__ F2 vrcp(F2 a) {
+  float x, y;
+  f2u(a, x, y);
+  return f2(__fdividef(1.0f, x), __fdividef(1.0f, y));
+}
 __device__ __forceinline__ float vlog1p(float a) { return log1pf(a); }
-__device__ __forceinline__ F2 vlog1p(F2 a) { return F2{log1pf(a.x), log1pf(a.y)}; }
+__device__ __forceinline__ F2 vlog1p(F2 a) {
+  float x, y;
+  f2u(a, x, y);
+  return f2(log1pf(x), log1pf(y));
+}
 __device__ __forceinline__ float vexp(float a) { return expf(a); }
-__device__ __forceinline__ F2 vexp(F2 a) { return F2{expf(a.x), expf(a.y)}; }
+__device__ __forceinline__ F2 vexp(F2 a) {
+  float x, y;
+  f2u(a, x, y);
+  return f2(expf(x), expf(y));
+}
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
-__device__ __forceinline__ F2 vmin(F2 a, float b) { return F2{fminf(a.x, b), fminf(a.y, b)}; }
+__device__ __forceinline__ F2 vmin(F2 a, float b) {
+  float x, y;
+  f2u(a, x, y);
+  return f2(fminf(x, b), fminf(y, b));
+}
 __device__ __forceinline__ bool vge(float a, float b) { return a >= b; }
-__device__ __forceinline__ B2 vge(F2 a, float b) { return B2{a.x >= b, a.y >= b}; }
+__device__ __forceinline__ B2 vge(F2 a, float b) {
+  float x, y;
+  f2u(a, x, y);
+  return B2{x >= b, y >= b};
+}
 __device__ __forceinline__ bool vgt(float a, float b) { return a > b; }
-__device__ __forceinline__ B2 vgt(F2 a, float b) { return B2{a.x > b, a.y > b}; }
+__device__ __forceinline__ B2 vgt(F2 a, float b) {
+  float x, y;
+  f2u(a, x, y);
+  return B2{x > b, y > b};
+}
 __device__ __forceinline__ bool vlt(float a, float b) { return a < b; }
-__device__ __forceinline__ B2 vlt(F2 a, float b) { return B2{a.x < b, a.y < b}; }
+__device__ __forceinline__ B2 vlt(F2 a, float b) {
+  float x, y;
+  f2u(a, x, y);
+  return B2{x < b, y < b};
+}
 __device__ __forceinline__ float vsel(bool m, float a, float b) { return m ? a : b; }
-__device__ __forceinline__ F2 vsel(B2 m, F2 a, F2 b) { return F2{m.x ? a.x : b.x, m.y ? a.y : b.y}; }
+__device__ __forceinline__ F2 vsel(B2 m, F2 a, F2 b) {
+  float ax, ay, bx, by;
+  f2u(a, ax, ay);
+  f2u(b, bx, by);
+  return f2(m.x ? ax : bx, m.y ? ay : by);
+}
 __device__ __forceinline__ bool mand(bool a, bool b) { return a && b; }
 __device__ __forceinline__ B2 mand(B2 a, B2 b) { return B2{a.x && b.x, a.y && b.y}; }
 __device__ __forceinline__ bool mandn(bool a, bool b) { return a && !b; }  // a and not b
@@ -187,10 +233,18 @@ __device__ __forceinline__ bool many(B2 a) { return a.x || a.y; }
 __device__ __forceinline__ bool mall(bool a) { return a; }
 __device__ __forceinline__ bool mall(B2 a) { return a.x && a.y; }
 __device__ __forceinline__ float vsum(float a) { return a; }
-__device__ __forceinline__ float vsum(F2 a) { return a.x + a.y; }
+__device__ __forceinline__ float vsum(F2 a) {
+  float x, y;
+  f2u(a, x, y);
+  return x + y;
+}
 // element k (0 or 1) of a value or mask
 __device__ __forceinline__ float vget(float a, int) { return a; }
-__device__ __forceinline__ float vget(F2 a, int k) { return k ? a.y : a.x; }
+__device__ __forceinline__ float vget(F2 a, int k) {
+  float x, y;
+  f2u(a, x, y);
+  return k ? y : x;
+}
 __device__ __forceinline__ bool mget(bool a, int) { return a; }
 __device__ __forceinline__ bool mget(B2 a, int k) { return k ? a.y : a.x; }
 

@@ -144,10 +144,10 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
     for (int kk = 0; kk < L; ++kk)
       sg[kk] = fmaf(gg[kk][0], cfg.bg[0], fmaf(gg[kk][1], cfg.bg[1], gg[kk][2] * cfg.bg[2]));
     if constexpr (L == 2) {
-      T[v] = F2{t[0], t[1]};
-      Sg[v] = F2{sg[0], sg[1]};
+      T[v] = f2(t[0], t[1]);
+      Sg[v] = f2(sg[0], sg[1]);
 #pragma unroll
-      for (int ch = 0; ch < 3; ++ch) g[v][ch] = F2{gg[0][ch], gg[1][ch]};
+      for (int ch = 0; ch < 3; ++ch) g[v][ch] = f2(gg[0][ch], gg[1][ch]);
     } else {
       T[v] = t[0];
       Sg[v] = sg[0];
@@ -226,8 +226,8 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           if constexpr (L == 2) {
-            dx[v] = F2{dxs[(L * v) % PW], dxs[(L * v + 1) % PW]};
-            dy[v] = F2{dys[(L * v) / PW], dys[(L * v + 1) / PW]};
+            dx[v] = f2(dxs[(L * v) % PW], dxs[(L * v + 1) % PW]);
+            dy[v] = f2(dys[(L * v) / PW], dys[(L * v + 1) / PW]);
           } else {
             dx[v] = dxs[v % PW];
             dy[v] = dys[v / PW];
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
           m1 = vsum(dq);
           m3 = vsum(vmul(dq, dx[0]));
           m4 = vsum(vmul(dx[0], cqy));
-          const F2 dyr = F2{dys[0], dys[1]}, rq = F2{vsum(q[0]), vsum(q[1])};  // per-row sums
+          const F2 dyr = f2(dys[0], dys[1]), rq = f2(vsum(q[0]), vsum(q[1]));  // per-row sums
           const F2 dr = vmul(dyr, rq);
           m2 = vsum(dr);
           m5 = vsum(vmul(dr, dyr));

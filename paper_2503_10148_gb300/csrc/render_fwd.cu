@@ -116,8 +116,8 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           if constexpr (L == 2) {
-            dx[v] = F2{pixel_offset(fbx, (L * v) % PW, a.x), pixel_offset(fbx, (L * v + 1) % PW, a.x)};
-            dy[v] = F2{pixel_offset(fby, (L * v) / PW, a.y), pixel_offset(fby, (L * v + 1) / PW, a.y)};
+            dx[v] = f2(pixel_offset(fbx, (L * v) % PW, a.x), pixel_offset(fbx, (L * v + 1) % PW, a.x));
+            dy[v] = f2(pixel_offset(fby, (L * v) / PW, a.y), pixel_offset(fby, (L * v + 1) / PW, a.y));
           } else {
             dx[v] = pixel_offset(fbx, v % PW, a.x);
             dy[v] = pixel_offset(fby, v / PW, a.y);
