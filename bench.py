@@ -429,6 +429,7 @@ def run_ours(args):
         "plain": plain,
     }
     result["relocate"] = relocate_leg(scene_np, device)
+    result["inference"] = inference_leg(scene_np, cams, device, cfg)
     if not args.no_serve:
         result["serve"] = serve_leg(device, cfg, args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -472,6 +473,36 @@ def relocate_leg(scene_np, device, reps: int = 5) -> dict:
     return {"workload": "clusters_1p5m_4views scene, 10 % of opacities transparent, at most 5 % moved per call, "
                         "<= 31 copies per target", "components": n, "moved": int(moved.cpu()[0]),
             "ms": round(ms, 4), "mcomponents_per_s": round(n / ms / 1e3, 1)}
+
+
+def inference_leg(scene_np, cams, device, cfg, reps: int = 50) -> dict:
+    """Inference-only rendering of the benchmark scene (project -> bin ->
+    sort -> render_fwd, no backward): views per second at 1297x840 with one
+    view per frame and with the four views in one frame, eager launches on
+    one stream, timed with CUDA events over `reps` frames after a warm-up
+    (the scene and cameras resident in HBM)."""
+    import torch
+    from paper_2503_10148_gb300 import frame as F
+    sc = F.Scene.from_numpy(scene_np, device)
+    out = {"workload": "clusters_1p5m_4views scene (1.5M components, SH degree 3), forward only, 1297x840"}
+    for name, views in (("one_view", cams[:1]), ("four_views", cams)):
+        fr = F.Frame([sc], views, cfg=cfg, device=device)
+        fr.forward(grow=True)
+        for _ in range(3):
+            fr.forward(grow=False)
+        torch.cuda.synchronize(device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fr.forward(grow=False)
+        e1.record()
+        torch.cuda.synchronize(device)
+        st, _, _ = fr.status()
+        assert st == 0, st
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms_per_frame": round(ms, 4), "views_per_s": round(len(views) * 1e3 / ms, 1)}
+        del fr
+    return out
 
 
 # ------------------------------------------------------------------ serving
