@@ -249,11 +249,14 @@ def test_forward_shell_8views_800_sampled():
 
 
 @pytest.mark.parametrize("case", ["ragged", "no_termination", "lowpass", "background", "large_nu", "clamped_alpha",
-                                  "sh1", "sh2"])
+                                  "sh1", "sh2", "large_nu_packed", "no_termination_packed"])
 def test_forward_edge_cases(case):
     scene = inputs.scene_uniform_cube(1500, seed=11)
     cam = inputs.look_at((0.3, -0.2, 3.0), width=100, height=60)
     kw = {}
+    if case.endswith("_packed"):  # 32x32 tiles: pixels in packed pairs
+        case = case[:-len("_packed")]
+        kw.update(tile_w=32, tile_h=32)
     if case == "no_termination":
         kw["t_min"] = 0.0
     elif case == "lowpass":
@@ -382,13 +385,16 @@ def test_backward_gradcheck_50k_against_oracle_fd_and_analytic():
     assert checked >= 180
 
 
-def test_backward_edge_cases_large_nu_and_clamp():
+@pytest.mark.parametrize("tile", [(16, 16), (32, 32)])
+def test_backward_edge_cases_large_nu_and_clamp(tile):
+    """Large nu (the log1pf/expf path) and clamped alpha, one pixel per lane
+    (16x16 tiles) and packed pixel pairs (32x32)."""
     scene = inputs.scene_uniform_cube(1200, seed=13)
     rng = np.random.default_rng(4)
     scene["nu"] = np.exp(rng.uniform(0, math.log(2e4), 1200)).astype(np.float32)  # some beyond the 1e4 limit
     scene["opacity_raw"][:100] = np.float32(3.5)  # |o| > alpha_max: clamped alpha
     cam = inputs.look_at((0.1, 0.2, 3.0), width=96, height=72)
-    cfg = frame.make_cfg(bg=(0.3, 0.1, 0.6), lowpass=0.3)
+    cfg = frame.make_cfg(bg=(0.3, 0.1, 0.6), lowpass=0.3, tile_w=tile[0], tile_h=tile[1])
     fr, sc, cams = gpu_forward(scene, [cam], cfg)
     cfgd = frame.cfg_dict(cfg)
     s32 = f32_scene(scene)

@@ -55,14 +55,16 @@ def test_sghmc_with_the_adam_gradient_against_oracle(burn_in):
     assert np.allclose(st.r.cpu().numpy().reshape(-1), rr, rtol=1e-5, atol=2e-6)
 
 
-def test_gaussian_kernel_forward_and_backward_against_oracle():
+@pytest.mark.parametrize("tile", [(16, 16), (32, 32)])
+def test_gaussian_kernel_forward_and_backward_against_oracle(tile):
     """kernel = 1 (T2D = exp(-h/2)): the forward within 1e-4 per channel and
-    the gradient within the bar of the t kernel (nu gets none)."""
+    the gradient within the bar of the t kernel (nu gets none); one pixel
+    per lane (16x16 tiles) and packed pixel pairs (32x32)."""
     from gpu_util import (assert_groups_close, gpu_forward, masked_weights, oracle_views, scene_grads_flat,
                           sh_basis_bound)
     require_gpu()
     scene, cams = inputs.tiny_cube_2k()
-    cfg = frame.make_cfg(kernel=1)
+    cfg = frame.make_cfg(kernel=1, tile_w=tile[0], tile_h=tile[1])
     fr, sc, cams = gpu_forward(scene, cams, cfg)
     cfgd = frame.cfg_dict(cfg)
     assert cfgd["kernel"] == 1
