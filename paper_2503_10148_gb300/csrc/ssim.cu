@@ -8,7 +8,8 @@
 // memory (asynchronous copies, zero-filled outside the image); a horizontal 11-tap pass over the 42 rows gives the windowed sums
 // of x, y, x^2, y^2, xy, a vertical pass the five window statistics at each
 // pixel (both passes register-blocked: a thread makes 4 adjacent outputs
-// from 14 loaded values), then SSIM and its partials
+// from 14 loaded values; x and y staged interleaved so that the (x, y) and
+// (x^2, y^2) sums run as packed FP32 pairs), then SSIM and its partials
 //   a = dS/dmx - 2 mx dS/dsx2 - my dS/dsxy,  b = dS/dsx2,  c = dS/dsxy
 // (written to the scratch maps) and the sums of S and |x - y| (one FP64
 // atomic per CTA).  Gradient pass: the same tiling over the maps gives
@@ -68,14 +69,46 @@ __device__ __forceinline__ void stage(float (*s)[HX], const float* plane, int W,
     }
   }
 }
+// Two planes interleaved: s[r][q] = (plane a, plane b) at the same pixel, so
+// that a pixel's pair loads as one 64-bit word (the operand of the packed
+// FP32 instructions).
+__device__ __forceinline__ void stage2(float2 (*s)[HX], const float* pa, const float* pb, int W, int H, int x0,
+                                       int y0) {
+  const int lane = threadIdx.x & 31;
+  for (int r = threadIdx.x >> 5; r < HY; r += NT / 32) {
+    const int gy = y0 - R + r;
+    const bool row_in = gy >= 0 && gy < H;
+    const size_t row = (size_t)(row_in ? gy : 0) * W;
+#pragma unroll
+    for (int q = lane; q < HX; q += 32) {
+      const int gx = x0 - R + q;
+      const bool in = row_in && gx >= 0 && gx < W;
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(&s[r][q].x);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(in ? pa + row + gx : pa),
+                   "r"(in ? 4 : 0)
+                   : "memory");
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa + 4u), "l"(in ? pb + row + gx : pb),
+                   "r"(in ? 4 : 0)
+                   : "memory");
+    }
+  }
+}
+__device__ __forceinline__ F2 ld2(const float2& v) {
+  F2 r;
+  r.v = *reinterpret_cast<const unsigned long long*>(&v);
+  return r;
+}
+__device__ __forceinline__ void st2(float2& d, F2 v) { *reinterpret_cast<unsigned long long*>(&d) = v.v; }
+
 __device__ __forceinline__ void stage_wait() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 __global__ void __launch_bounds__(NT) k_ssim_value(const sss_frame_plan P, const SsimArgs A) {
-  __shared__ float sx[HY][HX], sy[HY][HX];
-  __shared__ float hsum[5][HY][TX];
+  __shared__ float2 s_xy[HY][HX];             // (x, y) per pixel
+  __shared__ float2 h01[HY][TX], h23[HY][TX];  // horizontal sums (x, y), (x^2, y^2)
+  __shared__ float h4[HY][TX];                 // horizontal sum of x y
   __shared__ double red[2][NT / 32];
   const uint32_t t = blockIdx.x;
   const int ch = blockIdx.y;
@@ -91,38 +124,43 @@ __global__ void __launch_bounds__(NT) k_ssim_value(const sss_frame_plan P, const
   // regions (out-of-image pixels stage as 0 and enter as -c, i.e. zero
   // padding is kept; the window weights sum to 1, so the statistics are
   // shift-invariant).  The shift is applied as the staged values are read.
-  stage(sx, A.pred + plane_off, W, H, x0, y0);
-  stage(sy, A.target + plane_off, W, H, x0, y0);
+  stage2(s_xy, A.pred + plane_off, A.target + plane_off, W, H, x0, y0);
   stage_wait();
   __syncthreads();
-  const float cx = sx[R][R], cy = sy[R][R];  // the tile's first pixel (inside the image)
+  const float cx = s_xy[R][R].x, cy = s_xy[R][R].y;  // the tile's first pixel (inside the image)
+  const F2 cxy = f2(cx, cy);
+  // the x and y sums run as packed pairs: (x, y) and (x^2, y^2) per tap,
+  // x y alone; each element is rounded as the scalar fmaf would round it
+  F2 w2[NTAP];
+#pragma unroll
+  for (int k = 0; k < NTAP; ++k) w2[k] = vsplat<F2>(A.w[k]);
   // horizontal: item = (row, group of WB columns); windowed sums of x, y,
   // x^2, y^2, xy for WB adjacent columns from WB + 10 staged values
   for (int it = threadIdx.x; it < HY * (TX / WB); it += NT) {
     const int r = it / (TX / WB), q0 = (it - r * (TX / WB)) * WB;
-    float xv[WB + 2 * R], yv[WB + 2 * R];
+    F2 v[WB + 2 * R], v2[WB + 2 * R];
+    float vxy[WB + 2 * R];
 #pragma unroll
     for (int k = 0; k < WB + 2 * R; ++k) {
-      xv[k] = sx[r][q0 + k] - cx;
-      yv[k] = sy[r][q0 + k] - cy;
+      v[k] = vsub(ld2(s_xy[r][q0 + k]), cxy);  // (x - cx, y - cy)
+      v2[k] = vmul(v[k], v[k]);
+      float a, b;
+      f2u(v[k], a, b);
+      vxy[k] = a * b;
     }
 #pragma unroll
     for (int o = 0; o < WB; ++o) {
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+      F2 s01 = vsplat<F2>(0.f), s23 = vsplat<F2>(0.f);
+      float s4 = 0.f;
 #pragma unroll
       for (int k = 0; k < NTAP; ++k) {
-        const float a = xv[o + k], b = yv[o + k], wk = A.w[k];
-        s0 = fmaf(wk, a, s0);
-        s1 = fmaf(wk, b, s1);
-        s2 = fmaf(wk, a * a, s2);
-        s3 = fmaf(wk, b * b, s3);
-        s4 = fmaf(wk, a * b, s4);
+        s01 = vfma(w2[k], v[o + k], s01);
+        s23 = vfma(w2[k], v2[o + k], s23);
+        s4 = fmaf(A.w[k], vxy[o + k], s4);
       }
-      hsum[0][r][q0 + o] = s0;
-      hsum[1][r][q0 + o] = s1;
-      hsum[2][r][q0 + o] = s2;
-      hsum[3][r][q0 + o] = s3;
-      hsum[4][r][q0 + o] = s4;
+      st2(h01[r][q0 + o], s01);
+      st2(h23[r][q0 + o], s23);
+      h4[r][q0 + o] = s4;
     }
   }
   __syncthreads();
@@ -134,29 +172,34 @@ __global__ void __launch_bounds__(NT) k_ssim_value(const sss_frame_plan P, const
   // vertical: item = (column, group of WB rows)
   for (int it = threadIdx.x; it < TX * (TY / WB); it += NT) {
     const int q = it % TX, r0 = (it / TX) * WB;
-    float m5[WB][5];
+    F2 m01[WB], m23[WB];
+    float m4[WB];
 #pragma unroll
-    for (int o = 0; o < WB; ++o)
-#pragma unroll
-      for (int c = 0; c < 5; ++c) m5[o][c] = 0.f;
+    for (int o = 0; o < WB; ++o) {
+      m01[o] = m23[o] = vsplat<F2>(0.f);
+      m4[o] = 0.f;
+    }
 #pragma unroll
     for (int k = 0; k < WB + 2 * R; ++k) {
-      float hv[5];
-#pragma unroll
-      for (int c = 0; c < 5; ++c) hv[c] = hsum[c][r0 + k][q];
+      const F2 a01 = ld2(h01[r0 + k][q]), a23 = ld2(h23[r0 + k][q]);
+      const float a4 = h4[r0 + k][q];
 #pragma unroll
       for (int o = 0; o < WB; ++o) {
         const int tap = k - o;
         if (tap < 0 || tap >= NTAP) continue;
-#pragma unroll
-        for (int c = 0; c < 5; ++c) m5[o][c] = fmaf(A.w[tap], hv[c], m5[o][c]);
+        m01[o] = vfma(w2[tap], a01, m01[o]);
+        m23[o] = vfma(w2[tap], a23, m23[o]);
+        m4[o] = fmaf(A.w[tap], a4, m4[o]);
       }
     }
 #pragma unroll
     for (int ob = 0; ob < WB; ++ob) {
     const int r = r0 + ob;
     const int gx = x0 + q, gy = y0 + r;
-    const float* m = m5[ob];
+    float m[5];
+    f2u(m01[ob], m[0], m[1]);
+    f2u(m23[ob], m[2], m[3]);
+    m[4] = m4[ob];
     if (gx >= W || gy >= H) continue;
     const float sx2 = m[2] - m[0] * m[0], sy2 = m[3] - m[1] * m[1], sxy = m[4] - m[0] * m[1];
     const float mx = m[0] + cx, my = m[1] + cy;
@@ -174,7 +217,7 @@ __global__ void __launch_bounds__(NT) k_ssim_value(const sss_frame_plan P, const
     A.maps[3 * (size_t)A.n_pixels + o] = dS_dsx2;
     A.maps[6 * (size_t)A.n_pixels + o] = dS_dsxy;
     ssf += S;
-    l1f += fabsf(sx[r + R][q + R] - sy[r + R][q + R]);
+    l1f += fabsf(s_xy[r + R][q + R].x - s_xy[r + R][q + R].y);
     }
   }
   // CTA sums -> one FP64 atomic each
@@ -209,8 +252,10 @@ __global__ void k_ssim_finish(const SsimArgs A) {
 }
 
 __global__ void __launch_bounds__(NT) k_ssim_grad(const sss_frame_plan P, const SsimArgs A) {
-  __shared__ float sm[3][HY][HX];
-  __shared__ float hsum[3][HY][TX];
+  __shared__ float2 s_ab[HY][HX];  // maps a and b per pixel
+  __shared__ float s_c[HY][HX];
+  __shared__ float2 h_ab[HY][TX];
+  __shared__ float h_c[HY][TX];
   const uint32_t t = blockIdx.x;
   const int ch = blockIdx.y;
   const int j = job_of_ssim_tile(P, A, t);
@@ -220,24 +265,34 @@ __global__ void __launch_bounds__(NT) k_ssim_grad(const sss_frame_plan P, const 
   const int lt = (int)(t - A.tile_base[j]);
   const int x0 = (lt % tiles_x) * TX, y0 = (lt / tiles_x) * TY;
   const size_t plane_off = 3 * (size_t)J.pix_base + (size_t)ch * W * H;
-#pragma unroll
-  for (int m = 0; m < 3; ++m) stage(sm[m], A.maps + m * 3 * (size_t)A.n_pixels + plane_off, W, H, x0, y0);
+  stage2(s_ab, A.maps + plane_off, A.maps + 3 * (size_t)A.n_pixels + plane_off, W, H, x0, y0);
+  stage(s_c, A.maps + 6 * (size_t)A.n_pixels + plane_off, W, H, x0, y0);
   stage_wait();
   __syncthreads();
+  // windowed sums of a and b as packed pairs, c alone
+  F2 w2[NTAP];
+#pragma unroll
+  for (int k = 0; k < NTAP; ++k) w2[k] = vsplat<F2>(A.w[k]);
   for (int it = threadIdx.x; it < HY * (TX / WB); it += NT) {
     const int r = it / (TX / WB), q0 = (it - r * (TX / WB)) * WB;
+    F2 vab[WB + 2 * R];
+    float vc[WB + 2 * R];
 #pragma unroll
-    for (int mi = 0; mi < 3; ++mi) {
-      float mv[WB + 2 * R];
+    for (int k = 0; k < WB + 2 * R; ++k) {
+      vab[k] = ld2(s_ab[r][q0 + k]);
+      vc[k] = s_c[r][q0 + k];
+    }
 #pragma unroll
-      for (int k = 0; k < WB + 2 * R; ++k) mv[k] = sm[mi][r][q0 + k];
+    for (int o = 0; o < WB; ++o) {
+      F2 acc = vsplat<F2>(0.f);
+      float accc = 0.f;
 #pragma unroll
-      for (int o = 0; o < WB; ++o) {
-        float acc = 0.f;
-#pragma unroll
-        for (int k = 0; k < NTAP; ++k) acc = fmaf(A.w[k], mv[o + k], acc);
-        hsum[mi][r][q0 + o] = acc;
+      for (int k = 0; k < NTAP; ++k) {
+        acc = vfma(w2[k], vab[o + k], acc);
+        accc = fmaf(A.w[k], vc[o + k], accc);
       }
+      st2(h_ab[r][q0 + o], acc);
+      h_c[r][q0 + o] = accc;
     }
   }
   __syncthreads();
@@ -256,20 +311,30 @@ __global__ void __launch_bounds__(NT) k_ssim_grad(const sss_frame_plan P, const 
       xs[ob] = A.pred[o];
       ys[ob] = A.target[o];
     }
-    float cv[WB][3];
+    F2 cab[WB];
+    float cc[WB];
 #pragma unroll
-    for (int o = 0; o < WB; ++o) cv[o][0] = cv[o][1] = cv[o][2] = 0.f;
+    for (int o = 0; o < WB; ++o) {
+      cab[o] = vsplat<F2>(0.f);
+      cc[o] = 0.f;
+    }
 #pragma unroll
     for (int k = 0; k < WB + 2 * R; ++k) {
-      const float h0 = hsum[0][r0 + k][q], h1 = hsum[1][r0 + k][q], h2 = hsum[2][r0 + k][q];
+      const F2 hab = ld2(h_ab[r0 + k][q]);
+      const float hc = h_c[r0 + k][q];
 #pragma unroll
       for (int o = 0; o < WB; ++o) {
         const int tap = k - o;
         if (tap < 0 || tap >= NTAP) continue;
-        cv[o][0] = fmaf(A.w[tap], h0, cv[o][0]);
-        cv[o][1] = fmaf(A.w[tap], h1, cv[o][1]);
-        cv[o][2] = fmaf(A.w[tap], h2, cv[o][2]);
+        cab[o] = vfma(w2[tap], hab, cab[o]);
+        cc[o] = fmaf(A.w[tap], hc, cc[o]);
       }
+    }
+    float cv[WB][3];
+#pragma unroll
+    for (int o = 0; o < WB; ++o) {
+      f2u(cab[o], cv[o][0], cv[o][1]);
+      cv[o][2] = cc[o];
     }
 #pragma unroll
     for (int ob = 0; ob < WB; ++ob) {
