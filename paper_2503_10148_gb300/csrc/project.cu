@@ -141,7 +141,7 @@ __device__ __forceinline__ void project_component(const sss_frame_plan& P, int s
   }
 }
 
-__global__ void __launch_bounds__(256) k_project(const sss_frame_plan P, void* ws) {
+__global__ void __launch_bounds__(128, 5) k_project(const sss_frame_plan P, void* ws) {
   const uint32_t gidx = blockIdx.x * blockDim.x + threadIdx.x;
   if (gidx >= P.scene_comp_base[P.n_scenes]) return;
   const int s = scene_of_comp(P, gidx);
@@ -160,7 +160,7 @@ extern "C" int sss_project(const sss_frame_plan* plan, void* ws, sss_stream_t st
   if (!plan || !ws) return SSS_ERR_INVALID_ARG;
   const uint32_t total = plan->scene_comp_base[plan->n_scenes];
   if (total == 0) return SSS_OK;
-  sss::k_project<<<sss::ceil_div(total, 256), 256, 0, (cudaStream_t)stream>>>(*plan, ws);
+  sss::k_project<<<sss::ceil_div(total, 128), 128, 0, (cudaStream_t)stream>>>(*plan, ws);
   SSS_LAUNCH_CHECK();
   return SSS_OK;
 }

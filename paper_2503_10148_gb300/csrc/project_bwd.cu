@@ -195,7 +195,7 @@ struct GradSet {
   sss_params g[SSS_MAX_SCENES];
 };
 
-__global__ void __launch_bounds__(256, 2) k_project_bwd(const sss_frame_plan P, const void* ws, const GradSet G) {
+__global__ void __launch_bounds__(128, 5) k_project_bwd(const sss_frame_plan P, const void* ws, const GradSet G) {
   const uint32_t gidx = blockIdx.x * blockDim.x + threadIdx.x;
   if (gidx >= P.scene_comp_base[P.n_scenes]) return;
   const int s = scene_of_comp(P, gidx);
@@ -224,7 +224,7 @@ extern "C" int sss_project_bwd(const sss_frame_plan* plan, void* ws, const sss_p
   }
   const uint32_t total = P.scene_comp_base[P.n_scenes];
   if (total == 0) return SSS_OK;
-  sss::k_project_bwd<<<sss::ceil_div(total, 256), 256, 0, (cudaStream_t)stream>>>(P, ws, G);
+  sss::k_project_bwd<<<sss::ceil_div(total, 128), 128, 0, (cudaStream_t)stream>>>(P, ws, G);
   SSS_LAUNCH_CHECK();
   return SSS_OK;
 }
