@@ -106,7 +106,7 @@ typedef struct sss_camera {
 
 /* ------------------------------------------------------ raster options */
 typedef struct sss_raster_cfg {
-  int32_t tile_w, tile_h; /* 16x16, 32x16, 16x32 or 32x32 pixels             */
+  int32_t tile_w, tile_h; /* 16x16, 32x16, 16x32, 32x32, 64x32 or 32x64 pixels */
   int32_t batch;          /* records each warp stages in shared memory per
                              round (double buffered, cp.async); 32, the only
                              value built, one record per lane              */

@@ -19,7 +19,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "tuned.json")
 
-TILES = ((16, 16), (32, 16), (16, 32), (32, 32))
+TILES = ((16, 16), (32, 16), (16, 32), (32, 32), (64, 32), (32, 64))
 
 
 def cached(name: str) -> dict | None:

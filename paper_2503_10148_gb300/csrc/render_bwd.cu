@@ -87,7 +87,7 @@ __device__ __forceinline__ F2 log1p_minus_u(F2 u, F2 log_base) {
 }
 
 template <int PW, int PH, bool PAPER_NU>
-__global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const sss_frame_plan P, void* ws,
+__global__ void __launch_bounds__(64, PW * PH >= 8 ? 8 : (PW * PH >= 4 ? 12 : 16)) k_render_bwd(const sss_frame_plan P, void* ws,
                                                                            const float* __restrict__ dl_drgb) {
   constexpr int NPIX = PW * PH;
   constexpr int TW = 16 * PW, TH = 16 * PH;
@@ -388,5 +388,7 @@ extern "C" int sss_render_bwd(const sss_frame_plan* plan, void* ws, const float*
   if (pw == 2 && ph == 1) return sss::launch_tile<2, 1>(P, ws, dL_drgb, st);
   if (pw == 1 && ph == 2) return sss::launch_tile<1, 2>(P, ws, dL_drgb, st);
   if (pw == 2 && ph == 2) return sss::launch_tile<2, 2>(P, ws, dL_drgb, st);
+  if (pw == 4 && ph == 2) return sss::launch_tile<4, 2>(P, ws, dL_drgb, st);
+  if (pw == 2 && ph == 4) return sss::launch_tile<2, 4>(P, ws, dL_drgb, st);
   return SSS_ERR_UNSUPPORTED;
 }

@@ -21,7 +21,7 @@ namespace sss {
 namespace {
 
 template <int PW, int PH, bool COUNT>
-__global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, void* ws, float* __restrict__ out_rgb) {
+__global__ void __launch_bounds__(64, PW * PH >= 8 ? 10 : 16) k_render_fwd(const sss_frame_plan P, void* ws, float* __restrict__ out_rgb) {
   constexpr int NPIX = PW * PH;
   constexpr int TW = 16 * PW, TH = 16 * PH;
   constexpr int L = LaneVec<NPIX>::L, NV = LaneVec<NPIX>::NV;
@@ -229,5 +229,7 @@ extern "C" int sss_render_fwd(const sss_frame_plan* plan, void* ws, float* out_r
   if (pw == 2 && ph == 1) return sss::launch_batch<2, 1>(P, ws, out_rgb, st);
   if (pw == 1 && ph == 2) return sss::launch_batch<1, 2>(P, ws, out_rgb, st);
   if (pw == 2 && ph == 2) return sss::launch_batch<2, 2>(P, ws, out_rgb, st);
+  if (pw == 4 && ph == 2) return sss::launch_batch<4, 2>(P, ws, out_rgb, st);
+  if (pw == 2 && ph == 4) return sss::launch_batch<2, 4>(P, ws, out_rgb, st);
   return SSS_ERR_UNSUPPORTED;
 }
