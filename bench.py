@@ -181,7 +181,9 @@ def _cfg(args):
 
 
 def stage_breakdown(ts, reps, device):
-    """Eager steps with CUDA events between the stages (same stream)."""
+    """Eager steps with CUDA events between the stages (same stream); like
+    the timed steps, each starts from the configured scene (the copy is
+    outside the events)."""
     import torch
     from paper_2503_10148_gb300 import frame as F
     fr = ts.frame
@@ -189,6 +191,10 @@ def stage_breakdown(ts, reps, device):
     names = ["project", "bin", "sort", "render_fwd", "loss", "render_bwd", "project_bwd", "sghmc_step"]
     acc = {n: 0.0 for n in names}
     for _ in range(reps):
+        if ts.initial is not None:
+            with torch.no_grad():
+                for f in F.FIELDS:
+                    ts.scene.t[f].copy_(ts.initial[f])
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
         ev[0].record(st)
         fr.project(st); ev[1].record(st)
