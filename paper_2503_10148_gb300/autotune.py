@@ -2,9 +2,10 @@
 
 For a workload it times the whole captured train step (``train.TrainStep``)
 for every (tile_w, tile_h) candidate and keeps the fastest.  Tile size
-trades pair count (bigger tiles: fewer pairs to sort, fewer splat records
-gathered) against per-warp culling efficiency (each warp of a tile covers
-an eighth of it and skips the records whose ellipse misses its block).
+trades pair count (bigger tiles: fewer pairs to sort) against the render's
+work per tile: a tile is rendered as sub-tiles of at most 32 x 32 pixels,
+each walking the tile's whole list (its warps skip the records whose
+ellipse misses their block).
 The render kernels stage 32 records per warp and round, one per lane, so
 the staging batch is fixed and not a candidate.
 
@@ -19,7 +20,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "tuned.json")
 
-TILES = ((16, 16), (32, 16), (16, 32), (32, 32), (64, 32), (32, 64))
+TILES = ((16, 16), (32, 16), (16, 32), (32, 32), (64, 32), (32, 64), (64, 64), (128, 64), (64, 128), (128, 128))
 
 
 def cached(name: str) -> dict | None:

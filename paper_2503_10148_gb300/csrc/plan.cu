@@ -9,11 +9,8 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-bool tile_ok(int w, int h) {
-  const bool a = (w == 16 || w == 32) && (h == 16 || h == 32);
-  const bool b = (w == 64 && h == 32) || (w == 32 && h == 64);
-  return a || b;
-}
+bool side_ok(int s) { return s == 16 || s == 32 || s == 64 || s == 128; }
+bool tile_ok(int w, int h) { return side_ok(w) && side_ok(h); }
 bool batch_ok(int b) { return b == 32; }
 
 }  // namespace

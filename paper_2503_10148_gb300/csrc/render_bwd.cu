@@ -87,7 +87,7 @@ __device__ __forceinline__ F2 log1p_minus_u(F2 u, F2 log_base) {
 }
 
 template <int PW, int PH, bool PAPER_NU>
-__global__ void __launch_bounds__(64, PW * PH >= 8 ? 8 : (PW * PH >= 4 ? 12 : 16)) k_render_bwd(const sss_frame_plan P, void* ws,
+__global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const sss_frame_plan P, void* ws,
                                                                            const float* __restrict__ dl_drgb) {
   constexpr int NPIX = PW * PH;
   constexpr int TW = 16 * PW, TH = 16 * PH;
@@ -96,17 +96,20 @@ __global__ void __launch_bounds__(64, PW * PH >= 8 ? 8 : (PW * PH >= 4 ? 12 : 16
   using M = MaskT<V>;
   __shared__ WarpBuf s_wb[2];
 
-  // four CTAs of two warps per tile; warp w of the tile's 2 x 4 layout
-  const uint32_t tile = blockIdx.x >> 2;
+  // sub-tiles of the list tile as in the forward; warp w of a sub-tile's
+  // 2 x 4 layout
+  const sss_raster_cfg& cfg = P.cfg;
+  const uint32_t SX = (uint32_t)cfg.tile_w / TW, SY = (uint32_t)cfg.tile_h / TH;
+  const uint32_t cta = blockIdx.x >> 2, tile = cta / (SX * SY), sub = cta - tile * (SX * SY);
   WarpBuf& S = s_wb[threadIdx.x >> 5];
   const int j = job_of_tile(P, tile);
   const sss_job_desc& J = P.jobs[j];
-  const sss_raster_cfg& cfg = P.cfg;
   const uint32_t lt = tile - J.tile_base;
   const int tx = (int)(lt % (uint32_t)J.tiles_x), ty = (int)(lt / (uint32_t)J.tiles_x);
   const int warp = (int)((blockIdx.x & 3u) << 1) | (int)(threadIdx.x >> 5);
   const unsigned lane = threadIdx.x & 31;
-  const int bx = tx * TW + (warp & 1) * 8 * PW, by = ty * TH + (warp >> 1) * 4 * PH;
+  const int bx = tx * cfg.tile_w + (int)(sub % SX) * TW + (warp & 1) * 8 * PW;
+  const int by = ty * cfg.tile_h + (int)(sub / SX) * TH + (warp >> 1) * 4 * PH;
   const int lx = bx + (lane & 7) * PW, ly = by + (lane >> 3) * PH;
   const int W = J.cam.width, H = J.cam.height;
   const size_t hw = (size_t)W * H;
@@ -364,7 +367,8 @@ __global__ void __launch_bounds__(64, PW * PH >= 8 ? 8 : (PW * PH >= 4 ? 12 : 16
 template <int PW, int PH, bool PAPER_NU>
 int launch_batch(const sss_frame_plan& P, void* ws, const float* g, cudaStream_t st) {
   // 32 records per warp and batch whatever cfg.batch says (checked by the plan)
-  k_render_bwd<PW, PH, PAPER_NU><<<4 * P.n_tiles, 64, 0, st>>>(P, ws, g);
+  const unsigned subs = (unsigned)(P.cfg.tile_w / (16 * PW)) * (unsigned)(P.cfg.tile_h / (16 * PH));
+  k_render_bwd<PW, PH, PAPER_NU><<<4 * subs * P.n_tiles, 64, 0, st>>>(P, ws, g);
   SSS_LAUNCH_CHECK();
   return SSS_OK;
 }
@@ -383,12 +387,10 @@ extern "C" int sss_render_bwd(const sss_frame_plan* plan, void* ws, const float*
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemsetAsync(sss::ws_ptr<float>(ws, P.ws_off_grad2d), 0, 48 * (size_t)P.n_entries, st) != cudaSuccess)
     return SSS_ERR_CUDA;
-  const int pw = P.cfg.tile_w / 16, ph = P.cfg.tile_h / 16;
+  const int pw = (P.cfg.tile_w >= 32 ? 32 : P.cfg.tile_w) / 16, ph = (P.cfg.tile_h >= 32 ? 32 : P.cfg.tile_h) / 16;
   if (pw == 1 && ph == 1) return sss::launch_tile<1, 1>(P, ws, dL_drgb, st);
   if (pw == 2 && ph == 1) return sss::launch_tile<2, 1>(P, ws, dL_drgb, st);
   if (pw == 1 && ph == 2) return sss::launch_tile<1, 2>(P, ws, dL_drgb, st);
   if (pw == 2 && ph == 2) return sss::launch_tile<2, 2>(P, ws, dL_drgb, st);
-  if (pw == 4 && ph == 2) return sss::launch_tile<4, 2>(P, ws, dL_drgb, st);
-  if (pw == 2 && ph == 4) return sss::launch_tile<2, 4>(P, ws, dL_drgb, st);
   return SSS_ERR_UNSUPPORTED;
 }

@@ -1,9 +1,10 @@
 // a4: per-pixel front-to-back compositing with signed alpha
 // (Sec. 3.4 Eq. SSS_color; signed opacity Sec. 3.3).
 //
-// An image tile of (16 PW) x (16 PH) pixels is covered by eight warps laid
-// out 2 x 4, run as four CTAs of two warps; warp w owns an (8 PW) x (4 PH)
-// box and lane l a PW x PH block of pixels inside it.  Warps are
+// A render sub-tile of (16 PW) x (16 PH) pixels (at most 32 x 32; a list
+// tile of the binning may hold several) is covered by eight warps laid out
+// 2 x 4, run as four CTAs of two warps; warp w owns an (8 PW) x (4 PH) box
+// and lane l a PW x PH block of pixels inside it.  Warps are
 // independent (no CTA barrier): each walks the tile's list in rounds of 32
 // records, one 48-byte record per lane gathered by entry index with
 // cp.async into the warp's own double buffer (the next round is in flight
@@ -21,7 +22,7 @@ namespace sss {
 namespace {
 
 template <int PW, int PH, bool COUNT>
-__global__ void __launch_bounds__(64, PW * PH >= 8 ? 10 : 16) k_render_fwd(const sss_frame_plan P, void* ws, float* __restrict__ out_rgb) {
+__global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, void* ws, float* __restrict__ out_rgb) {
   constexpr int NPIX = PW * PH;
   constexpr int TW = 16 * PW, TH = 16 * PH;
   constexpr int L = LaneVec<NPIX>::L, NV = LaneVec<NPIX>::NV;
@@ -29,16 +30,21 @@ __global__ void __launch_bounds__(64, PW * PH >= 8 ? 10 : 16) k_render_fwd(const
   using M = MaskT<V>;
   __shared__ WarpBuf s_wb[2];
 
-  // four CTAs of two warps per tile; warp w of the tile's 2 x 4 layout
-  const uint32_t tile = blockIdx.x >> 2;
+  // a list tile of cfg.tile_w x cfg.tile_h pixels is rendered as SX x SY
+  // sub-tiles of TW x TH, each by four CTAs of two warps; warp w of the
+  // sub-tile's 2 x 4 layout.  Every sub-tile walks the whole list of its
+  // tile (the per-warp cull drops what misses its box).
+  const sss_raster_cfg& cfg = P.cfg;
+  const uint32_t SX = (uint32_t)cfg.tile_w / TW, SY = (uint32_t)cfg.tile_h / TH;
+  const uint32_t cta = blockIdx.x >> 2, tile = cta / (SX * SY), sub = cta - tile * (SX * SY);
   const int warp = (int)((blockIdx.x & 3u) << 1) | (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
   WarpBuf& S = s_wb[threadIdx.x >> 5];
   const int j = job_of_tile(P, tile);
   const sss_job_desc& J = P.jobs[j];
-  const sss_raster_cfg& cfg = P.cfg;
   const uint32_t lt = tile - J.tile_base;
   const int tx = (int)(lt % (uint32_t)J.tiles_x), ty = (int)(lt / (uint32_t)J.tiles_x);
-  const int bx = tx * TW + (warp & 1) * 8 * PW, by = ty * TH + (warp >> 1) * 4 * PH;
+  const int bx = tx * cfg.tile_w + (int)(sub % SX) * TW + (warp & 1) * 8 * PW;
+  const int by = ty * cfg.tile_h + (int)(sub / SX) * TH + (warp >> 1) * 4 * PH;
   const int lx = bx + (lane & 7) * PW, ly = by + (lane >> 3) * PH;
   const int W = J.cam.width, H = J.cam.height;
 
@@ -209,10 +215,11 @@ __global__ void __launch_bounds__(64, PW * PH >= 8 ? 10 : 16) k_render_fwd(const
 template <int PW, int PH>
 int launch_batch(const sss_frame_plan& P, void* ws, float* out, cudaStream_t st) {
   // the staging batch is 32 records per warp (the only value the plan accepts)
+  const unsigned subs = (unsigned)(P.cfg.tile_w / (16 * PW)) * (unsigned)(P.cfg.tile_h / (16 * PH));
   if (P.cfg.count_pairs)
-    k_render_fwd<PW, PH, true><<<4 * P.n_tiles, 64, 0, st>>>(P, ws, out);
+    k_render_fwd<PW, PH, true><<<4 * subs * P.n_tiles, 64, 0, st>>>(P, ws, out);
   else
-    k_render_fwd<PW, PH, false><<<4 * P.n_tiles, 64, 0, st>>>(P, ws, out);
+    k_render_fwd<PW, PH, false><<<4 * subs * P.n_tiles, 64, 0, st>>>(P, ws, out);
   SSS_LAUNCH_CHECK();
   return SSS_OK;
 }
@@ -224,12 +231,11 @@ extern "C" int sss_render_fwd(const sss_frame_plan* plan, void* ws, float* out_r
   if (!plan || !ws || !out_rgb) return SSS_ERR_INVALID_ARG;
   const sss_frame_plan& P = *plan;
   cudaStream_t st = (cudaStream_t)stream;
-  const int pw = P.cfg.tile_w / 16, ph = P.cfg.tile_h / 16;
+  // render sub-tiles of at most 32 x 32 (lanes of up to 2 x 2 pixels)
+  const int pw = (P.cfg.tile_w >= 32 ? 32 : P.cfg.tile_w) / 16, ph = (P.cfg.tile_h >= 32 ? 32 : P.cfg.tile_h) / 16;
   if (pw == 1 && ph == 1) return sss::launch_batch<1, 1>(P, ws, out_rgb, st);
   if (pw == 2 && ph == 1) return sss::launch_batch<2, 1>(P, ws, out_rgb, st);
   if (pw == 1 && ph == 2) return sss::launch_batch<1, 2>(P, ws, out_rgb, st);
   if (pw == 2 && ph == 2) return sss::launch_batch<2, 2>(P, ws, out_rgb, st);
-  if (pw == 4 && ph == 2) return sss::launch_batch<4, 2>(P, ws, out_rgb, st);
-  if (pw == 2 && ph == 4) return sss::launch_batch<2, 4>(P, ws, out_rgb, st);
   return SSS_ERR_UNSUPPORTED;
 }

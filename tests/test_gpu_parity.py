@@ -140,7 +140,7 @@ def test_bin_sort_bit_exact_tiny():
     _check_bin_sort(fr)
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (32, 16), (16, 32), (32, 32), (64, 32)])
+@pytest.mark.parametrize("tile", [(16, 16), (32, 16), (16, 32), (32, 32), (64, 32), (64, 64)])
 def test_bin_sort_bit_exact_multiview(tile):
     scene, cams = inputs.shell_100k_8views()
     scene = inputs.subset_scene(scene, np.arange(0, 100_000, 3))
@@ -189,7 +189,8 @@ def _check_forward(fr, scene, cams, cfgd, pix=None):
     return worst, flagged
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (32, 16), (16, 32), (32, 32), (64, 32), (32, 64)])
+@pytest.mark.parametrize("tile", [(16, 16), (32, 16), (16, 32), (32, 32), (64, 32), (32, 64), (64, 64), (64, 16),
+                                  (128, 64), (128, 128)])
 def test_forward_tiny_all_tile_configs(tile):
     scene, cams = inputs.tiny_cube_2k()
     cfg = frame.make_cfg(tile_w=tile[0], tile_h=tile[1])
@@ -318,7 +319,7 @@ def _grad2d_report(fr, g2d_ref, g2d_abs, cams, scene):
 
 
 @pytest.mark.parametrize("nu_mode,tile", [(0, (16, 16)), (1, (16, 16)), (0, (32, 16)), (0, (16, 32)), (1, (32, 32)),
-                                          (0, (64, 32)), (1, (32, 64))])
+                                          (0, (64, 32)), (1, (32, 64)), (0, (64, 64)), (1, (128, 128))])
 def test_backward_tiny_against_oracle_analytic(nu_mode, tile):
     scene, cams = inputs.tiny_cube_2k()
     cfg = frame.make_cfg(nu_grad_mode=nu_mode, tile_w=tile[0], tile_h=tile[1])
