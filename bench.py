@@ -63,6 +63,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-serve", action="store_true", help="skip the render-server leg")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="Poisson arrival window of the server leg")
+    ap.add_argument("--serve-tile", default="32x32",
+                    help="WxH list tile of the server leg (single views of mixed sizes: latency, not throughput)")
     ap.add_argument("--workload", default="clusters_1p5m_4views", choices=sorted(WORKLOADS),
                     help="smaller seeded workloads exist for profiling; the benchmark line uses the default")
     return ap.parse_args()
@@ -460,7 +462,8 @@ def run_ours(args):
     result["relocate"] = relocate_leg(scene_np, device)
     result["inference"] = inference_leg(scene_np, cams, device, cfg)
     if not args.no_serve:
-        result["serve"] = serve_leg(device, cfg, args.serve_seconds)
+        stw, sth = (int(v) for v in args.serve_tile.split("x"))
+        result["serve"] = serve_leg(device, F.make_cfg(tile_w=stw, tile_h=sth), args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -551,7 +554,8 @@ def serve_leg(device, cfg, seconds: float) -> dict:
     scenes = [F.Scene.from_numpy(s, device) for s in inputs.serving_scenes()]
     reqs = server.poisson_requests(len(scenes), rate=200.0, duration=seconds, seed=21)
     budget = 16 << 30
-    out = {"workload": SERVE_WORKLOAD, "hbm_budget_gb": budget >> 30, "arrival_window_s": seconds}
+    out = {"workload": SERVE_WORKLOAD, "hbm_budget_gb": budget >> 30, "arrival_window_s": seconds,
+           "tile": f"{cfg.tile_w}x{cfg.tile_h}"}
     for name, burst in (("poisson", False), ("burst", True)):
         rs = [dataclasses.replace(r, arrival=0.0) for r in reqs] if burst else reqs
         srv = server.RenderServer(scenes, cfg, hbm_budget_bytes=budget, device=device)
