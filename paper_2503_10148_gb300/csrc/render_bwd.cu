@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
 
 template <int PW, int PH, bool PAPER_NU>
 int launch_batch(const sss_frame_plan& P, void* ws, const float* g, cudaStream_t st) {
-  // 32 records per warp and batch whatever cfg.batch says (checked by the plan)
+  // 32 records per warp and round (the only staging depth the plan accepts)
   const unsigned subs = (unsigned)(P.cfg.tile_w / (16 * PW)) * (unsigned)(P.cfg.tile_h / (16 * PH));
   k_render_bwd<PW, PH, PAPER_NU><<<4 * subs * P.n_tiles, 64, 0, st>>>(P, ws, g);
   SSS_LAUNCH_CHECK();
