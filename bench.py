@@ -58,6 +58,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--tile", default=None, help="WxH tile, e.g. 16x16 (default: autotuned cache or 16x16)")
+    ap.add_argument("--batch", type=int, default=None, help="records per warp and staging round with --tile: 32 or 64")
     ap.add_argument("--no-plain", action="store_true", help="skip the one-frame-per-view comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -175,10 +176,10 @@ def _cfg(args):
     from paper_2503_10148_gb300 import autotune, frame
     if getattr(args, "tile", None):
         tw, th = (int(v) for v in args.tile.split("x"))
-        return frame.make_cfg(tile_w=tw, tile_h=th), "cli"
+        return frame.make_cfg(tile_w=tw, tile_h=th, batch=getattr(args, "batch", None) or 32), "cli"
     best = autotune.cached(getattr(args, "workload", "clusters_1p5m_4views"))
     if best:
-        return frame.make_cfg(tile_w=best["tile_w"], tile_h=best["tile_h"]), "autotuned"
+        return frame.make_cfg(tile_w=best["tile_w"], tile_h=best["tile_h"], batch=best.get("batch", 32)), "autotuned"
     return frame.make_cfg(), "default"
 
 

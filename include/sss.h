@@ -111,8 +111,8 @@ typedef struct sss_raster_cfg {
                              32 x 32 (eight warps, lanes of up to 2 x 2
                              pixels), each walking its tile's whole list   */
   int32_t batch;          /* records each warp stages in shared memory per
-                             round (double buffered, cp.async); 32, the only
-                             value built, one record per lane              */
+                             round (double buffered, cp.async): 32 or 64,
+                             one or two per lane                          */
   int32_t nu_grad_mode;   /* 0: exact dT/dnu (default); 1: the SM's printed
                              form, which omits -1/2 ln(1 + h/nu) T2D          */
   float tau;              /* alpha threshold, 1/255: a splat contributes to a

@@ -1,13 +1,15 @@
-"""Autotuner for the rasterizer's launch shape: the tile size.
+"""Autotuner for the rasterizer's launch shape: the tile size and the
+staging batch.
 
 For a workload it times the whole captured train step (``train.TrainStep``)
-for every (tile_w, tile_h) candidate and keeps the fastest.  Tile size
+for every (tile_w, tile_h, batch) candidate and keeps the fastest.  Tile size
 trades pair count (bigger tiles: fewer pairs to sort) against the render's
 work per tile: a tile is rendered as sub-tiles of at most 32 x 32 pixels,
 each walking the tile's whole list (its warps skip the records whose
 ellipse misses their block).
-The render kernels stage 32 records per warp and round, one per lane, so
-the staging batch is fixed and not a candidate.
+The staging batch is the number of records a warp gathers per round, 32 or
+64 (one or two per lane): deeper rounds mean fewer rounds, each with more
+gathers in flight, at twice the shared memory.
 
 Results are stored per workload name in ``tuned.json`` next to this file;
 ``cached(name)`` returns the stored choice or None.
@@ -21,6 +23,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "tuned.json")
 
 TILES = ((16, 16), (32, 16), (16, 32), (32, 32), (64, 32), (32, 64), (64, 64), (128, 64), (64, 128), (128, 128))
+BATCHES = (32, 64)
 
 
 def cached(name: str) -> dict | None:
@@ -53,14 +56,14 @@ def tune(name: str, scene, cams, targets, candidates=None, steps: int = 5, devic
     from . import frame as F
     from . import train
 
-    candidates = candidates or list(TILES)
+    candidates = candidates or [(tw, th, b) for (tw, th) in TILES for b in BATCHES]
     snapshot = {f: scene.t[f].clone() for f in F.FIELDS}
     results = []
-    for tw, th in candidates:
+    for tw, th, b in candidates:
         with torch.no_grad():  # every candidate starts from the same parameters
             for f in F.FIELDS:
                 scene.t[f].copy_(snapshot[f])
-        cfg = F.make_cfg(tile_w=tw, tile_h=th)
+        cfg = F.make_cfg(tile_w=tw, tile_h=th, batch=b)
         ts = train.TrainStep(scene, cams, targets, cfg=cfg, device=device, **(step_kw or {}))
         ts.calibrate()
         ts.capture()
@@ -74,15 +77,15 @@ def tune(name: str, scene, cams, targets, candidates=None, steps: int = 5, devic
         torch.cuda.synchronize(device)
         ms = e0.elapsed_time(e1) / steps
         ts.check()
-        results.append((ms, tw, th))
-        log(f"autotune {name}: tile {tw}x{th}: {ms:.3f} ms/step")
+        results.append((ms, tw, th, b))
+        log(f"autotune {name}: tile {tw}x{th} batch {b}: {ms:.3f} ms/step")
         del ts
         torch.cuda.empty_cache()
     with torch.no_grad():
         for f in F.FIELDS:
             scene.t[f].copy_(snapshot[f])
-    ms, tw, th = min(results)
-    choice = {"tile_w": tw, "tile_h": th, "ms_per_step": round(ms, 3),
-              "candidates": {f"{a}x{c}": round(m, 3) for m, a, c in results}}
+    ms, tw, th, b = min(results)
+    choice = {"tile_w": tw, "tile_h": th, "batch": b, "ms_per_step": round(ms, 3),
+              "candidates": {f"{a}x{c}/{d}": round(m, 3) for m, a, c, d in results}}
     store(name, choice, path)
     return choice

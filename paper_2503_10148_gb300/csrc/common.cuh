@@ -410,29 +410,37 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Per-warp staging of splat records, 32 per batch (slot = lane), double
-// buffered: a warp gathers batch i+1 with cp.async while it evaluates batch
-// i, and no other warp touches its buffers (no CTA barrier).
+// Per-warp staging of splat records, 32 R per batch (slot r*32 + lane is
+// staged by lane `lane`), double buffered: a warp gathers batch i+1 with
+// cp.async while it evaluates batch i, and no other warp touches its buffers
+// (no CTA barrier).  R (1 or 2) is the staging depth the autotuner picks.
+template <int R>
 struct WarpBuf {
-  float4 a[2][32], b[2][32], c[2][32];
-  uint32_t e[2][32];
+  float4 a[2][32 * R], b[2][32 * R], c[2][32 * R];
+  uint32_t e[2][32 * R];
 };
 
-// Lane `lane` fills slot `lane` of buffer k with record e, or with an empty
-// slot (h_max < 0, never hit) when !valid; one commit group per call.
-__device__ __forceinline__ void warp_stage(WarpBuf& S, int k, const SplatRec* __restrict__ rec, uint32_t e,
-                                           bool valid, int lane) {
-  if (valid) {
-    const float4* src = reinterpret_cast<const float4*>(rec + e);
-    cp_async16(&S.a[k][lane], src);
-    cp_async16(&S.b[k][lane], src + 1);
-    cp_async16(&S.c[k][lane], src + 2);
-  } else {
-    S.a[k][lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    S.b[k][lane] = make_float4(1.0f, 0.0f, -1.0f, 1.0f);
-    S.c[k][lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+// Lane `lane` fills slots r*32 + lane (r < R) of buffer k with records e[r],
+// or with an empty slot (h_max < 0, never hit) where !valid[r]; one commit
+// group per call.
+template <int R>
+__device__ __forceinline__ void warp_stage(WarpBuf<R>& S, int k, const SplatRec* __restrict__ rec,
+                                           const uint32_t (&e)[R], const bool (&valid)[R], int lane) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int slot = r * 32 + lane;
+    if (valid[r]) {
+      const float4* src = reinterpret_cast<const float4*>(rec + e[r]);
+      cp_async16(&S.a[k][slot], src);
+      cp_async16(&S.b[k][slot], src + 1);
+      cp_async16(&S.c[k][slot], src + 2);
+    } else {
+      S.a[k][slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      S.b[k][slot] = make_float4(1.0f, 0.0f, -1.0f, 1.0f);
+      S.c[k][slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    S.e[k][slot] = valid[r] ? e[r] : 0u;
   }
-  S.e[k][lane] = valid ? e : 0u;
   cp_async_commit();
 }
 

@@ -11,7 +11,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 bool side_ok(int s) { return s == 16 || s == 32 || s == 64 || s == 128; }
 bool tile_ok(int w, int h) { return side_ok(w) && side_ok(h); }
-bool batch_ok(int b) { return b == 32; }
+bool batch_ok(int b) { return b == 32 || b == 64; }
 
 }  // namespace
 

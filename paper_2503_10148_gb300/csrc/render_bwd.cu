@@ -86,22 +86,23 @@ __device__ __forceinline__ F2 log1p_minus_u(F2 u, F2 log_base) {
   return vsel(vlt(u, 0.25f), series, vsub(log_base, u));
 }
 
-template <int PW, int PH, bool PAPER_NU>
+template <int PW, int PH, int R, bool PAPER_NU>
 __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const sss_frame_plan P, void* ws,
                                                                            const float* __restrict__ dl_drgb) {
   constexpr int NPIX = PW * PH;
+  constexpr uint32_t B = 32 * R;  // records per warp and round
   constexpr int TW = 16 * PW, TH = 16 * PH;
   constexpr int L = LaneVec<NPIX>::L, NV = LaneVec<NPIX>::NV;
   using V = typename std::conditional<L == 2, F2, float>::type;
   using M = MaskT<V>;
-  __shared__ WarpBuf s_wb[2];
+  __shared__ WarpBuf<R> s_wb[2];
 
   // sub-tiles of the list tile as in the forward; warp w of a sub-tile's
   // 2 x 4 layout
   const sss_raster_cfg& cfg = P.cfg;
   const uint32_t SX = (uint32_t)cfg.tile_w / TW, SY = (uint32_t)cfg.tile_h / TH;
   const uint32_t cta = blockIdx.x >> 2, tile = cta / (SX * SY), sub = cta - tile * (SX * SY);
-  WarpBuf& S = s_wb[threadIdx.x >> 5];
+  WarpBuf<R>& S = s_wb[threadIdx.x >> 5];
   const int j = job_of_tile(P, tile);
   const sss_job_desc& J = P.jobs[j];
   const uint32_t lt = tile - J.tile_base;
@@ -168,50 +169,70 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
 
   // list positions are relative to range.x; pixel p has contributors in
   // [0, last[p]).  The warp walks its own contributors back to front in
-  // batches of 32: batch i covers [lo_i, hi_i), hi_0 = warp_max (the
-  // deepest contributor of the warp's pixels), lo_i = max(hi_i - 32, 0);
+  // batches of B: batch i covers [lo_i, hi_i), hi_0 = warp_max (the
+  // deepest contributor of the warp's pixels), lo_i = max(hi_i - B, 0);
   // batch i + 1 is gathered and the entry ids of batch i + 2 are loaded
   // while batch i is evaluated.
-  const uint32_t n_batches = (warp_max + 31) / 32;
-  auto lo_of = [&](uint32_t i) { return warp_max > (i + 1) * 32 ? warp_max - (i + 1) * 32 : 0u; };
+  const uint32_t n_batches = (warp_max + B - 1) / B;
+  auto lo_of = [&](uint32_t i) { return warp_max > (i + 1) * B ? warp_max - (i + 1) * B : 0u; };
   if (n_batches > 0) {
     uint32_t lo = lo_of(0);
-    uint32_t e_next = lo + lane < warp_max ? __ldg(vals + lo + lane) : 0u;
-    warp_stage(S, 0, rec, e_next, lo + lane < warp_max, lane);
+    uint32_t e_next[R];
+    bool v_next[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t q = lo + r * 32 + lane;
+      v_next[r] = q < warp_max;
+      e_next[r] = v_next[r] ? __ldg(vals + q) : 0u;
+    }
+    warp_stage<R>(S, 0, rec, e_next, v_next, lane);
     if (n_batches > 1) {
       const uint32_t lo1 = lo_of(1);
-      e_next = lo1 + lane < lo ? __ldg(vals + lo1 + lane) : 0u;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const uint32_t q = lo1 + r * 32 + lane;
+        e_next[r] = q < lo ? __ldg(vals + q) : 0u;
+      }
     }
     for (uint32_t i = 0; i < n_batches; ++i) {
       lo = lo_of(i);
       const int k = (int)(i & 1);
       if (i + 1 < n_batches) {
         const uint32_t lo1 = lo_of(i + 1);
-        warp_stage(S, k ^ 1, rec, e_next, lo1 + lane < lo, lane);
-        e_next = 0u;
-        if (i + 2 < n_batches) {
-          const uint32_t lo2 = lo_of(i + 2);
-          if (lo2 + lane < lo1) e_next = __ldg(vals + lo2 + lane);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v_next[r] = lo1 + r * 32 + lane < lo;
+        warp_stage<R>(S, k ^ 1, rec, e_next, v_next, lane);
+        const uint32_t lo2 = i + 2 < n_batches ? lo_of(i + 2) : 0u;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const uint32_t q = lo2 + r * 32 + lane;
+          e_next[r] = (i + 2 < n_batches && q < lo1) ? __ldg(vals + q) : 0u;
         }
         cp_async_wait<1>();
       } else {
         cp_async_wait<0>();
       }
       __syncwarp();
-      unsigned m;
-      {
-        const float4 a = S.a[k][lane], b = S.b[k][lane];
+      unsigned mm[R];
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) {
+        const int sl = rr * 32 + lane;
+        const float4 a = S.a[k][sl], b = S.b[k][sl];
         int ox, oy;
-        rec_origin(S.c[k][lane].w, ox, oy);
+        rec_origin(S.c[k][sl].w, ox, oy);
         const bool hit = b.z >= 0.0f &&
                          ellipse_hits_box(a.x, a.y, a.z, a.w, b.x, fmaf(b.z, 2.0f * kHPad, b.z) + 1e-3f,
                                           (float)(bx - ox) + 0.5f, (float)(bx - ox + 8 * PW) - 0.5f,
                                           (float)(by - oy) + 0.5f, (float)(by - oy + 4 * PH) - 0.5f);
-        m = __ballot_sync(0xffffffffu, hit);
+        mm[rr] = __ballot_sync(0xffffffffu, hit);
       }
+#pragma unroll
+      for (int rr = R - 1; rr >= 0; --rr) {
+      unsigned m = mm[rr];
       while (m) {
-        const int si = 31 - __clz(m);
-        m &= ~(1u << si);
+        const int sb = 31 - __clz(m);
+        m &= ~(1u << sb);
+        const int si = rr * 32 + sb;
         const uint32_t pos = lo + si;
         const float4 a = S.a[k][si], b = S.b[k][si], c = S.c[k][si];
         const float cb2 = 2.0f * a.w;
@@ -358,24 +379,31 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
           if (slot >= 0) atomicAdd(g2d + (size_t)S.e[k][si] * 12 + slot, tot);
         }
       }
+      }
       __syncwarp();  // every lane is done with buffer k before it is refilled
     }
     cp_async_wait<0>();
   }
 }
 
-template <int PW, int PH, bool PAPER_NU>
+template <int PW, int PH, int R, bool PAPER_NU>
 int launch_batch(const sss_frame_plan& P, void* ws, const float* g, cudaStream_t st) {
-  // 32 records per warp and round (the only staging depth the plan accepts)
   const unsigned subs = (unsigned)(P.cfg.tile_w / (16 * PW)) * (unsigned)(P.cfg.tile_h / (16 * PH));
-  k_render_bwd<PW, PH, PAPER_NU><<<4 * subs * P.n_tiles, 64, 0, st>>>(P, ws, g);
+  k_render_bwd<PW, PH, R, PAPER_NU><<<4 * subs * P.n_tiles, 64, 0, st>>>(P, ws, g);
   SSS_LAUNCH_CHECK();
   return SSS_OK;
 }
 
+template <int PW, int PH, bool PAPER_NU>
+int launch_depth(const sss_frame_plan& P, void* ws, const float* g, cudaStream_t st) {
+  // records staged per warp and round: cfg.batch = 32 or 64 (checked by the plan)
+  return P.cfg.batch == 64 ? launch_batch<PW, PH, 2, PAPER_NU>(P, ws, g, st)
+                           : launch_batch<PW, PH, 1, PAPER_NU>(P, ws, g, st);
+}
+
 template <int PW, int PH>
 int launch_tile(const sss_frame_plan& P, void* ws, const float* g, cudaStream_t st) {
-  return P.cfg.nu_grad_mode == 1 ? launch_batch<PW, PH, true>(P, ws, g, st) : launch_batch<PW, PH, false>(P, ws, g, st);
+  return P.cfg.nu_grad_mode == 1 ? launch_depth<PW, PH, true>(P, ws, g, st) : launch_depth<PW, PH, false>(P, ws, g, st);
 }
 
 }  // namespace

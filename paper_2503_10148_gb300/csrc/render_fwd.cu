@@ -6,10 +6,11 @@
 // 2 x 4, run as four CTAs of two warps; warp w owns an (8 PW) x (4 PH) box
 // and lane l a PW x PH block of pixels inside it.  Warps are
 // independent (no CTA barrier): each walks the tile's list in rounds of 32
-// records, one 48-byte record per lane gathered by entry index with
-// cp.async into the warp's own double buffer (the next round is in flight
-// while this one is evaluated).  The warp tests the 32 staged splats against
-// its box in parallel (exact ellipse/box test) and walks only the
+// or 64 records (cfg.batch; one or two 48-byte records per lane) gathered
+// by entry index with cp.async into the warp's own double buffer (the next
+// round is in flight while this one is evaluated).  The warp tests the
+// staged splats against its box in parallel (exact ellipse/box test) and
+// walks only the
 // survivors, in list (= depth) order, so pairs whose ellipse misses the
 // warp's 32 PW PH pixels cost nothing; it stops when all its pixels are
 // done.  A lane's pixels are evaluated two at a time with packed FP32
@@ -21,14 +22,15 @@
 namespace sss {
 namespace {
 
-template <int PW, int PH, bool COUNT>
+template <int PW, int PH, int R, bool COUNT>
 __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, void* ws, float* __restrict__ out_rgb) {
   constexpr int NPIX = PW * PH;
+  constexpr uint32_t B = 32 * R;  // records per warp and round
   constexpr int TW = 16 * PW, TH = 16 * PH;
   constexpr int L = LaneVec<NPIX>::L, NV = LaneVec<NPIX>::NV;
   using V = typename std::conditional<L == 2, F2, float>::type;
   using M = MaskT<V>;
-  __shared__ WarpBuf s_wb[2];
+  __shared__ WarpBuf<R> s_wb[2];
 
   // a list tile of cfg.tile_w x cfg.tile_h pixels is rendered as SX x SY
   // sub-tiles of TW x TH, each by four CTAs of two warps; warp w of the
@@ -38,7 +40,7 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
   const uint32_t SX = (uint32_t)cfg.tile_w / TW, SY = (uint32_t)cfg.tile_h / TH;
   const uint32_t cta = blockIdx.x >> 2, tile = cta / (SX * SY), sub = cta - tile * (SX * SY);
   const int warp = (int)((blockIdx.x & 3u) << 1) | (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
-  WarpBuf& S = s_wb[threadIdx.x >> 5];
+  WarpBuf<R>& S = s_wb[threadIdx.x >> 5];
   const int j = job_of_tile(P, tile);
   const sss_job_desc& J = P.jobs[j];
   const uint32_t lt = tile - J.tile_base;
@@ -78,30 +80,49 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
   uint32_t n_eval = 0, n_contrib = 0;  // pair counters (COUNT only)
 
   const uint32_t n_list = range.y - range.x;
-  const uint32_t n_batches = (n_list + 31) / 32;
+  const uint32_t n_batches = (n_list + B - 1) / B;
   if (!warp_done && n_batches > 0) {
-    // batch i = list positions [32 i, 32 i + 32); batch i + 1 is gathered and
+    // batch i = list positions [B i, B i + B); batch i + 1 is gathered and
     // the entry ids of batch i + 2 are loaded while batch i is evaluated
-    uint32_t e_next = lane < n_list ? __ldg(vals + lane) : 0u;
-    warp_stage(S, 0, rec, e_next, lane < n_list, lane);
-    if (n_batches > 1) e_next = 32 + lane < n_list ? __ldg(vals + 32 + lane) : 0u;
+    uint32_t e_next[R];
+    bool v_next[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t q = r * 32 + lane;
+      v_next[r] = q < n_list;
+      e_next[r] = v_next[r] ? __ldg(vals + q) : 0u;
+    }
+    warp_stage<R>(S, 0, rec, e_next, v_next, lane);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t q = B + r * 32 + lane;
+      e_next[r] = (n_batches > 1 && q < n_list) ? __ldg(vals + q) : 0u;
+    }
     for (uint32_t i = 0; i < n_batches && !warp_done; ++i) {
-      const uint32_t p0 = i * 32;
+      const uint32_t p0 = i * B;
       const int k = (int)(i & 1);
       if (i + 1 < n_batches) {
-        warp_stage(S, k ^ 1, rec, e_next, p0 + 32 + lane < n_list, lane);
-        const uint32_t q = p0 + 64 + lane;
-        e_next = (i + 2 < n_batches && q < n_list) ? __ldg(vals + q) : 0u;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v_next[r] = p0 + B + r * 32 + lane < n_list;
+        warp_stage<R>(S, k ^ 1, rec, e_next, v_next, lane);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const uint32_t q = p0 + 2 * B + r * 32 + lane;
+          e_next[r] = (i + 2 < n_batches && q < n_list) ? __ldg(vals + q) : 0u;
+        }
         cp_async_wait<1>();
       } else {
         cp_async_wait<0>();
       }
       __syncwarp();
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) {
       unsigned m;
       {
-        const float4 a = S.a[k][lane], b = S.b[k][lane];
+        const int sl = rr * 32 + lane;
+        const float4 a = S.a[k][sl], b = S.b[k][sl];
         int ox, oy;
-        rec_origin(S.c[k][lane].w, ox, oy);
+        rec_origin(S.c[k][sl].w, ox, oy);
         const bool hit = b.z >= 0.0f &&
                          ellipse_hits_box(a.x, a.y, a.z, a.w, b.x, fmaf(b.z, 2.0f * kHPad, b.z) + 1e-3f,
                                           (float)(bx - ox) + 0.5f, (float)(bx - ox + 8 * PW) - 0.5f,
@@ -109,7 +130,7 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
         m = __ballot_sync(0xffffffffu, hit);
       }
       while (m && !warp_done) {
-        const int si = __ffs(m) - 1;
+        const int si = rr * 32 + __ffs(m) - 1;
         m &= m - 1;
         const float4 a = S.a[k][si], b = S.b[k][si], c = S.c[k][si];
         const float cb2 = 2.0f * a.w, inv_nu = __fdividef(1.0f, b.w);
@@ -179,6 +200,7 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
         }
         warp_done = __all_sync(0xffffffffu, ld);
       }
+      }
       __syncwarp();  // every lane is done with buffer k before it is refilled
     }
     cp_async_wait<0>();  // no copy into this warp's buffers outlives the loop
@@ -212,16 +234,21 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
   }
 }
 
-template <int PW, int PH>
-int launch_batch(const sss_frame_plan& P, void* ws, float* out, cudaStream_t st) {
-  // the staging batch is 32 records per warp (the only value the plan accepts)
+template <int PW, int PH, int R>
+int launch_depth(const sss_frame_plan& P, void* ws, float* out, cudaStream_t st) {
   const unsigned subs = (unsigned)(P.cfg.tile_w / (16 * PW)) * (unsigned)(P.cfg.tile_h / (16 * PH));
   if (P.cfg.count_pairs)
-    k_render_fwd<PW, PH, true><<<4 * subs * P.n_tiles, 64, 0, st>>>(P, ws, out);
+    k_render_fwd<PW, PH, R, true><<<4 * subs * P.n_tiles, 64, 0, st>>>(P, ws, out);
   else
-    k_render_fwd<PW, PH, false><<<4 * subs * P.n_tiles, 64, 0, st>>>(P, ws, out);
+    k_render_fwd<PW, PH, R, false><<<4 * subs * P.n_tiles, 64, 0, st>>>(P, ws, out);
   SSS_LAUNCH_CHECK();
   return SSS_OK;
+}
+
+template <int PW, int PH>
+int launch_batch(const sss_frame_plan& P, void* ws, float* out, cudaStream_t st) {
+  // records staged per warp and round: cfg.batch = 32 or 64 (checked by the plan)
+  return P.cfg.batch == 64 ? launch_depth<PW, PH, 2>(P, ws, out, st) : launch_depth<PW, PH, 1>(P, ws, out, st);
 }
 
 }  // namespace

@@ -129,7 +129,7 @@ def test_plan_rejects_bad_arguments(lib, bad):
         cfg.tile_w = 8
         expect = _abi.SSS_ERR_UNSUPPORTED
     elif bad == "batch":
-        cfg.batch = 64  # one record per lane and round: only 32 is built
+        cfg.batch = 48  # 32 or 64 records per warp and round
         expect = _abi.SSS_ERR_UNSUPPORTED
     elif bad == "deg":
         scenes = [_dummy_scene(10, 4)]

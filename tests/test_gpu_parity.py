@@ -189,11 +189,13 @@ def _check_forward(fr, scene, cams, cfgd, pix=None):
     return worst, flagged
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (32, 16), (16, 32), (32, 32), (64, 32), (32, 64), (64, 64), (64, 16),
-                                  (128, 64), (128, 128)])
-def test_forward_tiny_all_tile_configs(tile):
+@pytest.mark.parametrize("tile,batch", [((16, 16), 32), ((32, 16), 32), ((16, 32), 32), ((32, 32), 32),
+                                        ((64, 32), 32), ((32, 64), 32), ((64, 64), 32), ((64, 16), 32),
+                                        ((128, 64), 32), ((128, 128), 32), ((16, 16), 64), ((32, 32), 64),
+                                        ((64, 128), 64)])
+def test_forward_tiny_all_tile_configs(tile, batch):
     scene, cams = inputs.tiny_cube_2k()
-    cfg = frame.make_cfg(tile_w=tile[0], tile_h=tile[1])
+    cfg = frame.make_cfg(tile_w=tile[0], tile_h=tile[1], batch=batch)
     fr, _, cams = gpu_forward(scene, cams, cfg)
     _check_forward(fr, f32_scene(scene), cams, frame.cfg_dict(cfg))
 
@@ -319,10 +321,12 @@ def _grad2d_report(fr, g2d_ref, g2d_abs, cams, scene):
 
 
 @pytest.mark.parametrize("nu_mode,tile", [(0, (16, 16)), (1, (16, 16)), (0, (32, 16)), (0, (16, 32)), (1, (32, 32)),
-                                          (0, (64, 32)), (1, (32, 64)), (0, (64, 64)), (1, (128, 128))])
+                                          (0, (64, 32)), (1, (32, 64)), (0, (64, 64)), (1, (128, 128)),
+                                          (0, (16, 16, 64)), (1, (64, 128, 64))])
 def test_backward_tiny_against_oracle_analytic(nu_mode, tile):
     scene, cams = inputs.tiny_cube_2k()
-    cfg = frame.make_cfg(nu_grad_mode=nu_mode, tile_w=tile[0], tile_h=tile[1])
+    batch = tile[2] if len(tile) > 2 else 32  # records per warp and staging round
+    cfg = frame.make_cfg(nu_grad_mode=nu_mode, tile_w=tile[0], tile_h=tile[1], batch=batch)
     fr, sc, cams = gpu_forward(scene, cams, cfg)
     cfgd = frame.cfg_dict(cfg)
     s32 = f32_scene(scene)
