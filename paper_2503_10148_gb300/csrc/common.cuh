@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "sss.h"
 
 namespace sss {
@@ -274,26 +276,35 @@ __device__ __forceinline__ V conic_h(V dx, V dy, float ca, float cb2, float cc) 
   return vfma(dx, t, vmul(vmul(vsplat<V>(cc), dy), dy));
 }
 
-template <class V>
+// CLAMP = false when |o| T2D cannot reach alpha_max (the caller checks |o|
+// against alpha_max with a margin for T2D's rounding above 1 near h = 0):
+// then the clamp is the identity and is taken out per splat.
+template <class V, bool CLAMP = true>
 __device__ __forceinline__ MaskT<V> finish_pair(V h, V t2d, V lb, float oabs, float osgn, float tau, float amax,
                                                 PairEval<V>& r) {
   const V aabs = vmul(vsplat<V>(oabs), t2d);
   r.h = h;
   r.t2d = t2d;
-  r.alpha = vmul(vsplat<V>(osgn), vmin(aabs, amax));
+  if constexpr (CLAMP) {
+    r.alpha = vmul(vsplat<V>(osgn), vmin(aabs, amax));
+    r.clamped = vgt(aabs, amax);
+  } else {
+    r.alpha = vmul(vsplat<V>(osgn), aabs);
+    if constexpr (std::is_same<V, F2>::value) r.clamped = B2{false, false};
+    else r.clamped = false;
+  }
   r.log_base = lb;
-  r.clamped = vgt(aabs, amax);
   return vge(aabs, tau);
 }
 
-template <class V>
+template <class V, bool CLAMP = true>
 __device__ __forceinline__ MaskT<V> eval_pair_fast(V dx, V dy, float ca, float cb2, float cc, float oabs, float osgn,
                                                    float nu, float inv_nu, float tau, float amax, PairEval<V>& r) {
   const V h = conic_h(dx, dy, ca, cb2, cc);
   const float e = fmaf(nu, -0.5f, -1.0f);  // -(nu + 2) / 2
   const V l2 = vlg2(vfma(h, vsplat<V>(inv_nu), vsplat<V>(1.0f)));
-  return finish_pair(h, vex2(vmul(vsplat<V>(e), l2)), vmul(l2, vsplat<V>(0.69314718055994531f)), oabs, osgn, tau,
-                     amax, r);
+  return finish_pair<V, CLAMP>(h, vex2(vmul(vsplat<V>(e), l2)), vmul(l2, vsplat<V>(0.69314718055994531f)), oabs,
+                               osgn, tau, amax, r);
 }
 
 template <class V>

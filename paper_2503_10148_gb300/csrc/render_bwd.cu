@@ -261,7 +261,13 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
         // uniform over the warp
         PairEval<V> r[NV];
         M ok[NV];
-        if (nu <= kFastNuMax) {
+        // the alpha clamp is the identity when |o| T2D cannot reach alpha_max
+        // (the forward makes the same choice, so both take identical decisions)
+        if (nu <= kFastNuMax && oabs * 1.0001f <= amax) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v)
+            ok[v] = eval_pair_fast<V, false>(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, nu, inv_nu, tau, amax, r[v]);
+        } else if (nu <= kFastNuMax) {
 #pragma unroll
           for (int v = 0; v < NV; ++v)
             ok[v] = eval_pair_fast(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, nu, inv_nu, tau, amax, r[v]);

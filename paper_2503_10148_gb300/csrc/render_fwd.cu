@@ -155,7 +155,14 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
         // branch is uniform over the warp
         PairEval<V> r[NV];
         M ok[NV];
-        if (b.w <= kFastNuMax) {
+        // the alpha clamp is the identity when |o| T2D cannot reach alpha_max;
+        // T2D <= 1 up to the rounding of h near 0 (a few 1e-6 at most for
+        // nu <= kFastNuMax), hence the margin
+        if (b.w <= kFastNuMax && oabs * 1.0001f <= amax) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v)
+            ok[v] = eval_pair_fast<V, false>(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, b.w, inv_nu, tau, amax, r[v]);
+        } else if (b.w <= kFastNuMax) {
 #pragma unroll
           for (int v = 0; v < NV; ++v)
             ok[v] = eval_pair_fast(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, b.w, inv_nu, tau, amax, r[v]);
