@@ -46,7 +46,7 @@ MUFU_PER_SM_CLK = 16
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 # algorithmic work per contributing (splat, pixel) pair, counted from the
-# method's formulas: FP32 flops (FMA = 2) and MUFU ops
+# method's formulas (not our instructions): FP32 flops (FMA = 2) and MUFU ops
 FWD_FLOPS, FWD_MUFU = 22, 2
 BWD_FLOPS, BWD_MUFU = 75, 4
 

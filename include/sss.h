@@ -333,7 +333,7 @@ int sss_loss_l1(const float* pred, const float* target, uint32_t count, float* d
 int sss_loss_l1_grad(const float* pred, const float* target, uint32_t count, const float* dL_dloss,
                      float* dL_dpred, sss_stream_t stream);
 
-/* Image loss of Sec. 3.4 over every image of a frame (NEXT-1):
+/* Image loss of Sec. 3.4 over every image of a frame:
  *   L = (1 - eps_dssim) L1 + eps_dssim (1 - SSIM),
  * L1 and SSIM both averaged over all pixels and channels of all jobs.  SSIM
  * as in 3DGS (the loss the paper cites): 11 x 11 Gaussian window with sigma

@@ -1,5 +1,5 @@
-"""Variants of the method on the GPU against the oracle: the
-Adam gradient in the SGHMC update of the means."""
+"""Variants of the method on the GPU against the oracle: the Adam gradient
+in the SGHMC update of the means, and the Gaussian kernel (nu -> infinity)."""
 import numpy as np
 import pytest
 import torch
