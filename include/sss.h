@@ -106,10 +106,11 @@ typedef struct sss_camera {
 
 /* ------------------------------------------------------ raster options */
 typedef struct sss_raster_cfg {
-  int32_t tile_w, tile_h; /* 16, 32, 64 or 128 pixels each: the tiles of the pair
-                             lists; the render runs sub-tiles of at most
-                             32 x 32 (eight warps, lanes of up to 2 x 2
-                             pixels), each walking its tile's whole list   */
+  int32_t tile_w, tile_h; /* 16, 32, 64 (default) or 128 pixels each: the
+                             tiles of the pair lists; the render runs
+                             sub-tiles of at most 32 x 32 (eight warps,
+                             lanes of up to 2 x 2 pixels), each walking its
+                             tile's whole list                             */
   int32_t batch;          /* records each warp stages in shared memory per
                              round (double buffered, cp.async): 32 or 64,
                              one or two per lane                          */

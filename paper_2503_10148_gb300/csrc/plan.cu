@@ -22,8 +22,8 @@ int sss_version(void) { return 100; }
 void sss_default_cfg(sss_raster_cfg* cfg) {
   if (!cfg) return;
   std::memset(cfg, 0, sizeof(*cfg));
-  cfg->tile_w = 16;
-  cfg->tile_h = 16;
+  cfg->tile_w = 64;  // list tiles of 64 x 64, rendered as 32 x 32 sub-tiles
+  cfg->tile_h = 64;
   cfg->batch = 32;
   cfg->nu_grad_mode = 0;
   cfg->tau = 1.0f / 255.0f;

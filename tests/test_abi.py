@@ -70,7 +70,7 @@ def test_status_strings_and_defaults(lib):
     assert _abi.status_string(0) == "ok"
     assert "capacity" in _abi.status_string(-2)
     c = _abi.sss_default_cfg()
-    assert (c.tile_w, c.tile_h, c.batch) == (16, 16, 32)
+    assert (c.tile_w, c.tile_h, c.batch) == (64, 64, 32)
     assert abs(c.tau - 1 / 255) < 1e-9 and abs(c.t_min - 1e-4) < 1e-10 and abs(c.alpha_max - 0.99) < 1e-7
     assert c.lowpass == 0.0 and c.znear == pytest.approx(0.2)
     assert _abi.sss_version() >= 100
@@ -97,7 +97,9 @@ def _cam(w, h):
 def test_plan_layout_and_offsets(lib):
     scenes = [_dummy_scene(1000), _dummy_scene(37, 0)]
     cams = [_cam(1297, 840), _cam(100, 60), _cam(17, 16)]
-    plan = _abi.sss_plan_frame(scenes, cams, [0, 1, 0], _abi.sss_default_cfg(), 5000)
+    cfg16 = _abi.sss_default_cfg()
+    cfg16.tile_w = cfg16.tile_h = 16
+    plan = _abi.sss_plan_frame(scenes, cams, [0, 1, 0], cfg16, 5000)
     assert plan.n_entries == 1000 + 37 + 1000
     tiles = [82 * 53, 7 * 4, 2 * 1]
     assert plan.n_tiles == sum(tiles)

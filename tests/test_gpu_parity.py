@@ -211,7 +211,7 @@ def test_forward_last_contributor_matches_oracle():
     v = v.cpu().numpy().astype(np.int64)
     W = cams[0].width
     ys, xs = np.divmod(np.arange(W * cams[0].height), W)
-    tile = (ys // 16) * fr.plan.jobs[0].tiles_x + xs // 16
+    tile = (ys // fr.cfg.tile_h) * fr.plan.jobs[0].tiles_x + xs // fr.cfg.tile_w
     comp = np.where(last > 0, v[np.maximum(rng[tile, 0] + last - 1, 0)], -1)
     ok = ref["flags"] == 0
     assert np.array_equal(comp[ok], ref["last"][ok])
@@ -256,7 +256,7 @@ def test_forward_shell_8views_800_sampled():
 def test_forward_edge_cases(case):
     scene = inputs.scene_uniform_cube(1500, seed=11)
     cam = inputs.look_at((0.3, -0.2, 3.0), width=100, height=60)
-    kw = {}
+    kw = dict(tile_w=16, tile_h=16)  # one pixel per lane (scalar FP32)
     if case.endswith("_packed"):  # 32x32 tiles: pixels in packed pairs
         case = case[:-len("_packed")]
         kw.update(tile_w=32, tile_h=32)
