@@ -185,8 +185,8 @@ def _cfg(args):
 
 def stage_breakdown(ts, reps, device):
     """Eager steps with CUDA events between the stages (same stream); like
-    the timed steps, each starts from the configured scene (the copy is
-    outside the events)."""
+    the timed steps, each starts from the configured scene (the sampler
+    writes its update beside it)."""
     import torch
     from paper_2503_10148_gb300 import frame as F
     fr = ts.frame
@@ -194,10 +194,6 @@ def stage_breakdown(ts, reps, device):
     names = ["project", "bin", "sort", "render_fwd", "loss", "render_bwd", "project_bwd", "sghmc_step"]
     acc = {n: 0.0 for n in names}
     for _ in range(reps):
-        if ts.initial is not None:
-            with torch.no_grad():
-                for f in F.FIELDS:
-                    ts.scene.t[f].copy_(ts.initial[f])
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
         ev[0].record(st)
         fr.project(st); ev[1].record(st)
@@ -212,7 +208,7 @@ def stage_breakdown(ts, reps, device):
         ev[5].record(st)
         fr.render_bwd(ts.dl, st); ev[6].record(st)
         fr.project_bwd([ts.grads], st); ev[7].record(st)
-        F.sghmc_step(ts.scene, ts.grads, ts.state, ts.sp, stream=st); ev[8].record(st)
+        ts.sample(st); ev[8].record(st)
         torch.cuda.synchronize(device)
         for i, n in enumerate(names):
             acc[n] += ev[i].elapsed_time(ev[i + 1])
@@ -224,11 +220,8 @@ def count_pairs(ts, device):
     step renders: the step starts from the configured scene, so one counting
     forward of that scene (outside the timed region) gives them."""
     import torch
-    from paper_2503_10148_gb300 import frame as F
+    assert ts.after is not None, "the timed steps must leave the configured scene unchanged"
     torch.cuda.synchronize(device)
-    with torch.no_grad():
-        for f in F.FIELDS:
-            ts.scene.t[f].copy_(ts.initial[f])
     out = ts.frame.count_pairs()
     torch.cuda.synchronize(device)
     return out
@@ -330,8 +323,8 @@ def run_ours(args):
     scene = F.Scene.from_numpy(scene_np, device)
     targets = torch.as_tensor(targets_np, device=device)
     cfg, cfg_src = _cfg(args)
-    # every timed step starts from the configured scene (a device copy inside
-    # the captured step), so the workload does not drift under the sampler
+    # every timed step starts from the configured scene (the sampler writes
+    # its update beside it), so the workload does not drift under the sampler
     ts = train.TrainStep(scene, cams, targets, cfg=cfg, device=device, loss="full", eps_dssim=0.2, reg_opacity=0.01,
                          reg_scale=0.01, restart=True)
     ts.calibrate()

@@ -319,6 +319,19 @@ typedef struct sss_step_params {
 int sss_sghmc_step(const sss_params* params, const sss_params* grads, float* momentum, float* adam_m,
                    float* adam_v, const sss_step_params* sp, float* xi_out, sss_stream_t stream);
 
+/* The same step with the updated parameters written to params_out (device
+ * arrays of the same layout, n and sh_degree) instead of over params, which
+ * it then only reads; momentum, the Adam moments and the step counter are
+ * updated in place as above.  params_out's arrays are either params' own
+ * (the step in place: sss_sghmc_step is this call with params_out = params)
+ * or arrays that overlap none of params'.  Lets a caller keep the pre-step
+ * parameters, e.g. to run repeated steps from one configuration without
+ * copying it back.  Errors as sss_sghmc_step, and SSS_ERR_INVALID_ARG for a
+ * NULL params_out or one whose n or sh_degree differs. */
+int sss_sghmc_step_to(const sss_params* params, const sss_params* params_out, const sss_params* grads,
+                      float* momentum, float* adam_m, float* adam_v, const sss_step_params* sp, float* xi_out,
+                      sss_stream_t stream);
+
 /* L1 term of the loss (Sec. 3.4): loss_out[0] = sum |pred - target| / count
  * (overwritten; the partial sums are added in an unspecified order) and,
  * when dL_dpred is not NULL, dL_dpred = sign(pred - target) / count (0 where

@@ -95,6 +95,8 @@ _SIGS = {
     "sss_project_bwd": [POINTER(sss_frame_plan), c_void_p, POINTER(sss_params), c_void_p],
     "sss_sghmc_step": [POINTER(sss_params), POINTER(sss_params), c_void_p, c_void_p, c_void_p,
                        POINTER(sss_step_params), c_void_p, c_void_p],
+    "sss_sghmc_step_to": [POINTER(sss_params), POINTER(sss_params), POINTER(sss_params), c_void_p, c_void_p,
+                          c_void_p, POINTER(sss_step_params), c_void_p, c_void_p],
     "sss_loss_l1": [c_void_p, c_void_p, c_uint32, c_void_p, c_void_p, c_void_p],
     "sss_loss_l1_grad": [c_void_p, c_void_p, c_uint32, c_void_p, c_void_p, c_void_p],
     "sss_loss_image": [POINTER(sss_frame_plan), c_void_p, c_void_p, c_float, c_void_p, c_void_p, c_void_p],
@@ -211,6 +213,15 @@ def sss_sghmc_step(params: sss_params, grads: sss_params, momentum_ptr: int, ada
     _check("sss_sghmc_step", lib().sss_sghmc_step(ctypes.byref(params), ctypes.byref(grads), c_void_p(momentum_ptr),
                                                   c_void_p(adam_m_ptr), c_void_p(adam_v_ptr), ctypes.byref(sp),
                                                   c_void_p(xi_out_ptr or None), _stream(stream)))
+
+
+def sss_sghmc_step_to(params: sss_params, params_out: sss_params, grads: sss_params, momentum_ptr: int,
+                      adam_m_ptr: int, adam_v_ptr: int, sp: sss_step_params, xi_out_ptr: int = 0, stream=None):
+    _check("sss_sghmc_step_to", lib().sss_sghmc_step_to(ctypes.byref(params), ctypes.byref(params_out),
+                                                        ctypes.byref(grads), c_void_p(momentum_ptr),
+                                                        c_void_p(adam_m_ptr), c_void_p(adam_v_ptr),
+                                                        ctypes.byref(sp), c_void_p(xi_out_ptr or None),
+                                                        _stream(stream)))
 
 
 def sss_loss_l1(pred_ptr: int, target_ptr: int, count: int, grad_ptr: int, loss_ptr: int, stream=None):

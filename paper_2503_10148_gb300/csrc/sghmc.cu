@@ -5,7 +5,8 @@
 // four components per thread with their loads in flight).  Pure streaming:
 // per component at SH degree 3 they read parameters, gradients and moments
 // and write parameters and moments back (about 1.6 KB), so they run at HBM
-// speed.
+// speed.  The updated parameters go to a second set of arrays, which may be
+// the input arrays themselves (an update in place).
 //
 // Noise: Philox4x32-10 (Salmon et al., SC'11) -- ten rounds of two 32x32->64
 // multiplications by the published multipliers on counter words 0 and 2,
@@ -21,7 +22,8 @@ namespace sss {
 namespace {
 
 struct StepArgs {
-  sss_params p, g;
+  sss_params p, g;  // parameters before the step, gradients
+  sss_params q;     // parameters after the step (q's arrays may be p's)
   float* r;
   float* m;
   float* v;
@@ -65,6 +67,15 @@ __device__ __forceinline__ StepNow step_now(const StepArgs& a) {
 // Each thread updates kPer components with all their loads in flight.
 constexpr int kPer = 4;
 
+// Row `row` (numbered as above) of a parameter set of n components.
+__device__ __forceinline__ float* param_row(const sss_params& s, int row, size_t n) {
+  if (row < 3) return s.log_scale + row * n;
+  if (row < 7) return s.quat + (row - 3) * n;
+  if (row == 7) return s.nu;
+  if (row == 8) return s.opacity_raw;
+  return s.sh + (row - 9) * n;
+}
+
 __global__ void __launch_bounds__(256) k_adam(const StepArgs a) {
   __shared__ StepNow s_t;
   if (threadIdx.x == 0) s_t = step_now(a);
@@ -72,21 +83,12 @@ __global__ void __launch_bounds__(256) k_adam(const StepArgs a) {
   const StepNow t = s_t;
   const int row = blockIdx.y;
   const size_t n = (size_t)a.p.n;
-  float* p;
-  const float* g;
-  float lr;
-  int reg = 0;
-  if (row < 3) {
-    p = a.p.log_scale + row * n, g = a.g.log_scale + row * n, lr = a.lr[0], reg = a.reg_s != 0.0f ? 1 : 0;
-  } else if (row < 7) {
-    p = a.p.quat + (row - 3) * n, g = a.g.quat + (row - 3) * n, lr = a.lr[1];
-  } else if (row == 7) {
-    p = a.p.nu, g = a.g.nu, lr = a.lr[2];
-  } else if (row == 8) {
-    p = a.p.opacity_raw, g = a.g.opacity_raw, lr = a.lr[3], reg = a.reg_o != 0.0f ? 2 : 0;
-  } else {
-    p = a.p.sh + (row - 9) * n, g = a.g.sh + (row - 9) * n, lr = a.lr[4];
-  }
+  const float* p = param_row(a.p, row, n);
+  float* p_out = param_row(a.q, row, n);
+  const float* g = param_row(a.g, row, n);
+  const int grp = row < 3 ? 0 : (row < 7 ? 1 : (row == 7 ? 2 : (row == 8 ? 3 : 4)));
+  const float lr = a.lr[grp];
+  const int reg = (row < 3 && a.reg_s != 0.0f) ? 1 : ((row == 8 && a.reg_o != 0.0f) ? 2 : 0);
   float* m = a.m + row * n;
   float* v = a.v + row * n;
   const size_t base = (size_t)blockIdx.x * (256 * kPer) + threadIdx.x;
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(256) k_adam(const StepArgs a) {
     v[i] = vv;
     float np = pp[k] - lr * (mm * t.inv_bc1) / (sqrtf(vv * t.inv_bc2) + a.adam_eps);
     if (row == 7) np = fminf(fmaxf(np, 1.0f), 1e4f);
-    p[i] = np;
+    p_out[i] = np;
   }
 }
 
@@ -177,7 +179,7 @@ __device__ __forceinline__ void step_component(const StepArgs& a, uint32_t i, co
     float mu = a.p.mean[j] - a.eps * a.eps * G;
     if (a.burn_in) mu += gate * a.eps * sq * noise[c];
     else mu += gate * a.eps * fr * rr + gate * a.eps * sq * xi[c];
-    a.p.mean[j] = mu;
+    a.q.mean[j] = mu;
   }
 }
 
@@ -202,11 +204,13 @@ __global__ void __launch_bounds__(256) k_sghmc(const StepArgs a) {
 }  // namespace
 }  // namespace sss
 
-extern "C" int sss_sghmc_step(const sss_params* params, const sss_params* grads, float* momentum, float* adam_m,
-                              float* adam_v, const sss_step_params* sp, float* xi_out, sss_stream_t stream) {
-  if (!params || !grads || !momentum || !adam_m || !adam_v || !sp) return SSS_ERR_INVALID_ARG;
+extern "C" int sss_sghmc_step_to(const sss_params* params, const sss_params* params_out, const sss_params* grads,
+                                 float* momentum, float* adam_m, float* adam_v, const sss_step_params* sp,
+                                 float* xi_out, sss_stream_t stream) {
+  if (!params || !params_out || !grads || !momentum || !adam_m || !adam_v || !sp) return SSS_ERR_INVALID_ARG;
   if (params->n < 0 || params->sh_degree < 0 || params->sh_degree > 3 || grads->n != params->n ||
-      grads->sh_degree != params->sh_degree)
+      grads->sh_degree != params->sh_degree || params_out->n != params->n ||
+      params_out->sh_degree != params->sh_degree)
     return SSS_ERR_INVALID_ARG;
   if (params->n == 0) return SSS_OK;
   if (!(sp->beta1 >= 0.0f && sp->beta1 < 1.0f && sp->beta2 >= 0.0f && sp->beta2 < 1.0f && sp->eps >= 0.0f &&
@@ -214,6 +218,7 @@ extern "C" int sss_sghmc_step(const sss_params* params, const sss_params* grads,
     return SSS_ERR_INVALID_ARG;
   sss::StepArgs a;
   a.p = *params;
+  a.q = *params_out;
   a.g = *grads;
   a.r = momentum;
   a.m = adam_m;
@@ -250,4 +255,9 @@ extern "C" int sss_sghmc_step(const sss_params* params, const sss_params* grads,
     SSS_LAUNCH_CHECK();
   }
   return SSS_OK;
+}
+
+extern "C" int sss_sghmc_step(const sss_params* params, const sss_params* grads, float* momentum, float* adam_m,
+                              float* adam_v, const sss_step_params* sp, float* xi_out, sss_stream_t stream) {
+  return sss_sghmc_step_to(params, params, grads, momentum, adam_m, adam_v, sp, xi_out, stream);
 }

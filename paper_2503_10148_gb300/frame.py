@@ -309,9 +309,16 @@ class SamplerState:
 
 
 def sghmc_step(scene: Scene, grads: Scene, state: SamplerState, sp: abi.sss_step_params, xi_out=None,
-               stream=None):
-    abi.sss_sghmc_step(scene.params(), grads.params(), state.r.data_ptr(), state.m.data_ptr(), state.v.data_ptr(),
-                       sp, xi_out.data_ptr() if xi_out is not None else 0, stream)
+               stream=None, out: Scene | None = None):
+    """One sampler step on ``scene``, in place, or into ``out`` (a scene of
+    the same size and degree, in separate memory) leaving ``scene`` as it was."""
+    xi = xi_out.data_ptr() if xi_out is not None else 0
+    if out is None:
+        abi.sss_sghmc_step(scene.params(), grads.params(), state.r.data_ptr(), state.m.data_ptr(),
+                           state.v.data_ptr(), sp, xi, stream)
+    else:
+        abi.sss_sghmc_step_to(scene.params(), out.params(), grads.params(), state.r.data_ptr(), state.m.data_ptr(),
+                              state.v.data_ptr(), sp, xi, stream)
 
 
 def loss_l1(pred: torch.Tensor, target: torch.Tensor, grad_out: torch.Tensor, loss_out: torch.Tensor, stream=None):

@@ -37,9 +37,10 @@ class TrainStep:
         Sec. 3.4, (1 - eps_dssim) L1 + eps_dssim D-SSIM plus the opacity and
         scale regularisers (their gradients added by the sampler step).
         ``restart=True`` starts every step from the parameters the step was
-        built with (one device-to-device copy at the start of the step, part
-        of the captured graph): repeated steps then run the same workload
-        instead of a scene that drifts under the sampler (for timing)."""
+        built with: the sampler writes its update into a second parameter set
+        (``self.after``, through sss_sghmc_step_to) and leaves the scene as
+        it was, so repeated steps run the same workload instead of a scene
+        that drifts under the sampler (for timing), with no copy back."""
         if form not in ("autograd", "direct") or loss not in ("l1", "full"):
             raise ValueError((form, loss))
         self.form = form
@@ -64,7 +65,7 @@ class TrainStep:
             self.loss = self.loss3[0:1]
         self.headroom = headroom
         self.graph = None
-        self.initial = {f: scene.t[f].detach().clone() for f in F.FIELDS} if restart else None
+        self.after = scene.zeros_like() if restart else None  # the sampler's output with restart
         if form == "autograd":
             self.leaves = AG.leaves(scene)
             self.one = torch.ones((), dtype=torch.float32, device=self.device)
@@ -83,10 +84,6 @@ class TrainStep:
         """Enqueue one step on the current stream (no host synchronisation)."""
         st = torch.cuda.current_stream(self.device)
         fr = self.frame
-        if self.initial is not None:
-            with torch.no_grad():
-                for f in F.FIELDS:
-                    self.scene.t[f].copy_(self.initial[f])
         if self.form == "autograd":
             rgb = AG.render(fr, self.leaves, grow=False)
             if self.loss_kind == "full":
@@ -96,7 +93,7 @@ class TrainStep:
             grads = torch.autograd.grad(loss, self.leaves, grad_outputs=self.one)
             self.rgb_out, self.loss = rgb, loss
             self.grads = F.Scene(dict(zip(F.FIELDS, grads)), self.scene.n, self.scene.sh_degree)
-            F.sghmc_step(self.scene, self.grads, self.state, self.sp, stream=st)
+            self.sample(st)
             return
         fr.project(st)
         fr.bin(st)
@@ -109,7 +106,12 @@ class TrainStep:
             F.loss_l1(fr.rgb, self.targets, self.dl, self.loss, st)
         fr.render_bwd(self.dl, st)
         fr.project_bwd([self.grads], st)
-        F.sghmc_step(self.scene, self.grads, self.state, self.sp, stream=st)
+        self.sample(st)
+
+    def sample(self, stream=None):
+        """The sampler step on this step's gradients: in place, or with
+        ``restart`` into ``self.after``."""
+        F.sghmc_step(self.scene, self.grads, self.state, self.sp, stream=stream, out=self.after)
 
     def time_kernels(self, names=("render_fwd", "render_bwd")) -> bool:
         """Record CUDA events around these launches in every later step,
@@ -190,13 +192,9 @@ class PlainStep:
         regs = dict(reg_opacity=reg_opacity, reg_scale=reg_scale) if loss == "full" else {}
         self.sp = F.step_params(step_counter=self.step_counter, **{**regs, **(sampler or {})})
         self.scratch = [F.loss_image_scratch(fr) for fr in self.frames] if loss == "full" else None
-        self.initial = {f: scene.t[f].detach().clone() for f in F.FIELDS} if restart else None
+        self.after = scene.zeros_like() if restart else None  # the sampler's output with restart
 
     def run(self):
-        if self.initial is not None:
-            with torch.no_grad():
-                for f in F.FIELDS:
-                    self.scene.t[f].copy_(self.initial[f])
         for v, (fr, tgt, dl, g) in enumerate(zip(self.frames, self.targets, self.dl, self.grads)):
             fr.forward(grow=True)
             if self.loss_kind == "full":
@@ -207,4 +205,4 @@ class PlainStep:
             fr.backward(dl, [g])
         for f in F.FIELDS:
             self.total.t[f].copy_(torch.stack([g.t[f] for g in self.grads]).sum(0))
-        F.sghmc_step(self.scene, self.total, self.state, self.sp)
+        F.sghmc_step(self.scene, self.total, self.state, self.sp, out=self.after)

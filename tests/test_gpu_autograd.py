@@ -161,3 +161,42 @@ def test_trainstep_autograd_graph_gradients_equal_direct():
     for f in frame.FIELDS:
         a, b = ts.grads.t[f], grads["direct"][f]
         assert float((a - b).norm()) <= 1e-5 * float(b.norm()) + 1e-30, f
+
+
+def test_trainstep_restart_replays_leave_the_scene_and_repeat_the_step():
+    """With restart, captured replays read the configured scene, leave it
+    unchanged and write the update beside it: with the sampler's step index
+    and moments reset, two replays write the same parameters, and the
+    gradients of every replay are those of the configured scene."""
+    scene, cams = inputs.shell_100k_8views()
+    scene = inputs.subset_scene(scene, np.arange(0, 100_000, 50))
+    cams = [frame.f32_camera(inputs.look_at(c.position, width=192, height=128)) for c in cams[:2]]
+    targets = torch.as_tensor(np.concatenate([t.reshape(-1) for t in inputs.target_images(cams, seed=4)]),
+                              device=DEV)
+    sc = frame.Scene.from_numpy(scene, DEV)
+    orig = {f: sc.t[f].detach().clone() for f in frame.FIELDS}
+    ts = train.TrainStep(sc, cams, targets, device=DEV, form="autograd", loss="full", restart=True)
+    ts.calibrate()
+    ts.capture()
+    outs, grads = [], []
+    for _ in range(2):
+        ts.step_counter.zero_()
+        for x in (ts.state.r, ts.state.m, ts.state.v):
+            x.zero_()
+        ts.replay()
+        torch.cuda.synchronize()
+        ts.check()
+        outs.append({f: ts.after.t[f].clone() for f in frame.FIELDS})
+        grads.append({f: ts.grads.t[f].detach().clone() for f in frame.FIELDS})
+    for f in frame.FIELDS:
+        assert torch.equal(sc.t[f].detach(), orig[f]), f
+        assert not torch.equal(outs[0][f], orig[f]), f
+        # same parameters in: the same gradients up to the order of the float
+        # atomics of render_bwd
+        ga, gb = grads[0][f], grads[1][f]
+        assert float((ga - gb).norm()) <= 1e-5 * float(gb.norm()) + 1e-30, f
+    # same gradients, noise and moments: the same SGHMC update of the means
+    # (linear in the gradient; the first Adam step of the other groups moves
+    # by lr sign(g), which the atomics' order may flip where g is near 0)
+    a, b = outs[0]["mean"], outs[1]["mean"]
+    assert float((a - b).abs().max()) <= 1e-6 * max(float(a.abs().max()), 1.0)

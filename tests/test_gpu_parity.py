@@ -454,6 +454,41 @@ def test_sghmc_step_against_oracle(burn_in, step):
     assert np.allclose(st.v.cpu().numpy().reshape(-1), vv[3 * n:], rtol=1e-5, atol=1e-7)
 
 
+@pytest.mark.parametrize("burn_in", [False, True])
+def test_sghmc_step_to_matches_the_step_in_place(burn_in):
+    """sss_sghmc_step_to writes bit for bit the parameters the in-place step
+    leaves (regularisers on), updates momentum and moments identically, and
+    leaves its input parameters as they were."""
+    scene = inputs.scene_sphere_shell(5000, seed=11)
+    rng = np.random.default_rng(12)
+    a, b, orig = (frame.Scene.from_numpy(scene, DEV) for _ in range(3))
+    grads = a.zeros_like()
+    for f in frame.FIELDS:
+        grads.t[f].copy_(torch.as_tensor(rng.normal(size=tuple(grads.t[f].shape)).astype(np.float32)))
+    sa, sb = frame.SamplerState(a), frame.SamplerState(b)
+    r0 = torch.as_tensor(rng.normal(size=tuple(sa.r.shape)).astype(np.float32) * 0.1, device=DEV)
+    m0 = torch.as_tensor(rng.normal(size=tuple(sa.m.shape)).astype(np.float32) * 0.01, device=DEV)
+    v0 = torch.as_tensor(np.abs(rng.normal(size=tuple(sa.v.shape))).astype(np.float32) * 0.01, device=DEV)
+    for s in (sa, sb):
+        s.r.copy_(r0)
+        s.m.copy_(m0)
+        s.v.copy_(v0)
+    kw = dict(eps=2e-2, C=0.6, burn_in=burn_in, seed=3, step=7, reg_opacity=0.01, reg_scale=0.01)
+    out = b.zeros_like()
+    frame.sghmc_step(a, grads, sa, frame.step_params(**kw))
+    frame.sghmc_step(b, grads, sb, frame.step_params(**kw), out=out)
+    torch.cuda.synchronize()
+    for f in frame.FIELDS:
+        assert torch.equal(out.t[f], a.t[f]), f
+        assert torch.equal(b.t[f], orig.t[f]), f
+        assert not torch.equal(a.t[f], orig.t[f]), f  # the step moved every group
+    for x, y in ((sa.r, sb.r), (sa.m, sb.m), (sa.v, sb.v)):
+        assert torch.equal(x, y)
+    bad = frame.Scene.zeros(b.n - 1, b.sh_degree, DEV)
+    with pytest.raises(_abi.SSSError):
+        frame.sghmc_step(b, grads, sb, frame.step_params(**kw), out=bad)
+
+
 def test_sghmc_noise_moments_on_gpu():
     n = 1_000_000
     scene = inputs.scene_uniform_cube(n, seed=2)
