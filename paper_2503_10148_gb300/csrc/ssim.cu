@@ -23,6 +23,11 @@ namespace {
 constexpr int TX = 32, TY = 32, R = 5, HX = TX + 2 * R, HY = TY + 2 * R, NT = 256;
 constexpr int WB = 4;  // outputs per thread along a pass
 constexpr int NTAP = 2 * R + 1;
+// Row pitches of the shared arrays, odd in words and in 8-byte pairs: the
+// horizontal pass gives consecutive lanes consecutive rows (same columns),
+// so with an odd pitch every 4-byte access of a warp falls in distinct
+// banks and every 8-byte access takes the minimal two wavefronts.
+constexpr int HXP = HX + 1, TXP = TX + 1;
 
 struct SsimArgs {
   const float* pred;
@@ -52,7 +57,7 @@ __device__ __forceinline__ int job_of_ssim_tile(const sss_frame_plan& P, const S
 // once; pixels outside the image are zero-filled by the copy): warp w takes
 // rows w, w + 8, ..., its lanes the columns.  The caller waits
 // (stage_wait) and synchronises the CTA.
-__device__ __forceinline__ void stage(float (*s)[HX], const float* plane, int W, int H, int x0, int y0) {
+__device__ __forceinline__ void stage(float (*s)[HXP], const float* plane, int W, int H, int x0, int y0) {
   const int lane = threadIdx.x & 31;
   for (int r = threadIdx.x >> 5; r < HY; r += NT / 32) {
     const int gy = y0 - R + r;
@@ -72,7 +77,7 @@ __device__ __forceinline__ void stage(float (*s)[HX], const float* plane, int W,
 // Two planes interleaved: s[r][q] = (plane a, plane b) at the same pixel, so
 // that a pixel's pair loads as one 64-bit word (the operand of the packed
 // FP32 instructions).
-__device__ __forceinline__ void stage2(float2 (*s)[HX], const float* pa, const float* pb, int W, int H, int x0,
+__device__ __forceinline__ void stage2(float2 (*s)[HXP], const float* pa, const float* pb, int W, int H, int x0,
                                        int y0) {
   const int lane = threadIdx.x & 31;
   for (int r = threadIdx.x >> 5; r < HY; r += NT / 32) {
@@ -106,9 +111,9 @@ __device__ __forceinline__ void stage_wait() {
 }
 
 __global__ void __launch_bounds__(NT) k_ssim_value(const sss_frame_plan P, const SsimArgs A) {
-  __shared__ float2 s_xy[HY][HX];             // (x, y) per pixel
-  __shared__ float2 h01[HY][TX], h23[HY][TX];  // horizontal sums (x, y), (x^2, y^2)
-  __shared__ float h4[HY][TX];                 // horizontal sum of x y
+  __shared__ float2 s_xy[HY][HXP];              // (x, y) per pixel
+  __shared__ float2 h01[HY][TXP], h23[HY][TXP];  // horizontal sums (x, y), (x^2, y^2)
+  __shared__ float h4[HY][TXP];                  // horizontal sum of x y
   __shared__ double red[2][NT / 32];
   const uint32_t t = blockIdx.x;
   const int ch = blockIdx.y;
@@ -134,10 +139,11 @@ __global__ void __launch_bounds__(NT) k_ssim_value(const sss_frame_plan P, const
   F2 w2[NTAP];
 #pragma unroll
   for (int k = 0; k < NTAP; ++k) w2[k] = vsplat<F2>(A.w[k]);
-  // horizontal: item = (row, group of WB columns); windowed sums of x, y,
-  // x^2, y^2, xy for WB adjacent columns from WB + 10 staged values
+  // horizontal: item = (row, group of WB columns), rows fastest; windowed
+  // sums of x, y, x^2, y^2, xy for WB adjacent columns from WB + 10 staged
+  // values
   for (int it = threadIdx.x; it < HY * (TX / WB); it += NT) {
-    const int r = it / (TX / WB), q0 = (it - r * (TX / WB)) * WB;
+    const int r = it % HY, q0 = (it / HY) * WB;
     F2 v[WB + 2 * R], v2[WB + 2 * R];
     float vxy[WB + 2 * R];
 #pragma unroll
@@ -252,10 +258,10 @@ __global__ void k_ssim_finish(const SsimArgs A) {
 }
 
 __global__ void __launch_bounds__(NT) k_ssim_grad(const sss_frame_plan P, const SsimArgs A) {
-  __shared__ float2 s_ab[HY][HX];  // maps a and b per pixel
-  __shared__ float s_c[HY][HX];
-  __shared__ float2 h_ab[HY][TX];
-  __shared__ float h_c[HY][TX];
+  __shared__ float2 s_ab[HY][HXP];  // maps a and b per pixel
+  __shared__ float s_c[HY][HXP];
+  __shared__ float2 h_ab[HY][TXP];
+  __shared__ float h_c[HY][TXP];
   const uint32_t t = blockIdx.x;
   const int ch = blockIdx.y;
   const int j = job_of_ssim_tile(P, A, t);
@@ -274,7 +280,7 @@ __global__ void __launch_bounds__(NT) k_ssim_grad(const sss_frame_plan P, const 
 #pragma unroll
   for (int k = 0; k < NTAP; ++k) w2[k] = vsplat<F2>(A.w[k]);
   for (int it = threadIdx.x; it < HY * (TX / WB); it += NT) {
-    const int r = it / (TX / WB), q0 = (it - r * (TX / WB)) * WB;
+    const int r = it % HY, q0 = (it / HY) * WB;  // rows fastest, as in the value pass
     F2 vab[WB + 2 * R];
     float vc[WB + 2 * R];
 #pragma unroll
