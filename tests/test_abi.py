@@ -153,3 +153,26 @@ def test_device_entry_points_reject_null_arguments(lib):
     assert lib.sss_sghmc_step(None, None, None, None, None, None, None, None) == _abi.SSS_ERR_INVALID_ARG
     assert lib.sss_loss_l1(None, None, 0, None, None, None) == _abi.SSS_ERR_INVALID_ARG
     assert lib.sss_loss_l1_grad(None, None, 0, None, None, None) == _abi.SSS_ERR_INVALID_ARG
+    assert lib.sss_sghmc_step_to(None, None, None, None, None, None, None, None, None) == _abi.SSS_ERR_INVALID_ARG
+
+
+def test_sghmc_step_to_rejects_a_mismatched_output_before_any_launch(lib):
+    """The output parameter set must match the input's n and degree (and
+    exist); the checks precede every CUDA call, so no device is needed."""
+    import ctypes
+    p = _abi.sss_params()
+    p.n, p.sh_degree = 1000, 3
+    for f in ("mean", "log_scale", "quat", "nu", "opacity_raw", "sh"):
+        setattr(p, f, 0x1000)  # never dereferenced: the call returns first
+    sp = _abi.sss_step_params()
+    sp.beta1, sp.beta2, sp.eps, sp.C = 0.9, 0.999, 1e-3, 0.5
+    buf = ctypes.c_void_p(0x2000)
+    for n, deg in ((999, 3), (1000, 2)):
+        q = _abi.sss_params()
+        ctypes.pointer(q)[0] = p
+        q.n, q.sh_degree = n, deg
+        rc = lib.sss_sghmc_step_to(ctypes.byref(p), ctypes.byref(q), ctypes.byref(p), buf, buf, buf,
+                                   ctypes.byref(sp), None, None)
+        assert rc == _abi.SSS_ERR_INVALID_ARG, (n, deg)
+    rc = lib.sss_sghmc_step_to(ctypes.byref(p), None, ctypes.byref(p), buf, buf, buf, ctypes.byref(sp), None, None)
+    assert rc == _abi.SSS_ERR_INVALID_ARG
