@@ -15,6 +15,8 @@
 // (component, 0, step_lo, step_hi) under key (seed_lo, seed_hi); the four
 // words give three normals by Box-Muller.
 #include <cmath>
+#include <cstdint>
+#include <initializer_list>
 
 #include "common.cuh"
 
@@ -76,6 +78,28 @@ __device__ __forceinline__ float* param_row(const sss_params& s, int row, size_t
   return s.sh + (row - 9) * n;
 }
 
+// One Adam update (bias-corrected) of parameter pk of row `row`: the
+// regulariser's gradient joins gk first; mk and vk are updated in place and
+// the new parameter is returned.
+__device__ __forceinline__ float adam_update(const StepArgs& a, const StepNow& t, int row, int reg, float lr, float pk,
+                                             float gk, float& mk, float& vk) {
+  if (reg == 1) gk = fmaf(a.reg_s, expf(pk), gk);
+  if (reg == 2) {
+    const float o = tanhf(pk);
+    const float sg = o > 0.0f ? 1.0f : (o < 0.0f ? -1.0f : 0.0f);
+    gk = fmaf(a.reg_o * sg, fmaf(-o, o, 1.0f), gk);
+  }
+  mk = fmaf(a.beta1, mk, (1.0f - a.beta1) * gk);
+  vk = fmaf(a.beta2, vk, (1.0f - a.beta2) * gk * gk);
+  float np = pk - lr * (mk * t.inv_bc1) / (sqrtf(vk * t.inv_bc2) + a.adam_eps);
+  if (row == 7) np = fminf(fmaxf(np, 1.0f), 1e4f);
+  return np;
+}
+
+// VEC: n is a multiple of 4 and every array is 16-byte aligned, so a
+// thread's kPer = 4 components are adjacent and move as one 16-byte load or
+// store per array; otherwise they are strided by the CTA width.
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_adam(const StepArgs a) {
   __shared__ StepNow s_t;
   if (threadIdx.x == 0) s_t = step_now(a);
@@ -91,6 +115,24 @@ __global__ void __launch_bounds__(256) k_adam(const StepArgs a) {
   const int reg = (row < 3 && a.reg_s != 0.0f) ? 1 : ((row == 8 && a.reg_o != 0.0f) ? 2 : 0);
   float* m = a.m + row * n;
   float* v = a.v + row * n;
+  if (VEC) {
+    static_assert(kPer == 4, "one float4 per thread and array");
+    const size_t i = ((size_t)blockIdx.x * 256 + threadIdx.x) * 4;
+    if (i >= n) return;
+    const float4 gg = __ldg(reinterpret_cast<const float4*>(g + i));
+    const float4 pp = *reinterpret_cast<const float4*>(p + i);
+    float4 mo = *reinterpret_cast<const float4*>(m + i);
+    float4 vo = *reinterpret_cast<const float4*>(v + i);
+    float4 np;
+    np.x = adam_update(a, t, row, reg, lr, pp.x, gg.x, mo.x, vo.x);
+    np.y = adam_update(a, t, row, reg, lr, pp.y, gg.y, mo.y, vo.y);
+    np.z = adam_update(a, t, row, reg, lr, pp.z, gg.z, mo.z, vo.z);
+    np.w = adam_update(a, t, row, reg, lr, pp.w, gg.w, mo.w, vo.w);
+    *reinterpret_cast<float4*>(m + i) = mo;
+    *reinterpret_cast<float4*>(v + i) = vo;
+    *reinterpret_cast<float4*>(p_out + i) = np;
+    return;
+  }
   const size_t base = (size_t)blockIdx.x * (256 * kPer) + threadIdx.x;
   float pp[kPer], gg[kPer], mo[kPer], vo[kPer];
 #pragma unroll
@@ -107,19 +149,9 @@ __global__ void __launch_bounds__(256) k_adam(const StepArgs a) {
   for (int k = 0; k < kPer; ++k) {
     const size_t i = base + 256 * k;
     if (i >= n) continue;
-    float gk = gg[k];
-    if (reg == 1) gk = fmaf(a.reg_s, expf(pp[k]), gk);
-    if (reg == 2) {
-      const float o = tanhf(pp[k]);
-      const float sg = o > 0.0f ? 1.0f : (o < 0.0f ? -1.0f : 0.0f);
-      gk = fmaf(a.reg_o * sg, fmaf(-o, o, 1.0f), gk);
-    }
-    const float mm = fmaf(a.beta1, mo[k], (1.0f - a.beta1) * gk);
-    const float vv = fmaf(a.beta2, vo[k], (1.0f - a.beta2) * gk * gk);
-    m[i] = mm;
-    v[i] = vv;
-    float np = pp[k] - lr * (mm * t.inv_bc1) / (sqrtf(vv * t.inv_bc2) + a.adam_eps);
-    if (row == 7) np = fminf(fmaxf(np, 1.0f), 1e4f);
+    const float np = adam_update(a, t, row, reg, lr, pp[k], gg[k], mo[k], vo[k]);
+    m[i] = mo[k];
+    v[i] = vo[k];
     p_out[i] = np;
   }
 }
@@ -248,7 +280,17 @@ extern "C" int sss_sghmc_step_to(const sss_params* params, const sss_params* par
   // opacity, quaternion and scale, which the Adam rows then update
   sss::k_sghmc<<<sss::ceil_div((size_t)params->n, 256), 256, 0, (cudaStream_t)stream>>>(a);
   const int rows = 9 + 3 * (params->sh_degree + 1) * (params->sh_degree + 1);
-  sss::k_adam<<<dim3(sss::ceil_div((size_t)params->n, 256 * sss::kPer), rows), 256, 0, (cudaStream_t)stream>>>(a);
+  // 16-byte rows: n a multiple of 4 (each row then starts 16-byte aligned
+  // within its array) and every array 16-byte aligned
+  bool vec = params->n % 4 == 0 && (reinterpret_cast<uintptr_t>(adam_m) | reinterpret_cast<uintptr_t>(adam_v)) % 16 == 0;
+  for (const sss_params* s : {params, params_out, grads})
+    for (const float* f : {s->log_scale, s->quat, s->nu, s->opacity_raw, s->sh})
+      vec = vec && reinterpret_cast<uintptr_t>(f) % 16 == 0;
+  const dim3 grid(sss::ceil_div((size_t)params->n, 256 * sss::kPer), rows);
+  if (vec)
+    sss::k_adam<true><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+  else
+    sss::k_adam<false><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
   SSS_LAUNCH_CHECK();
   if (sp->step_counter) {
     sss::k_step_advance<<<1, 1, 0, (cudaStream_t)stream>>>(sp->step_counter);
