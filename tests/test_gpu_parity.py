@@ -413,9 +413,12 @@ def test_backward_edge_cases_large_nu_and_clamp(tile):
 
 # ---------------------------------------------------------------- a7 step
 
-@pytest.mark.parametrize("burn_in,step", [(False, 0), (True, 3), (False, (1 << 32) + 5)])
-def test_sghmc_step_against_oracle(burn_in, step):
-    scene = inputs.scene_sphere_shell(3000, seed=9)
+@pytest.mark.parametrize("burn_in,step,n_comp", [(False, 0, 3000), (True, 3, 3000), (False, (1 << 32) + 5, 3000),
+                                                  (False, 2, 2999), (True, 1, 2999)])
+def test_sghmc_step_against_oracle(burn_in, step, n_comp):
+    """n_comp = 2999 (not a multiple of 4) takes the Adam rows' strided
+    path, 3000 their 16-byte path."""
+    scene = inputs.scene_sphere_shell(n_comp, seed=9)
     n = scene["n"]
     rng = np.random.default_rng(10)
     sc = frame.Scene.from_numpy(scene, DEV)
@@ -454,12 +457,12 @@ def test_sghmc_step_against_oracle(burn_in, step):
     assert np.allclose(st.v.cpu().numpy().reshape(-1), vv[3 * n:], rtol=1e-5, atol=1e-7)
 
 
-@pytest.mark.parametrize("burn_in", [False, True])
-def test_sghmc_step_to_matches_the_step_in_place(burn_in):
+@pytest.mark.parametrize("burn_in,n_comp", [(False, 5000), (True, 5000), (False, 4999)])
+def test_sghmc_step_to_matches_the_step_in_place(burn_in, n_comp):
     """sss_sghmc_step_to writes bit for bit the parameters the in-place step
     leaves (regularisers on), updates momentum and moments identically, and
-    leaves its input parameters as they were."""
-    scene = inputs.scene_sphere_shell(5000, seed=11)
+    leaves its input parameters as they were (both Adam row paths)."""
+    scene = inputs.scene_sphere_shell(n_comp, seed=11)
     rng = np.random.default_rng(12)
     a, b, orig = (frame.Scene.from_numpy(scene, DEV) for _ in range(3))
     grads = a.zeros_like()
