@@ -2,7 +2,8 @@
 // sigmoidUpdate, SM Eq. SGHMC).  Two launches: k_sghmc updates the means
 // (one thread per component: the noise, the gate and the momentum), k_adam
 // every other parameter row (a 2D grid of (row, block of 1024 components),
-// four components per thread with their loads in flight).  Pure streaming:
+// four components per thread with their loads in flight, as 16-byte
+// accesses where the layout allows).  Pure streaming:
 // per component at SH degree 3 they read parameters, gradients and moments
 // and write parameters and moments back (about 1.6 KB), so they run at HBM
 // speed.  The updated parameters go to a second set of arrays, which may be
