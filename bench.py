@@ -613,15 +613,25 @@ def run_reference(args):
     from paper_2503_10148_gb300 import inputs
     oracle.build.build()
     scene_np, cams = inputs.clusters_1p5m_4views()
-    n_pix = 32
-    for w in range(max(args.warmup, 3)):
-        _oracle_sample(scene_np, cams, n_pix, seed=1000 + w)
+    warmup = max(args.warmup, 3)
+    # each step a bounded sample: as many pixels per view as fit in
+    # min(6 s, 150 s / (steps + warm-up)) beside the fixed projection of every
+    # (view, component) pair, from two pilot samples that count as warm-up
+    step_s = max(1.0, min(6.0, 150.0 / (args.steps + warmup)))
+    t8 = _oracle_sample(scene_np, cams, 8, seed=1000)
+    t40 = _oracle_sample(scene_np, cams, 40, seed=1001)
+    per_px = max((t40 - t8) / 32.0, 1e-5)
+    fixed = max(t8 - 8 * per_px, 0.0)
+    n_pix = int(max(32, min(20000, (step_s - fixed) / per_px)))
+    for w in range(warmup - 2):
+        _oracle_sample(scene_np, cams, n_pix, seed=1002 + w)
     times = [_oracle_sample(scene_np, cams, n_pix, seed=2000 + k) for k in range(args.steps)]
     total = sum(times)
     px = n_pix * len(cams) * args.steps
     value = px / total / 1e6
     sample = (f"each step: FP64 oracle fwd+bwd of {n_pix} seeded pixels per view x {len(cams)} views of the "
-              f"1.5M-component workload, projection of all (view, component) pairs included")
+              f"1.5M-component workload, projection of all (view, component) pairs included (pixels per view "
+              f"sized from two pilots to about {step_s:.1f} s per step)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 8), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(total / args.steps * 1e3, 1),
