@@ -93,3 +93,19 @@ def test_generators_are_deterministic_under_a_seed(gen):
     for f in ("mean", "log_scale", "quat", "nu", "opacity_raw", "sh"):
         assert np.array_equal(a[f], b[f]), f
     assert not np.array_equal(a["mean"], c["mean"])
+
+
+def test_cameras_look_at_the_target_with_a_50_degree_horizontal_fov():
+    cams = inputs.sphere_cameras(6, width=1297, height=840)
+    for c in cams:
+        V = np.asarray(c.viewmat, dtype=np.float64).reshape(3, 4)
+        R, t = V[:, :3], V[:, 3]
+        assert np.allclose(R @ R.T, np.eye(3), atol=1e-12) and np.linalg.det(R) > 0
+        centre = -R.T @ t
+        assert abs(np.linalg.norm(centre) - 3.0) < 1e-9  # on the radius-3 sphere
+        p = R @ np.zeros(3) + t  # the origin, in camera coordinates
+        assert p[2] > 0 and abs(p[0]) < 1e-9 and abs(p[1]) < 1e-9  # straight ahead
+        assert c.fx == c.fy and abs(2 * math.degrees(math.atan(c.width / (2 * c.fx))) - 50.0) < 1e-9
+        assert (c.cx, c.cy) == (c.width / 2, c.height / 2)
+    d = inputs.fibonacci_directions(64)
+    assert np.allclose(np.linalg.norm(d, axis=1), 1.0) and np.linalg.norm(d.mean(0)) < 0.05
