@@ -304,7 +304,8 @@ def kernels_per_step(plan, form: str = "autograd", loss: str = "full") -> int:
         loss_k = 3  # SSIM value, finish, gradient
     else:
         loss_k = 2 if form == "autograd" else 1  # value, then the gradient in the backward
-    return 1 + bin_k + sort_k + 1 + loss_k + 1 + 1 + 2
+    sampler_k = 3  # SGHMC, Adam rows, and the advance of the device step counter
+    return 1 + bin_k + sort_k + 1 + loss_k + 1 + 1 + sampler_k
 
 
 def run_ours(args):

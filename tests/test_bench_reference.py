@@ -76,3 +76,18 @@ def test_reference_arm_prints_only_on_rank_0(stand_in, monkeypatch, capsys):
     bench.run_reference(types.SimpleNamespace(steps=2, warmup=3, workload="clusters_1p5m_4views"))
     assert capsys.readouterr().out == ""
     assert stand_in == []  # no oracle work on the other ranks
+
+
+def test_kernels_per_step_counts_every_launch_of_the_timed_step():
+    """35 launches per step on the 1.5M-component workload (588 list tiles:
+    10 tile bits, two radix passes), as the launch list of the captured step
+    shows: project; depth sort (init, 4 x (histogram, scan, scatter)),
+    pair count, scan, finish, emission; tile sort (2 x 3, range init and
+    fix-up); render_fwd; SSIM value, finish, gradient; render_bwd;
+    project_bwd; SGHMC, Adam rows, step-counter advance."""
+    plan = types.SimpleNamespace(tile_bits=10)
+    assert bench.kernels_per_step(plan, "autograd", "full") == 35
+    assert bench.kernels_per_step(types.SimpleNamespace(tile_bits=13), "autograd", "full") == 35
+    assert bench.kernels_per_step(types.SimpleNamespace(tile_bits=17), "autograd", "full") == 38  # 3 passes
+    assert bench.kernels_per_step(plan, "autograd", "l1") == 34
+    assert bench.kernels_per_step(plan, "direct", "l1") == 33
