@@ -295,6 +295,31 @@ def test_single_component_closed_form(nu, o):
     assert ly.min() >= rec[oracle.P["py0"]] and ly.max() <= rec[oracle.P["py1"]]
     # at h = h_max the alpha threshold is met exactly
     assert abs(o) * oracle.t2d(rec[oracle.P["hmax"]], nu) == pytest.approx(TAU, rel=1e-12)
+    # and the pixel box is the tight one: the pixel centres between the
+    # extreme x and y of the ellipse h = h_max, found here by sampling its
+    # boundary d = sqrt(h_max) L (cos t, sin t) with L L^T = Sigma2D
+    Lc = np.linalg.cholesky(S)
+    t = np.linspace(0.0, 2.0 * math.pi, 200_001)
+    d = math.sqrt(rec[oracle.P["hmax"]]) * (Lc @ np.stack([np.cos(t), np.sin(t)]))
+    ex, ey = d[0].max(), d[1].max()
+    assert rec[oracle.P["px0"]] == max(math.ceil(m2[0] - ex - 0.5), 0)
+    assert rec[oracle.P["px1"]] == min(math.floor(m2[0] + ex - 0.5), cam.width - 1)
+    assert rec[oracle.P["py0"]] == max(math.ceil(m2[1] - ey - 0.5), 0)
+    assert rec[oracle.P["py1"]] == min(math.floor(m2[1] + ey - 0.5), cam.height - 1)
+
+
+def test_projection_limits_nu_to_the_paper_range():
+    """SM Implementation Details: nu is kept in [1, 1e4].  The projected nu is
+    the limited one, and a component beyond the limit renders exactly as one
+    at the limit."""
+    cam = inputs.look_at((0.0, 0.0, 3.0), width=64, height=48)
+    nus = [0.25, 1.0, 7.5, 9999.0, 1e4, 3e5]
+    recs = [oracle.project(_one_component([0.02, 0.01, 0.0], [-1.9, -2.1, -2.0], [0.9, 0.2, -0.1, 0.3], nu, 0.7,
+                                          rgb=[0.6, 0.3, 0.2]), cam)[0] for nu in nus]
+    assert [r[oracle.P["nu"]] for r in recs] == [1.0, 1.0, 7.5, 9999.0, 1e4, 1e4]
+    img = [oracle.render(r[None], cam, _cfg())["rgb"] for r in recs]
+    assert np.array_equal(img[0], img[1]) and np.array_equal(img[4], img[5])
+    assert not np.array_equal(img[3], img[4])
 
 
 # ---------------------------------------------------------------------------
@@ -588,6 +613,76 @@ def test_burn_in_noise_scales_with_covariance():
     s2 = math.exp(-2.6)
     expect = theta[:3 * n] - p["eps"] ** 2 * grad[:3 * n] + gate * p["eps"] * math.sqrt(2 * p["eps"] * p["C"]) * s2 * xi.reshape(-1)
     assert np.allclose(th[:3 * n], expect, rtol=1e-12, atol=1e-15)
+
+
+def test_burn_in_noise_is_anisotropic_covariance_times_xi():
+    """Burn-in with a rotated, anisotropic Sigma = R diag(e^{2s}) R^T (Sec. 3.4:
+    the noise is multiplied by Sigma during burn-in).  Sigma is built here from
+    scipy's rotation of each quaternion (scalar-last order) and distinct
+    log-scales per axis, so a transposed rotation (R^T D R) or a swapped axis
+    in the oracle fails.  The momentum update keeps its friction term."""
+    n = 40
+    sc, theta, grad, r, m, v = _step_setup(n=n, seed=11)
+    sl = oracle.theta_slices(n, 0)
+    rng = np.random.default_rng(17)
+    q = rng.normal(size=(4, n))
+    q[0] += 0.3  # away from the identity, both signs of w present
+    theta[sl["quat"]] = q.reshape(-1)
+    ls = np.stack([np.full(n, -0.4), np.full(n, -1.1), np.full(n, -2.0)]) + rng.uniform(-0.2, 0.2, (3, n))
+    theta[sl["log_scale"]] = ls.reshape(-1)
+    o = rng.uniform(-0.02, 0.02, n)
+    theta[sl["opacity_raw"]] = np.arctanh(o)
+    p = dict(eps=0.03, C=0.6, k=100.0, t0=0.005)
+    th, rr, _, _, xi = oracle.sghmc_step(theta, grad, r, m, v, n=n, sh_degree=0, params=p, burn_in=True,
+                                        seed=21, step=6)
+    rot = Rotation.from_quat(np.stack([q[1], q[2], q[3], q[0]], axis=1)).as_matrix()  # [n][3][3]
+    D = np.exp(2.0 * ls).T  # [n][3]
+    Sigma = np.einsum("nij,nj,nkj->nik", rot, D, rot)
+    noise = np.einsum("nij,jn->in", Sigma, xi)  # [3][n]
+    gate = 1.0 / (1.0 + np.exp(p["k"] * (np.abs(o) - p["t0"])))
+    sq = math.sqrt(2.0 * p["eps"] * p["C"])
+    G = grad[:3 * n].reshape(3, n)
+    mu0 = theta[:3 * n].reshape(3, n)
+    expect_mu = mu0 - p["eps"] ** 2 * G + gate * p["eps"] * sq * noise
+    assert np.allclose(th[:3 * n].reshape(3, n), expect_mu, rtol=1e-12, atol=1e-15)
+    expect_r = (1.0 - p["eps"] * p["C"]) * r.reshape(3, n) - p["eps"] * G + sq * xi
+    assert np.allclose(rr.reshape(3, n), expect_r, rtol=1e-12, atol=1e-15)
+    # the rotation matters: with R^T D R the displacement would differ
+    wrong = np.einsum("nji,nj,njk->nik", rot, D, rot)
+    assert np.max(np.abs(np.einsum("nij,jn->in", wrong, xi) - noise)) > 1e-3
+
+
+def test_adam_two_steps_from_nonzero_moments_follow_the_recurrence():
+    """Two consecutive steps from non-zero first and second moments (Adam,
+    Kingma & Ba 2015, on every group but the means): the recurrence written
+    out here, with the bias corrections of steps t = s + 1 and s + 2.  The
+    moments differ from each other and from zero, so an update that mixes m
+    and v, drops a bias correction or uses the wrong step fails."""
+    n = 60
+    sc, theta, grad, r, _, _ = _step_setup(n=n, seed=13)
+    rng = np.random.default_rng(29)
+    m0 = rng.normal(size=theta.shape) * 0.3
+    v0 = rng.uniform(0.05, 2.0, size=theta.shape)
+    grad2 = rng.normal(size=theta.shape)
+    lr = (1e-2, 2e-3, 5e-2, 3e-2, 4e-3)
+    b1, b2, eps_a = 0.85, 0.995, 1e-6
+    p = dict(lr=lr, beta1=b1, beta2=b2, adam_eps=eps_a)
+    s = 4
+    th1, r1, m1, v1, _ = oracle.sghmc_step(theta, grad, r, m0, v0, n=n, sh_degree=0, params=p, seed=2, step=s)
+    th2, _, m2, v2, _ = oracle.sghmc_step(th1, grad2, r1, m1, v1, n=n, sh_degree=0, params=p, seed=2, step=s + 1)
+    sl = oracle.theta_slices(n, 0)
+    for name, l in zip(("log_scale", "quat", "nu", "opacity_raw", "sh"), lr):
+        j = sl[name]
+        pp, mm, vv = theta[j].copy(), m0[j].copy(), v0[j].copy()
+        for t, g in ((s + 1, grad[j]), (s + 2, grad2[j])):
+            mm = b1 * mm + (1.0 - b1) * g
+            vv = b2 * vv + (1.0 - b2) * g * g
+            pp = pp - l * (mm / (1.0 - b1 ** t)) / (np.sqrt(vv / (1.0 - b2 ** t)) + eps_a)
+            if name == "nu":
+                pp = np.clip(pp, 1.0, 1e4)
+        assert np.allclose(m2[j], mm, rtol=1e-13, atol=0)
+        assert np.allclose(v2[j], vv, rtol=1e-13, atol=0)
+        assert np.allclose(th2[j], pp, rtol=1e-12, atol=1e-15)
 
 
 def test_adam_first_step_moves_by_learning_rate():
