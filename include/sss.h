@@ -314,6 +314,10 @@ typedef struct sss_step_params {
                              of dL/dmu (Implementation Details: the Adam
                              gradient in SGHMC) and the moments are updated */
   float* mu_adam_v;
+  uint32_t* philox_out;   /* optional device uint32[4][n] (NULL to skip):
+                             the four Philox4x32-10 words each component's
+                             normals were drawn from (row w = word w), so a
+                             caller can check the generator bit for bit */
 } sss_step_params;
 
 int sss_sghmc_step(const sss_params* params, const sss_params* grads, float* momentum, float* adam_m,
@@ -421,26 +425,31 @@ int sss_relocate(const sss_params* params, float* momentum, float* adam_m, float
 /* -------------------------------------------- no-allocation forward */
 /* No counterpart in the paper.  A forward render of one small frame for
  * callers that cannot allocate device memory when they render: a plug-in in
- * a host application that owns all device memory through its own pool, code
- * running while a stream is being captured (cudaMalloc is not allowed then),
- * or a real-time thread that must not wait on the allocator.  The whole
- * workspace lives in one file-scope __device__ array of
+ * a host application that owns all device memory through its own pool or
+ * budget, or a real-time render thread that must not take the allocator's
+ * locks or wait for the device synchronisation cudaMalloc can imply.  The
+ * whole workspace lives in one file-scope __device__ array of
  * SSS_STATIC_ARENA_BYTES in the library, so the caller passes only the scene,
  * the camera, the options and the output image.
  *   scene    device parameters of one scene, n <= SSS_STATIC_MAX_COMPONENTS
  *   cam      width * height <= SSS_STATIC_MAX_PIXELS
  *   out_rgb  device float[3][height][width]
  * Same computation as sss_project + sss_bin + sss_sort + sss_render_fwd on a
- * one-job frame.  Allocates nothing (no cudaMalloc, cudaFree or allocating
- * library call).  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current) and caches it;
- * make that first call before any stream capture.  Every call on a device
- * shares the one array and leaves its contents behind: calls whose work
+ * one-job frame, bit for bit.  Allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library call).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current) and caches
+ * it for the life of the process; a cudaDeviceReset of that device
+ * invalidates the cached address, so calls after one are not supported.
+ * Every call on a device shares the one array and leaves its contents
+ * behind (the kernels reset what must start at zero): calls whose work
  * overlaps on the GPU (other streams or host threads) race, so serialise
- * them.  The call synchronises `stream` before it returns, to report an
- * overflow.  Errors: SSS_ERR_INVALID_ARG (null pointer, size beyond the
- * limits, bad options), SSS_ERR_CAPACITY (the frame's workspace or its tile
- * pairs do not fit the array), SSS_ERR_CUDA. */
+ * them.  The call enqueues its kernels on `stream` and then synchronises
+ * `stream` (a blocking wait) to read the overflow status before it returns.
+ * Errors: SSS_ERR_INVALID_ARG (null pointer, size beyond the limits, bad
+ * options; nothing enqueued), SSS_ERR_CAPACITY (the frame's workspace does
+ * not fit the array, nothing enqueued; or its tile pairs overflowed the rest
+ * of the array, in which case out_rgb holds an incomplete image),
+ * SSS_ERR_CUDA. */
 #define SSS_STATIC_ARENA_BYTES (32u << 20)
 #define SSS_STATIC_MAX_COMPONENTS 65536
 #define SSS_STATIC_MAX_PIXELS (1024 * 1024)

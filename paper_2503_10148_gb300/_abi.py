@@ -64,7 +64,8 @@ class sss_step_params(Structure):
     _fields_ = [("eps", c_float), ("C", c_float), ("k", c_float), ("t0", c_float), ("burn_in", c_int32),
                 ("seed", c_uint64), ("step", c_uint64), ("lr", c_float * 5), ("beta1", c_float),
                 ("beta2", c_float), ("adam_eps", c_float), ("step_counter", c_void_p), ("reg_opacity", c_float),
-                ("reg_scale", c_float), ("mu_adam_m", c_void_p), ("mu_adam_v", c_void_p)]
+                ("reg_scale", c_float), ("mu_adam_m", c_void_p), ("mu_adam_v", c_void_p),
+                ("philox_out", c_void_p)]
 
 
 class sss_relocate_params(Structure):

@@ -10,9 +10,24 @@
 
 namespace sss {
 
-constexpr int kNumSMs = 152;          // GB300: 2 dies x 76 SMs
+constexpr int kNumSMs = 152;          // GB300: 2 dies x 76 SMs; the SM count
+                                      // when no device can be queried
 constexpr float kFastNuMax = 64.0f;   // above this nu the log/exp pair runs on
                                       // the accurate path (eval_pair_slow)
+
+// SM count of the current device (cudaDevAttrMultiProcessorCount), or kNumSMs
+// when no device is visible (host-only planning).  Sizes the persistent grids
+// of the sorts and scans and the grid-stride launches.  A host-side attribute
+// query: it enqueues nothing and is allowed while a stream is being captured.
+inline int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    (void)cudaGetLastError();
+    return kNumSMs;
+  }
+  return sms;
+}
 
 // ------------------------------------------------------------ workspace
 template <typename T>

@@ -73,7 +73,7 @@ extern "C" int sss_loss_l1(const float* pred, const float* target, uint32_t coun
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemsetAsync(loss_out, 0, sizeof(float), st) != cudaSuccess) return SSS_ERR_CUDA;
   if (count == 0) return SSS_OK;
-  const unsigned blocks = std::min<unsigned>(sss::ceil_div(count, 256), 8 * sss::kNumSMs);
+  const unsigned blocks = std::min<unsigned>(sss::ceil_div(count, 256), 8u * (unsigned)sss::device_sm_count());
   sss::k_loss_l1<<<blocks, 256, 0, st>>>(pred, target, count, 1.0f / (float)count, dL_dpred, loss_out);
   SSS_LAUNCH_CHECK();
   return SSS_OK;
@@ -83,7 +83,7 @@ extern "C" int sss_loss_l1_grad(const float* pred, const float* target, uint32_t
                                 float* dL_dpred, sss_stream_t stream) {
   if (!pred || !target || !dL_dpred) return SSS_ERR_INVALID_ARG;
   if (count == 0) return SSS_OK;
-  const unsigned blocks = std::min<unsigned>(sss::ceil_div(count, 256), 8 * sss::kNumSMs);
+  const unsigned blocks = std::min<unsigned>(sss::ceil_div(count, 256), 8u * (unsigned)sss::device_sm_count());
   sss::k_loss_l1_grad<<<blocks, 256, 0, (cudaStream_t)stream>>>(pred, target, count, 1.0f / (float)count, dL_dloss,
                                                                dL_dpred);
   SSS_LAUNCH_CHECK();
@@ -98,7 +98,7 @@ extern "C" int sss_regularizers(const sss_params* params, float reg_opacity, flo
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemsetAsync(loss_out, 0, sizeof(float), st) != cudaSuccess) return SSS_ERR_CUDA;
   if (params->n == 0) return SSS_OK;
-  const unsigned blocks = std::min<unsigned>(sss::ceil_div((size_t)params->n, 256), 8 * sss::kNumSMs);
+  const unsigned blocks = std::min<unsigned>(sss::ceil_div((size_t)params->n, 256), 8u * (unsigned)sss::device_sm_count());
   sss::k_regularizers<<<blocks, 256, 0, st>>>(params->opacity_raw, params->log_scale, (uint32_t)params->n,
                                               reg_opacity, reg_scale, loss_out);
   SSS_LAUNCH_CHECK();

@@ -112,7 +112,7 @@ int sss_plan_frame(const sss_params* scenes, int n_scenes, const sss_camera* cam
   }
   plan->scene_job_begin[n_scenes] = k;
 
-  plan->sort_blocks = 3 * sss::kNumSMs;  // resident CTAs of the radix scatter
+  plan->sort_blocks = 3 * sss::device_sm_count();  // resident CTAs of the radix scatter
   int passes = (bits + 7) / 8;
   plan->pair_slot = (uint32_t)(passes & 1);
 

@@ -43,7 +43,7 @@ RelocLayout layout(int32_t n, float max_fraction) {
   const double c = std::floor((double)max_fraction * (double)n);
   L.cap = (uint32_t)(c < 0.0 ? 0.0 : (c > (double)n ? (double)n : c));
   L.nb = (uint32_t)((n + RT - 1) / RT);
-  L.sort_blocks = 3 * kNumSMs;
+  L.sort_blocks = 3 * device_sm_count();
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;

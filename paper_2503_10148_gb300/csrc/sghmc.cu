@@ -41,6 +41,7 @@ struct StepArgs {
   float reg_o, reg_s;  // regulariser weights of the loss
   float* mu_m;         // optional Adam moments of dL/dmu (Adam gradient in SGHMC)
   float* mu_v;
+  uint32_t* philox_out;  // optional [4][n]: the raw Philox words of the noise
   float ln_beta1, ln_beta2;
 };
 
@@ -164,6 +165,12 @@ __device__ __forceinline__ void step_component(const StepArgs& a, uint32_t i, co
   const float gate = 1.0f / (1.0f + expf(a.k * (fabsf(o) - a.t0)));
   // three standard normals
   const uint4 w = philox4x32_10(make_uint4(i, 0u, t.lo, t.hi), a.seed_lo, a.seed_hi);
+  if (a.philox_out) {
+    a.philox_out[i] = w.x;
+    a.philox_out[n + i] = w.y;
+    a.philox_out[2 * n + i] = w.z;
+    a.philox_out[3 * n + i] = w.w;
+  }
   const float s24 = 1.0f / 16777216.0f;
   const float u1 = (float)((w.x >> 8) + 1u) * s24, u2 = (float)(w.y >> 8) * s24;
   const float u3 = (float)((w.z >> 8) + 1u) * s24, u4 = (float)(w.w >> 8) * s24;
@@ -275,6 +282,7 @@ extern "C" int sss_sghmc_step_to(const sss_params* params, const sss_params* par
   if ((sp->mu_adam_m == nullptr) != (sp->mu_adam_v == nullptr)) return SSS_ERR_INVALID_ARG;
   a.mu_m = sp->mu_adam_m;
   a.mu_v = sp->mu_adam_v;
+  a.philox_out = sp->philox_out;
   a.ln_beta1 = (float)std::log((double)sp->beta1);
   a.ln_beta2 = (float)std::log((double)sp->beta2);
   // the means first: the gate and the burn-in covariance read the pre-step

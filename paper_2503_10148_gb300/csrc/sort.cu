@@ -547,7 +547,7 @@ extern "C" int sss_sort(const sss_frame_plan* plan, void* ws, sss_stream_t strea
     if (cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)P.n_tiles, st) != cudaSuccess) return SSS_ERR_CUDA;
     return SSS_OK;
   }
-  const unsigned rgrid = min(ceil_div(P.n_tiles, 256), 4u * kNumSMs);
+  const unsigned rgrid = min(ceil_div(P.n_tiles, 256), 4u * (unsigned)device_sm_count());
   k_ranges_init<<<rgrid, 256, 0, st>>>(ranges, P.n_tiles);
   uint32_t* pkey = ws_ptr<uint32_t>(ws, P.ws_off_pkey);
   uint32_t* pval = ws_ptr<uint32_t>(ws, P.ws_off_pval);

@@ -2,18 +2,19 @@
 //
 // Some callers cannot allocate device memory at the time they need a frame:
 // a plug-in inside a host application that owns every device byte through
-// its own pool or budget, code running while a stream is being captured into
-// a CUDA graph (cudaMalloc is not allowed there), or a real-time thread that
-// must not take the allocator's locks or wait for the implicit device
-// synchronisation of cudaMalloc.  For them this entry point keeps the whole
-// workspace in one file-scope __device__ array of fixed size, so a frame needs
-// nothing but the caller's parameters and output image.
+// its own pool or budget, or a real-time thread that must not take the
+// allocator's locks or wait for the device synchronisation cudaMalloc can
+// imply.  For them this entry point keeps the whole workspace in one
+// file-scope __device__ array of fixed size, so a frame needs nothing but the
+// caller's parameters and output image.  The call synchronises its stream
+// before it returns (it reads the pair-overflow status).
 //
 // It runs the existing hot-path entry points (sss_project, sss_bin, sss_sort,
 // sss_render_fwd) on that array.  In host code `g_static_arena` names only a
 // host-side stand-in for the device array, so its device address is fetched
 // with cudaGetSymbolAddress once per device (with that device current) and
-// cached.
+// cached for the life of the process (a cudaDeviceReset of that device would
+// leave the cached address stale; calls after one are not supported).
 #include <cuda_runtime.h>
 
 #include <mutex>

@@ -274,13 +274,15 @@ class Frame:
 def step_params(eps=1e-3, C=0.5, k=100.0, t0=0.005, burn_in=False, seed=0, step=0,
                 lr=(5e-3, 1e-3, 1e-2, 5e-2, 2.5e-3), beta1=0.9, beta2=0.999, adam_eps=1e-15,
                 step_counter: torch.Tensor | None = None, reg_opacity=0.0, reg_scale=0.0,
-                mu_adam: tuple | None = None) -> abi.sss_step_params:
+                mu_adam: tuple | None = None, philox_out: torch.Tensor | None = None) -> abi.sss_step_params:
     """Sampler options.  With ``step_counter`` (a 1-element int64 device
     tensor) the step index is read from and advanced on the device, so a
     CUDA-graph replay of the step draws fresh noise.  ``reg_opacity`` and
     ``reg_scale`` are the loss's regulariser weights, whose gradients the
     step adds.  ``mu_adam`` = (m, v), two float32 [3][n] device tensors:
-    the SGHMC gradient becomes Adam's normalised gradient of dL/dmu."""
+    the SGHMC gradient becomes Adam's normalised gradient of dL/dmu.
+    ``philox_out``, an int32 or uint32 [4][n] device tensor, receives the
+    Philox words the noise of each component was drawn from."""
     sp = abi.sss_step_params()
     if step_counter is not None:
         assert step_counter.dtype == torch.int64 and step_counter.numel() == 1
@@ -294,6 +296,9 @@ def step_params(eps=1e-3, C=0.5, k=100.0, t0=0.005, burn_in=False, seed=0, step=
     sp.reg_opacity, sp.reg_scale = float(reg_opacity), float(reg_scale)
     if mu_adam is not None:
         sp.mu_adam_m, sp.mu_adam_v = mu_adam[0].data_ptr(), mu_adam[1].data_ptr()
+    if philox_out is not None:
+        assert philox_out.element_size() == 4 and philox_out.is_contiguous()
+        sp.philox_out = philox_out.data_ptr()
     return sp
 
 

@@ -120,3 +120,87 @@ def assert_groups_close(got, ref, n, sh_degree, mag, rel=GRAD_REL, norm=GRAD_NOR
         assert not bad.any(), (label, name, report[name], int(bad.sum()), a[bad][:5], b[bad][:5])
         assert l2 <= norm, (label, name, report[name])
     return report
+
+
+# ---------------------------------------------------------------- sampler step bar
+# An updated value (parameter, momentum, Adam moment) must be within 1e-6 of
+# the oracle's value relative to that value, or -- where the increment's own
+# terms are larger than the value or cancel -- within the FP32 rounding of
+# those terms: |got - ref| <= 1e-6 |ref| + 16 u D, D the sum of the
+# magnitudes of the increment's terms (for Adam, taken on the terms of m').
+# 16 bounds the FP32 roundings along one element's update (tanh, exp and the
+# division of the gate; log, sqrt and sincospi of Box-Muller; expm1 of the bias
+# corrections; the products and sums of the update), each at most an ulp of
+# its operands.  Both sides get the same FP32 hyper-parameters.
+STEP_REL = 1e-6
+STEP_ROUNDINGS = 16.0
+
+
+def f32(x):
+    """The FP32 value the kernel sees for a hyper-parameter (scalar or tuple)."""
+    if isinstance(x, (tuple, list)):
+        return tuple(float(np.float32(v)) for v in x)
+    return float(np.float32(x))
+
+
+def adam_increment_mag(m0, g_mag, v_new, lr, beta1, beta2, adam_eps, t):
+    """lr m^/(sqrt(v^) + eps) with m^ taken on the magnitudes of its terms."""
+    bc1 = 1.0 - beta1 ** t
+    bc2 = 1.0 - beta2 ** t
+    return lr * (beta1 * np.abs(m0) + (1.0 - beta1) * g_mag) / bc1 / (np.sqrt(np.abs(v_new) / bc2) + adam_eps)
+
+
+def _rotations(quat):
+    """[n][3][3] rotation matrices of (w, x, y, z) quaternions [4][n]."""
+    q = np.asarray(quat, np.float64)
+    q = q / np.linalg.norm(q, axis=0, keepdims=True)
+    w, x, y, z = q
+    return np.stack([np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+                     np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+                     np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], 1)
+
+
+def noise_mag(theta0, xi, n, sh_degree, burn_in):
+    """Per mean element, the magnitude of the noise term's factors: |xi| or,
+    in burn-in, sum_k |R_ak| s_k^2 sum_b |R_bk| |xi_b| (Sigma xi evaluated as
+    R (s^2 (R^T xi)))."""
+    xi = np.asarray(xi, np.float64).reshape(3, n)
+    if not burn_in:
+        return np.abs(xi)
+    sl = oracle.theta_slices(n, sh_degree)
+    R = np.abs(_rotations(theta0[sl["quat"]].reshape(4, n)))  # [n][a][k]
+    s2 = np.exp(2.0 * theta0[sl["log_scale"]].reshape(3, n)).T  # [n][k]
+    inner = np.einsum("nbk,bn->nk", R, np.abs(xi)) * s2
+    return np.einsum("nak,nk->an", R, inner)
+
+
+def step_mags(theta0, G_mag, r0, xi, n, sh_degree, p, burn_in):
+    """(mean increment magnitude, momentum increment magnitude), [3][n] each,
+    of mu' = mu - eps^2 G + g eps (1 - eps C) r + g eps sqrt(2 eps C) (xi or
+    Sigma xi) and r' = (1 - eps C) r - eps G + sqrt(2 eps C) xi."""
+    sl = oracle.theta_slices(n, sh_degree)
+    o = np.tanh(theta0[sl["opacity_raw"]])
+    gate = 1.0 / (1.0 + np.exp(np.minimum(p["k"] * (np.abs(o) - p["t0"]), 700.0)))
+    eps, C = p["eps"], p["C"]
+    sq = np.sqrt(2.0 * eps * C)
+    fr = abs(1.0 - eps * C)
+    r0 = np.abs(np.asarray(r0, np.float64).reshape(3, n))
+    G = np.asarray(G_mag, np.float64).reshape(3, n)
+    nm = noise_mag(theta0, xi, n, sh_degree, burn_in)
+    mu = eps * eps * G + gate * eps * sq * nm + (0.0 if burn_in else 1.0) * gate * eps * fr * r0
+    r = fr * r0 + eps * G + sq * np.abs(np.asarray(xi, np.float64).reshape(3, n))
+    return mu, r
+
+
+def assert_step_close(got, ref, mag, label="", rel=STEP_REL):
+    """|got - ref| <= rel |ref| + 16 u mag elementwise; returns the largest
+    ratio of error to bound and the fraction of elements whose bound is set by
+    the rounding term rather than rel |ref|."""
+    got = np.asarray(got, np.float64).reshape(-1)
+    ref = np.asarray(ref, np.float64).reshape(-1)
+    floor = STEP_ROUNDINGS * U32 * np.asarray(mag, np.float64).reshape(-1)
+    bound = rel * np.abs(ref) + floor
+    ratio = np.abs(got - ref) / np.maximum(bound, 1e-300)
+    worst = int(np.argmax(ratio))
+    assert ratio[worst] <= 1.0, (label, float(ratio[worst]), got[worst], ref[worst], float(bound[worst]))
+    return {"max_ratio": round(float(ratio.max()), 4), "floor_frac": round(float(np.mean(floor > rel * np.abs(ref))), 4)}

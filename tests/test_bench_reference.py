@@ -91,3 +91,20 @@ def test_kernels_per_step_counts_every_launch_of_the_timed_step():
     assert bench.kernels_per_step(types.SimpleNamespace(tile_bits=17), "autograd", "full") == 38  # 3 passes
     assert bench.kernels_per_step(plan, "autograd", "l1") == 34
     assert bench.kernels_per_step(plan, "direct", "l1") == 33
+
+
+def test_alu_roofline_follows_the_per_pair_work_and_device_ceiling():
+    """The render roofline: 50 FP32 flops + 2 MUFU per contributing pair for
+    the backward, the FP32 pipe binding (50 / (152 x 128 x 2) > 2 / (152 x
+    16)); at 1.314e9 pairs in 5.684 ms on 152 SMs at 2070 MHz that is 0.143
+    of the ceiling.  The ceiling scales with the SM count it is given."""
+    import bench
+    r = bench.roofline("render_bwd", 5.684, None, (1_313_980_094, 0), {}, "measured", 152, 2070.0)
+    assert r["bound"] == "alu" and r["frac"] == pytest.approx(0.1435, abs=5e-4)
+    assert r["peak"] == pytest.approx(80.548, abs=1e-3)
+    assert r["detailed_count"]["frac"] == pytest.approx(0.2152, abs=5e-4)
+    half = bench.roofline("render_bwd", 5.684, None, (1_313_980_094, 0), {}, "measured", 76, 2070.0)
+    assert half["frac"] == pytest.approx(2 * r["frac"], rel=1e-3)
+    f = bench.roofline("render_fwd", 2.0, None, (1_000_000_000, 2_000_000_000), {}, "measured", 152, 2070.0)
+    # 8 x 2e9 + 12 x 1e9 = 28e9 flops (0.348 ms of FP32) vs 2e9 MUFU (0.397 ms): the MUFU pipe binds
+    assert f["frac"] == pytest.approx(2e9 / (152 * 16 * 2.07e9) / 2e-3, rel=1e-3)

@@ -17,7 +17,8 @@ import torch
 import oracle
 from paper_2503_10148_gb300 import _abi, frame, inputs
 
-from gpu_util import (DEV, GRAD_NORM, GRAD_REL, assert_groups_close, f32_scene, gpu_forward, grad_den,
+from gpu_util import (DEV, GRAD_NORM, GRAD_REL, U32, adam_increment_mag, assert_groups_close, assert_step_close,
+                      f32, f32_scene, gpu_forward, grad_den, step_mags,
                       masked_weights, oracle_views, require_gpu, scene_grads_flat, sh_basis_bound)
 from oracle import Magnitudes
 
@@ -414,9 +415,12 @@ def test_backward_edge_cases_large_nu_and_clamp(tile):
 # ---------------------------------------------------------------- a7 step
 
 @pytest.mark.parametrize("burn_in,step,n_comp", [(False, 0, 3000), (True, 3, 3000), (False, (1 << 32) + 5, 3000),
-                                                  (False, 2, 2999), (True, 1, 2999)])
+                                                  (True, (1 << 33) + 1, 3000), (False, 2, 2999), (True, 1, 2999)])
 def test_sghmc_step_against_oracle(burn_in, step, n_comp):
-    """n_comp = 2999 (not a multiple of 4) takes the Adam rows' strided
+    """The step's Philox words equal the oracle's bit for bit (every
+    component, step indices above 2^32); every updated value is within the
+    sampler bar (1e-6 relative, or the FP32 rounding of the increment's
+    terms).  n_comp = 2999 (not a multiple of 4) takes the Adam rows' strided
     path, 3000 their 16-byte path."""
     scene = inputs.scene_sphere_shell(n_comp, seed=9)
     n = scene["n"]
@@ -434,27 +438,44 @@ def test_sghmc_step_against_oracle(burn_in, step, n_comp):
     theta0 = oracle.theta_from_scene(sc.to_numpy())
     g0 = scene_grads_flat(grads)
     r0 = st.r.cpu().numpy().astype(np.float64).reshape(-1)
-    K = 16
     m0 = st.m.cpu().numpy().astype(np.float64)
     v0 = st.v.cpu().numpy().astype(np.float64)
     # oracle moments use theta's layout: mean rows unused
     mo = np.concatenate([np.zeros(3 * n), m0.reshape(-1)])
     vo = np.concatenate([np.zeros(3 * n), v0.reshape(-1)])
-    params = dict(eps=2e-2, C=0.6, k=100.0, t0=0.005, lr=(5e-3, 1e-3, 1e-2, 5e-2, 2.5e-3), beta1=0.9, beta2=0.999,
-                  adam_eps=1e-8)
+    params = dict(eps=f32(2e-2), C=f32(0.6), k=f32(100.0), t0=f32(0.005), lr=f32((5e-3, 1e-3, 1e-2, 5e-2, 2.5e-3)),
+                  beta1=f32(0.9), beta2=f32(0.999), adam_eps=f32(1e-8))
+    words = torch.zeros(4, n, dtype=torch.int32, device=DEV)
     sp = frame.step_params(eps=params["eps"], C=params["C"], burn_in=burn_in, seed=77, step=step,
-                           lr=params["lr"], adam_eps=params["adam_eps"])
+                           lr=params["lr"], adam_eps=params["adam_eps"], philox_out=words)
     xi = torch.zeros(3, n, dtype=torch.float32, device=DEV)
     frame.sghmc_step(sc, grads, st, sp, xi_out=xi)
     torch.cuda.synchronize()
     th, rr, mm, vv, xir = oracle.sghmc_step(theta0, g0, r0, mo, vo, n=n, sh_degree=3, params=params,
                                              burn_in=burn_in, seed=77, step=step)
-    assert np.abs(xi.cpu().numpy() - xir).max() < 2e-5
+    # the generator, bit for bit: counter (i, 0, step_lo, step_hi), key (seed_lo, seed_hi)
+    got_w = words.cpu().numpy().view(np.uint32)
+    key = (77, 0)
+    want_w = np.stack([oracle.philox4x32_10((i, 0, step & 0xFFFFFFFF, step >> 32), key) for i in range(n)], axis=1)
+    assert np.array_equal(got_w, want_w)
+    # the normals: FP32 Box-Muller of identical uniforms
+    assert np.all(np.abs(xi.cpu().numpy() - xir) <= 8 * U32 * np.maximum(np.abs(xir), 1.0))
     got = oracle.theta_from_scene(sc.to_numpy())
-    assert np.all(np.abs(got - th) <= 2e-6 * np.maximum(np.abs(th), 1.0)), np.abs(got - th).max()
-    assert np.allclose(st.r.cpu().numpy().reshape(-1), rr, rtol=1e-5, atol=2e-6)
-    assert np.allclose(st.m.cpu().numpy().reshape(-1), mm[3 * n:], rtol=1e-5, atol=1e-7)
-    assert np.allclose(st.v.cpu().numpy().reshape(-1), vv[3 * n:], rtol=1e-5, atol=1e-7)
+    sl = oracle.theta_slices(n, 3)
+    mu_mag, r_mag = step_mags(theta0, np.abs(g0[sl["mean"]]), r0, xir, n, 3, params, burn_in)
+    rep = {"mean": assert_step_close(got[sl["mean"]], th[sl["mean"]], mu_mag, "mean"),
+           "momentum": assert_step_close(st.r.cpu().numpy(), rr, r_mag, "momentum")}
+    t = step + 1  # beta^t is 0 in both precisions above 2^24
+    b1, b2 = params["beta1"], params["beta2"]
+    for f, lr in zip(("log_scale", "quat", "nu", "opacity_raw", "sh"), params["lr"]):
+        j = sl[f]
+        ga = np.abs(g0[j])
+        inc = adam_increment_mag(mo[j], ga, vv[j], lr, b1, b2, params["adam_eps"], t)
+        rep[f] = assert_step_close(got[j], th[j], inc, f)
+        jm = slice(j.start - 3 * n, j.stop - 3 * n)
+        assert_step_close(st.m.cpu().numpy().reshape(-1)[jm], mm[j], b1 * np.abs(mo[j]) + (1 - b1) * ga, f + " m")
+        assert_step_close(st.v.cpu().numpy().reshape(-1)[jm], vv[j], vv[j], f + " v")
+    print("sampler bar", burn_in, step, rep)
 
 
 @pytest.mark.parametrize("burn_in,n_comp", [(False, 5000), (True, 5000), (False, 4999)])
