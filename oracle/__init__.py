@@ -21,7 +21,7 @@ from . import build as _build
 
 # projection record fields (doubles), same order as sss_oracle.c
 P_FIELDS = ("valid mx my cov_a cov_b cov_c con_a con_b con_c depth o nu r g b "
-            "clamp_r clamp_g clamp_b hmax px0 px1 py0 py1 tx0 tx1 ty0 ty1 ntiles").split()
+            "clamp_r clamp_g clamp_b hmax px0 px1 py0 py1 tx0 tx1 ty0 ty1 ntiles es").split()
 P = {name: i for i, name in enumerate(P_FIELDS)}
 P_STRIDE = len(P_FIELDS)
 # 2D gradient record fields: dL/d(mean2D x, y, conic a, b, c, o, nu, r, g, b)
@@ -57,12 +57,12 @@ def lib():
         L.orc_project.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _ip, _dp, _ip, _dp]
         L.orc_project.restype = None
         L.orc_render.argtypes = [ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _dp, _ip, ctypes.c_long,
-                                 _nullable(_lp), _dp, _nullable(_dp), _nullable(_ip), _nullable(_lp),
-                                 _nullable(_ip)]
+                                 _nullable(_lp), _nullable(_up), _dp, _nullable(_dp), _nullable(_ip),
+                                 _nullable(_lp), _nullable(_ip), _nullable(_ip)]
         L.orc_render.restype = None
         L.orc_backward.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp, _ip, _dp, _ip,
-                                   _nullable(_lp), _nullable(_lp), _dp, _nullable(_dp), _dp, _nullable(_dp),
-                                   _nullable(_dp), _nullable(_dp), _nullable(_dp)]
+                                   _nullable(_lp), _nullable(_lp), _nullable(_up), _dp, _nullable(_dp), _dp,
+                                   _nullable(_dp), _nullable(_dp), _nullable(_dp), _nullable(_dp)]
         L.orc_backward.restype = None
         L.orc_sghmc_step.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int,
                                      ctypes.c_uint64, ctypes.c_uint64, _nullable(_dp)]
@@ -151,28 +151,39 @@ def project(scene_or_theta, cam, cfg=None, *, n=None, sh_degree=None) -> np.ndar
     return out
 
 
-def render(proj: np.ndarray, cam, cfg=None, pix=None) -> dict:
-    """Brute-force composite of the pixels ``pix`` (linear y*W+x; None = all)."""
+def render(proj: np.ndarray, cam, cfg=None, pix=None, flip=None) -> dict:
+    """Brute-force composite of the pixels ``pix`` (linear y*W+x; None = all).
+
+    ``flags`` marks pixels with a decision (|alpha| >= tau, T' >= t_min)
+    within the rounding error of an FP32 evaluation, ``n_amb`` counts those
+    decisions; ``flip`` (one uint32 per pixel) takes the j-th of them the
+    other way where bit j is set: the other correct results."""
     fd, fi = cfg_arrays(cfg)
     n = proj.shape[0]
     pix_arr = None if pix is None else np.ascontiguousarray(pix, np.int64)
     npix = cam.width * cam.height if pix is None else len(pix_arr)
+    flip_arr = None if flip is None else np.ascontiguousarray(flip, np.uint32)
+    assert flip_arr is None or len(flip_arr) == npix
     rgb = np.zeros((3, npix), np.float64)
     T = np.zeros(npix, np.float64)
     nc = np.zeros(npix, np.int32)
     last = np.zeros(npix, np.int64)
     flags = np.zeros(npix, np.int32)
-    lib().orc_render(n, np.ascontiguousarray(proj), cam.width, cam.height, fd, fi, npix, pix_arr, rgb, T, nc,
-                     last, flags)
-    return dict(rgb=rgb, T=T, n_contrib=nc, last=last, flags=flags)
+    namb = np.zeros(npix, np.int32)
+    lib().orc_render(n, np.ascontiguousarray(proj), cam.width, cam.height, fd, fi, npix, pix_arr, flip_arr, rgb, T,
+                     nc, last, flags, namb)
+    return dict(rgb=rgb, T=T, n_contrib=nc, last=last, flags=flags, n_amb=namb)
 
 
 def backward(scene_or_theta, cams, cfg, dl_dc, pix=None, *, n=None, sh_degree=None, want_grad2d=False,
-             want_abs=False):
+             want_abs=False, flip=None):
     """Analytic FP64 gradient of L = sum(dl_dc * C) w.r.t. theta.
 
     dl_dc: list (one per view) of [3][npix_v] (or [3][H][W]) arrays.
     pix:   None (all pixels) or a list of linear-index arrays per view.
+    flip:  None or a list (one per view) of uint32 per pixel: the forward
+           each pixel is differentiated through takes its ambiguous decisions
+           as in ``render(..., flip=...)``.
     Returns grad theta (planar) and, if asked, grad2d [views][n][G_STRIDE];
     with want_abs also the sums of |summand| for both (grad_abs, grad2d_abs),
     the scale against which a floating-point evaluation of the same sums
@@ -195,14 +206,18 @@ def backward(scene_or_theta, cams, cfg, dl_dc, pix=None, *, n=None, sh_degree=No
         pix_cat = np.ascontiguousarray(np.concatenate([np.asarray(p, np.int64) for p in pix]))
         dl = np.concatenate([np.asarray(d, np.float64).reshape(3, -1).reshape(-1) for d in dl_dc])
     dl = np.ascontiguousarray(dl)
+    flip_cat = None
+    if flip is not None:
+        flip_cat = np.ascontiguousarray(np.concatenate([np.asarray(f, np.uint32).reshape(-1) for f in flip]))
+        assert len(flip_cat) * 3 == len(dl)
     grad = np.zeros_like(theta)
     g2d = np.zeros((V, n, G_STRIDE), np.float64) if want_grad2d else None
     gabs = np.zeros_like(theta) if want_abs else None
     gabsn = np.zeros_like(theta) if want_abs else None
     g2abs = np.zeros((V, n, G_STRIDE), np.float64) if (want_abs and want_grad2d) else None
     g2absn = np.zeros((V, n, G_STRIDE), np.float64) if (want_abs and want_grad2d) else None
-    lib().orc_backward(n, sh_degree, theta, V, cds, whs, fd, fi, npix, pix_cat, dl, g2d, grad, g2abs, gabs, gabsn,
-                       g2absn)
+    lib().orc_backward(n, sh_degree, theta, V, cds, whs, fd, fi, npix, pix_cat, flip_cat, dl, g2d, grad, g2abs, gabs,
+                       gabsn, g2absn)
     out = (grad,)
     if want_grad2d:
         out += (g2d,)

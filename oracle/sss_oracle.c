@@ -33,9 +33,9 @@
  * Parity notes: every function is a literal restatement; no blocking, fusion
  * or reordering beyond the definition.  The only shortcut is in orc_render:
  * a pair is skipped when h exceeds the value at which |o| T2D equals
- * tau * (1 - 2e-4); that is exactly equivalent to the |alpha| >= tau test it
+ * tau * (1 - 1e-2); that is exactly equivalent to the |alpha| >= tau test it
  * precedes (the skipped pairs all have |alpha| < tau) and keeps the near-tau
- * bookkeeping intact.
+ * bookkeeping (windows of at most 1e-2) intact.
  */
 #include <complex.h>
 #include <math.h>
@@ -62,7 +62,7 @@ typedef double complex cx;
 enum {
   P_VALID, P_MX, P_MY, P_COV_A, P_COV_B, P_COV_C, P_CON_A, P_CON_B, P_CON_C,
   P_DEPTH, P_O, P_NU, P_R, P_G, P_B, P_CLAMP_R, P_CLAMP_G, P_CLAMP_B, P_HMAX,
-  P_PX0, P_PX1, P_PY0, P_PY1, P_TX0, P_TX1, P_TY0, P_TY1, P_NTILES, P_STRIDE
+  P_PX0, P_PX1, P_PY0, P_PY1, P_TX0, P_TX1, P_TY0, P_TY1, P_NTILES, P_ES, P_STRIDE
 };
 
 /* --- 2D gradient record, doubles ---------------------------------------- */
@@ -324,6 +324,34 @@ static double kernel_limit(double o_abs, double nu, double a, const ocfg* cfg) {
   return cfg->kernel == 1 ? 2.0 * log(o_abs / a) : h_limit(o_abs, nu, a);
 }
 
+/* Scale of the rounding error of a Sigma2D computed in FP32, relative to its
+ * smallest eigenvalue: |J W|_F^2 s_max^2 / lambda_min(Sigma2D).  An FP32
+ * evaluation of Sigma2D = (J W R S)(J W R S)^T perturbs it by a few u times
+ * |J W|_F^2 s_max^2 (rotation and products rounded on the scale of the
+ * largest axis), and a perturbation dS of Sigma2D moves h = d^T Sigma2D^-1 d
+ * by at most |dS| h / lambda_min.  Used only for the ambiguity windows. */
+static double error_scale(int n, const double* th, size_t i, const ocam* cam, const double* rec) {
+  const double* V = cam->V;
+  double mu[3], p[3];
+  for (int c = 0; c < 3; ++c) mu[c] = th[TH_MEAN(n) + c * (size_t)n + i];
+  for (int r = 0; r < 3; ++r) p[r] = V[r * 4 + 0] * mu[0] + V[r * 4 + 1] * mu[1] + V[r * 4 + 2] * mu[2] + V[r * 4 + 3];
+  double limx = 1.3 * (cam->width / (2.0 * cam->fx)), limy = 1.3 * (cam->height / (2.0 * cam->fy));
+  double tx = fmin(fmax(p[0] / p[2], -limx), limx) * p[2], ty = fmin(fmax(p[1] / p[2], -limy), limy) * p[2];
+  double J[6] = {cam->fx / p[2], 0.0, -cam->fx * tx / (p[2] * p[2]), 0.0, cam->fy / p[2], -cam->fy * ty / (p[2] * p[2])};
+  double t2 = 0.0;
+  for (int r = 0; r < 2; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double a = J[r * 3 + 0] * V[0 * 4 + c] + J[r * 3 + 1] * V[1 * 4 + c] + J[r * 3 + 2] * V[2 * 4 + c];
+      t2 += a * a;
+    }
+  double lmax = th[TH_LS(n) + i];
+  for (int c = 1; c < 3; ++c) lmax = fmax(lmax, th[TH_LS(n) + c * (size_t)n + i]);
+  const double A = rec[P_COV_A], B = rec[P_COV_B], C = rec[P_COV_C];
+  const double tr = A + C, det = A * C - B * B;
+  const double lmin = 2.0 * det / (tr + sqrt(fmax(tr * tr - 4.0 * det, 0.0)));
+  return t2 * exp(2.0 * lmax) / lmin;
+}
+
 static void project_record(int n, int sh_deg, const double* th, size_t i, const ocam* cam, const ocfg* cfg,
                            double* rec) {
   cx buf[12 + 48];
@@ -376,6 +404,7 @@ static void project_record(int n, int sh_deg, const double* th, size_t i, const 
   long ty0 = (long)py0 / cfg->tile_h, ty1 = (long)py1 / cfg->tile_h;
   rec[P_TX0] = tx0; rec[P_TX1] = tx1; rec[P_TY0] = ty0; rec[P_TY1] = ty1;
   rec[P_NTILES] = (double)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+  rec[P_ES] = error_scale(n, th, i, cam, rec);
 }
 
 void orc_project(int n, int sh_deg, const double* theta, const double* camd, const int* wh, const double* cfgd,
@@ -430,40 +459,103 @@ static void cvec_push(cvec* c, contrib x) {
   c->v[c->n++] = x;
 }
 
+/* Ambiguity window of one (pixel, splat) decision.  Which splats contribute
+ * to a pixel is decided by |alpha| >= tau and by T' >= t_min; where such a
+ * decision lies within the rounding error of an FP32 evaluation (the
+ * precision of the paper's rasterizer), both outcomes are correct results.
+ * The window bounds, to first order, the relative error of alpha evaluated
+ * in FP32, as the sum of:
+ *   - the 2D covariance of an FP32 projection: |dh| <= 16 u E h, E the
+ *     error scale of the record (error_scale above; 16 u is 1.6 times the
+ *     largest |dh| / (u E h) measured for GB300's FP32 projection at the
+ *     alpha threshold over the shell and cluster workloads);
+ *   - the screen mean stored relative to its first tile's corner:
+ *     2 u (|m - corner| + 1) per coordinate (twice the largest measured
+ *     error), times |dh/dm|;
+ *   - evaluating h in FP32 from the offsets: 6 u q, q the sum of the
+ *     magnitudes of the three terms of h;
+ * times |dlnT2D/dh| = (nu+2) / (2 nu (1 + h/nu)) (1/2 for the Gaussian); plus
+ * T2D = 2^(-(nu+2)/2 log2(1 + h/nu)) with hardware log2 / exp2 of 2^-22
+ * error (absolute for log2, times the exponent; relative for exp2),
+ * 2 u (nu+2)/2 for rounding the argument 1 + h/nu, and 4 u for the rest
+ * (tanh of the opacity, products).  Capped at 1e-2 (the prefilter evaluates
+ * every pair with |alpha| >= tau (1 - 1e-2)). */
+#define ORC_U (1.0 / 16777216.0)
+#define ORC_MUFU (1.0 / 4194304.0)
+static double alpha_window(const double* r, double h, double dx, double dy, const ocfg* cfg) {
+  const double u = ORC_U;
+  const double ca = r[P_CON_A], cb = r[P_CON_B], cc = r[P_CON_C];
+  const double q = fabs(ca) * dx * dx + 2.0 * fabs(cb * dx * dy) + fabs(cc) * dy * dy;
+  const double ox = r[P_TX0] * cfg->tile_w, oy = r[P_TY0] * cfg->tile_h;
+  const double gm = 2.0 * fabs(ca * dx + cb * dy) * 2.0 * u * (fabs(r[P_MX] - ox) + 1.0) +
+                    2.0 * fabs(cb * dx + cc * dy) * 2.0 * u * (fabs(r[P_MY] - oy) + 1.0);
+  const double dh = 16.0 * u * r[P_ES] * h + gm + 6.0 * u * q;
+  double w;
+  if (cfg->kernel == 1) {
+    w = 0.5 * dh + ORC_MUFU + u * 0.5 * h;
+  } else {
+    const double nu = r[P_NU], e = 0.5 * (nu + 2.0);
+    w = e / nu / (1.0 + h / nu) * dh + log(2.0) * e * ORC_MUFU + 2.0 * u * e + ORC_MUFU;
+  }
+  w += 4.0 * u;
+  return w < 1e-2 ? w : 1e-2;
+}
+
 /* Composite pixel (px, py) (integer indices; sample point at the centre).
  * Readings: alpha = o T2D, skipped when |alpha| < tau; alpha clamped to
  * [-alpha_max, alpha_max]; front-to-back, stop before the component that
  * would bring T below t_min (t_min = 0 disables); background added with the
- * final transmittance. */
+ * final transmittance.
+ * Ambiguous decisions (alpha_window above; for the termination test, T' within
+ * the accumulated relative error of an FP32 T, 2 u + window |alpha| / |1 -
+ * alpha| per composited splat) set a flag bit; the j-th ambiguous decision met
+ * on the way is taken the other way when bit j of `flip` is set (the other
+ * correct result), and their number is returned in *n_amb. */
 static void composite_pixel(const double* proj, const long* order, long m, const double* hpre, const ocfg* cfg,
-                            long px, long py, double rgb[3], double* T_out, int* ncontrib, long* last, int* flags,
-                            cvec* keep) {
+                            long px, long py, uint32_t flip, double rgb[3], double* T_out, int* ncontrib,
+                            long* last, int* flags, int* n_amb, cvec* keep) {
   double u = (double)px + 0.5, v = (double)py + 0.5;
   double T = 1.0, C[3] = {0, 0, 0};
-  int nc = 0, fl = 0;
+  double errT = 0.0; /* relative error bound of an FP32 T along this path */
+  int nc = 0, fl = 0, ev = 0;
   long lst = -1;
   for (long k = 0; k < m; ++k) {
     long i = order[k];
     const double* r = proj + (size_t)i * P_STRIDE;
     double dx = u - r[P_MX], dy = v - r[P_MY];
     double h = r[P_CON_A] * dx * dx + 2.0 * r[P_CON_B] * dx * dy + r[P_CON_C] * dy * dy;
-    if (h > hpre[i]) continue; /* |alpha| < tau (1 - 2e-4) for sure */
+    if (h > hpre[i]) continue; /* |alpha| < tau (1 - 1e-2) for sure */
     double t2d = kernel_value(h, r[P_NU], cfg);
     double alpha = r[P_O] * t2d;
-    if (fabs(fabs(alpha) - cfg->tau) < 1e-4 * cfg->tau) fl |= F_NEAR_TAU;
-    if (!(fabs(alpha) >= cfg->tau)) continue;
+    const double W = alpha_window(r, h, dx, dy, cfg);
+    int include = fabs(alpha) >= cfg->tau;
+    if (fabs(fabs(alpha) - cfg->tau) <= W * cfg->tau) {
+      fl |= F_NEAR_TAU;
+      if (ev < 32 && ((flip >> ev) & 1u)) include = !include;
+      ++ev;
+    }
+    if (!include) continue;
     int clamped = 0;
     if (alpha > cfg->alpha_max) { alpha = cfg->alpha_max; clamped = 1; }
     if (alpha < -cfg->alpha_max) { alpha = -cfg->alpha_max; clamped = 1; }
     double Tn = T * (1.0 - alpha);
-    if (cfg->t_min > 0.0 && fabs(Tn - cfg->t_min) < 1e-3 * cfg->t_min) fl |= F_NEAR_TMIN;
-    if (cfg->t_min > 0.0 && Tn < cfg->t_min) break;
+    double errTn = errT + 2.0 * ORC_U + W * fabs(alpha) / fabs(1.0 - alpha);
+    if (cfg->t_min > 0.0) {
+      int term = Tn < cfg->t_min;
+      if (fabs(Tn - cfg->t_min) <= errTn * Tn) {
+        fl |= F_NEAR_TMIN;
+        if (ev < 32 && ((flip >> ev) & 1u)) term = !term;
+        ++ev;
+      }
+      if (term) break;
+    }
     if (keep) {
       contrib c = {i, alpha, T, t2d, h, dx, dy, clamped};
       cvec_push(keep, c);
     }
     for (int ch = 0; ch < 3; ++ch) C[ch] += r[P_R + ch] * alpha * T;
     T = Tn;
+    errT = errTn;
     ++nc;
     lst = i;
   }
@@ -472,22 +564,25 @@ static void composite_pixel(const double* proj, const long* order, long m, const
   *ncontrib = nc;
   *last = lst;
   *flags = fl;
+  if (n_amb) *n_amb = ev;
 }
 
 static double* prefilter_bounds(int n, const double* proj, const ocfg* cfg) {
   double* hpre = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   for (long i = 0; i < n; ++i) {
     const double* r = proj + (size_t)i * P_STRIDE;
-    hpre[i] = r[P_VALID] != 0.0 ? kernel_limit(fabs(r[P_O]), r[P_NU], cfg->tau * (1.0 - 2e-4), cfg) : -1.0;
+    hpre[i] = r[P_VALID] != 0.0 ? kernel_limit(fabs(r[P_O]), r[P_NU], cfg->tau * (1.0 - 1e-2), cfg) : -1.0;
   }
   return hpre;
 }
 
 /* Render npix pixels (linear indices pix[k] = y * width + x; pix == NULL means
- * all width*height pixels in order).  out_rgb is [3][npix]. */
+ * all width*height pixels in order).  out_rgb is [3][npix].  flip (optional,
+ * [npix]): per pixel, which ambiguous decisions to take the other way;
+ * out_namb (optional): the number of ambiguous decisions met. */
 void orc_render(int n, const double* proj, int width, int height, const double* cfgd, const int* cfgi, long npix,
-                const int64_t* pix, double* out_rgb, double* out_T, int32_t* out_n, int64_t* out_last,
-                int32_t* out_flags) {
+                const int64_t* pix, const uint32_t* flip, double* out_rgb, double* out_T, int32_t* out_n,
+                int64_t* out_last, int32_t* out_flags, int32_t* out_namb) {
   ocfg cfg = read_cfg(cfgd, cfgi);
   long m;
   long* order = sorted_valid(n, proj, &m);
@@ -498,14 +593,15 @@ void orc_render(int n, const double* proj, int width, int height, const double* 
     long lin = pix ? (long)pix[k] : k;
     long px = lin % width, py = lin / width;
     double rgb[3], T;
-    int nc, fl;
+    int nc, fl, na;
     long lst;
-    composite_pixel(proj, order, m, hpre, &cfg, px, py, rgb, &T, &nc, &lst, &fl, NULL);
+    composite_pixel(proj, order, m, hpre, &cfg, px, py, flip ? flip[k] : 0u, rgb, &T, &nc, &lst, &fl, &na, NULL);
     for (int c = 0; c < 3; ++c) out_rgb[(size_t)c * npix + k] = rgb[c];
     if (out_T) out_T[k] = T;
     if (out_n) out_n[k] = nc;
     if (out_last) out_last[k] = lst;
     if (out_flags) out_flags[k] = fl;
+    if (out_namb) out_namb[k] = na;
   }
   free(order);
   free(hpre);
@@ -634,7 +730,7 @@ static void pixel_backward(const double* proj, const cvec* cs, double T_final, c
  *            the whole list carries a rounding proportional to that count)
  * The 2D -> 3D chain uses the complex-step derivative of project_cx. */
 void orc_backward(int n, int sh_deg, const double* theta, int n_views, const double* cams, const int* whs,
-                  const double* cfgd, const int* cfgi, const int64_t* npix, const int64_t* pix,
+                  const double* cfgd, const int* cfgi, const int64_t* npix, const int64_t* pix, const uint32_t* flip,
                   const double* dL_dC, double* grad2d, double* grad, double* grad2d_abs, double* grad_abs,
                   double* grad_absn, double* grad2d_absn) {
   ocfg cfg = read_cfg(cfgd, cfgi);
@@ -648,11 +744,12 @@ void orc_backward(int n, int sh_deg, const double* theta, int n_views, const dou
   double* g2a = (grad2d_abs || grad_abs) ? (double*)malloc(sizeof(double) * G_STRIDE * (size_t)(n > 0 ? n : 1))
                                          : NULL;
   double* g2an = g2a ? (double*)malloc(sizeof(double) * G_STRIDE * (size_t)(n > 0 ? n : 1)) : NULL;
-  size_t pix_off = 0, dl_off = 0;
+  size_t pix_off = 0, dl_off = 0, flip_off = 0;
   for (int v = 0; v < n_views; ++v) {
     ocam cam = read_cam(cams + 16 * v, whs + 2 * v);
     long np = npix ? (long)npix[v] : (long)cam.width * cam.height;
     const int64_t* pv = pix ? pix + pix_off : NULL;
+    const uint32_t* fl_v = flip ? flip + flip_off : NULL;
     orc_project(n, sh_deg, theta, cams + 16 * v, whs + 2 * v, cfgd, cfgi, proj);
     memset(g2, 0, sizeof(double) * G_STRIDE * (size_t)n);
     if (g2a) memset(g2a, 0, sizeof(double) * G_STRIDE * (size_t)n);
@@ -672,7 +769,8 @@ void orc_backward(int n, int sh_deg, const double* theta, int n_views, const dou
         int nc, fl;
         long lst;
         cs.n = 0;
-        composite_pixel(proj, order, m, hpre, &cfg, px, py, rgb, &T, &nc, &lst, &fl, &cs);
+        composite_pixel(proj, order, m, hpre, &cfg, px, py, fl_v ? fl_v[k] : 0u, rgb, &T, &nc, &lst, &fl, NULL,
+                        &cs);
         double g[3] = {dl[k], dl[(size_t)np + k], dl[2 * (size_t)np + k]};
         pixel_backward(proj, &cs, T, g, &cfg, g2, g2a, g2an);
       }
@@ -726,6 +824,7 @@ void orc_backward(int n, int sh_deg, const double* theta, int n_views, const dou
       }
     }
     pix_off += pv ? (size_t)np : 0;
+    flip_off += (size_t)np;
     dl_off += 3 * (size_t)np;
   }
   free(proj);

@@ -44,43 +44,193 @@ def oracle_views(scene_np, cams, cfgd, pix=None):
     return out
 
 
-def masked_weights(cams, refs, seed, pix=None):
-    """Seeded dL/dC weights with the pixels the oracle flags as fragile (a
-    discrete decision within rounding distance) set to zero, so neither side's
-    gradient depends on them.  With pix given, only those pixels are nonzero."""
+# ---------------------------------------------------------------- forward bar
+# Every pixel is compared.  Where the oracle met no ambiguous decision (an
+# |alpha| or a T' within the FP32 rounding window of tau or t_min), the GPU
+# pixel must equal the oracle's within FWD_TOL per channel and in T.  Where it
+# met k of them, both outcomes of each are correct results: the GPU pixel
+# must equal, within FWD_TOL, one of the oracle's renders with those decisions
+# taken either way (all 2^(k+1) combinations of the first k + 1 decisions met,
+# the extra bit for a decision met only on another path).
+FWD_TOL = 1e-4
+FLIP_BITS = 10
+
+
+class ForwardCheck:
+    """Result of check_forward_view: flip[k] is the oracle's choice of
+    ambiguous decisions that the GPU's pixel k matched best (0 where none was
+    met); unresolved[k] is True where two different admissible results both
+    match the GPU's pixel within tol, so its image does not determine which
+    decisions it took (a gradient through it cannot be attributed);
+    [nc_lo, nc_hi] bounds the contributor count over the admissible results
+    within tol; stats summarises the view."""
+
+    def __init__(self, flip, unresolved, nc_lo, nc_hi, stats):
+        self.flip, self.unresolved, self.nc_lo, self.nc_hi, self.stats = flip, unresolved, nc_lo, nc_hi, stats
+
+
+def check_forward_view(proj, cam, cfgd, ref, img, T, pix=None, tol=FWD_TOL, last=None) -> ForwardCheck:
+    """Compares one view's GPU image [3][npix] and transmittance [npix] (the
+    pixels `pix`, or all) with the oracle render `ref` of the same pixels.
+    With `last` (the GPU's last contributor per pixel, component index or
+    -1), it must equal the oracle's too, and an admissible result matches
+    only with the same last contributor."""
+    img = np.asarray(img, np.float64)
+    T = np.asarray(T, np.float64)
+    npix = T.size
+    fl = ref["flags"] != 0
+    ok = ~fl
+    worst = 0.0
+    if ok.any():
+        worst = max(float(np.abs(img[:, ok] - ref["rgb"][:, ok]).max()), float(np.abs(T[ok] - ref["T"][ok]).max()))
+    assert worst <= tol, ("unflagged pixel", worst)
+    if last is not None:
+        last = np.asarray(last, np.int64)
+        assert np.array_equal(last[ok], ref["last"][ok]), int(np.sum(last[ok] != ref["last"][ok]))
+    flip = np.zeros(npix, np.uint32)
+    unresolved = np.zeros(npix, bool)
+    nc_lo = np.asarray(ref["n_contrib"], np.int64).copy()
+    nc_hi = nc_lo.copy()
+    idx = np.flatnonzero(fl)
+    worst_fl, primary = 0.0, 0
+    if idx.size:
+        k = ref["n_amb"][idx]
+        assert int(k.max()) < FLIP_BITS, ("ambiguous decisions per pixel", int(k.max()))
+        reps = 1 << (k + 1)
+        lin = (np.arange(npix) if pix is None else np.asarray(pix, np.int64))[idx]
+        rep_pos = np.repeat(np.arange(idx.size), reps)
+        masks = np.concatenate([np.arange(r) for r in reps]).astype(np.uint32)
+        alt = oracle.render(proj, cam, cfgd, lin[rep_pos], flip=masks)
+        err = np.maximum(np.abs(alt["rgb"] - img[:, idx[rep_pos]]).max(axis=0), np.abs(alt["T"] - T[idx[rep_pos]]))
+        if last is not None:  # a different last contributor is a different result
+            err = np.where(alt["last"] == last[idx[rep_pos]], err, np.inf)
+        starts = np.concatenate([[0], np.cumsum(reps)[:-1]])
+        best = np.minimum.reduceat(err, starts)
+        bad = best > tol
+        assert not bad.any(), ("flagged pixel matches no admissible result", int(bad.sum()), float(best.max()))
+        for i, (s0, r) in enumerate(zip(starts, reps)):
+            pick = s0 + int(np.argmin(err[s0:s0 + r]))  # the first combination reaching the best error
+            flip[idx[i]] = masks[pick]
+            good = np.flatnonzero(err[s0:s0 + r] <= tol) + s0
+            res = np.concatenate([alt["rgb"][:, good], alt["T"][None, good], alt["n_contrib"][None, good]])
+            unresolved[idx[i]] = np.unique(res, axis=1).shape[1] > 1
+            nc_lo[idx[i]] = alt["n_contrib"][good].min()
+            nc_hi[idx[i]] = alt["n_contrib"][good].max()
+        worst_fl = float(best.max())
+        primary = int((flip[idx] == 0).sum())
+    stats = {"pixels": int(npix), "flagged": int(idx.size), "flagged_frac": round(idx.size / max(npix, 1), 5),
+             "near_tau": int(np.sum((ref["flags"] & oracle.F_NEAR_TAU) != 0)),
+             "near_tmin": int(np.sum((ref["flags"] & oracle.F_NEAR_TMIN) != 0)),
+             "flagged_as_primary": primary, "unresolved": int(unresolved.sum()), "max_err_unflagged": worst,
+             "max_err_flagged": worst_fl}
+    return ForwardCheck(flip, unresolved, nc_lo, nc_hi, stats)
+
+
+def merge_stats(stats):
+    out = {"pixels": 0, "flagged": 0, "near_tau": 0, "near_tmin": 0, "flagged_as_primary": 0, "unresolved": 0,
+           "max_err_unflagged": 0.0, "max_err_flagged": 0.0}
+    for st in stats:
+        for k in ("pixels", "flagged", "near_tau", "near_tmin", "flagged_as_primary", "unresolved"):
+            out[k] += st[k]
+        for k in ("max_err_unflagged", "max_err_flagged"):
+            out[k] = max(out[k], st[k])
+    out["flagged_frac"] = round(out["flagged"] / max(out["pixels"], 1), 5)
+    return out
+
+
+def gpu_view(fr, j, cam, pix=None):
+    """GPU image [3][npix] and final T [npix] of job j (float64)."""
+    img = fr.image(j).reshape(3, -1).cpu().numpy().astype(np.float64)
+    pb = fr.plan.jobs[j].pix_base
+    T = fr.final_T()[pb:pb + cam.width * cam.height].cpu().numpy().astype(np.float64)
+    if pix is not None:
+        img, T = img[:, pix], T[pix]
+    return img, T
+
+
+def gpu_last_component(fr, j, cam, pix=None):
+    """Component index of each pixel's last contributor in job j (-1 when
+    none), from the GPU's list positions, tile ranges and sorted pairs."""
+    J = fr.plan.jobs[j]
+    hw = cam.width * cam.height
+    last = fr.last_contrib()[J.pix_base:J.pix_base + hw].cpu().numpy().astype(np.int64)
+    rng = fr.ranges().cpu().numpy().astype(np.int64)
+    _, vals = fr.sorted_pairs(fr.status()[1])
+    vals = vals.cpu().numpy().astype(np.int64)
+    ys, xs = np.divmod(np.arange(hw), cam.width)
+    tile = J.tile_base + (ys // fr.cfg.tile_h) * J.tiles_x + xs // fr.cfg.tile_w
+    comp = np.where(last > 0, vals[np.maximum(rng[tile, 0] + last - 1, 0)] - J.entry_base, -1)
+    return comp if pix is None else comp[pix]
+
+
+def check_forward_frame(fr, cams, cfgd, refs, pix=None, tol=FWD_TOL):
+    """check_forward_view for every job of a frame; returns (flips per view,
+    merged stats, unresolved masks per view)."""
+    flips, stats, unres = [], [], []
+    for j, (cam, (proj, ref)) in enumerate(zip(cams, refs)):
+        pj = None if pix is None else pix[j]
+        img, T = gpu_view(fr, j, cam, pj)
+        c = check_forward_view(proj, cam, cfgd, ref, img, T, pj, tol, last=gpu_last_component(fr, j, cam, pj))
+        flips.append(c.flip)
+        stats.append(c.stats)
+        unres.append(c.unresolved)
+    return flips, merge_stats(stats), unres
+
+
+def resolved_weights(fr, cams, cfgd, refs, seed, pix=None):
+    """Seeded dL/dC weights and, per view, the oracle's choice of ambiguous
+    decisions that the GPU's forward matched, so that the oracle
+    differentiates the same admissible forward.  Only the pixels whose image
+    matches two different admissible results (its decisions are then not
+    determined; counted in stats["unresolved"]) carry no weight.  With pix
+    given, only those pixels carry weight."""
+    flips, stats, unres = check_forward_frame(fr, cams, cfgd, refs, pix)
     ws = inputs.linear_loss_weights(cams, seed)
     out = []
-    for v, (w, (_, ref)) in enumerate(zip(ws, refs)):
+    for v, w in enumerate(ws):
         w = w.reshape(3, -1).copy()
         if pix is None:
-            w[:, ref["flags"] != 0] = 0.0
+            w[:, unres[v]] = 0.0
         else:
             keep = np.zeros(w.shape[1], bool)
-            keep[pix[v][ref["flags"] == 0]] = True
+            keep[np.asarray(pix[v])[~unres[v]]] = True
             w[:, ~keep] = 0.0
         out.append(w)
-    return out
+    return out, flips, stats
 
 
 def scene_grads_flat(g: frame.Scene) -> np.ndarray:
     return np.concatenate([g.t[f].detach().cpu().numpy().reshape(-1).astype(np.float64) for f in frame.FIELDS])
 
 
-GRAD_REL = 1e-3   # relative bar per element ...
+GRAD_REL = 1e-3   # the survey's bar: |g - g_ref| <= 1e-3 max(|g_ref|, 1e-3 max_group |g_ref|) ...
 U32 = 2.0 ** -24  # FP32 unit roundoff
-# ... unless the difference is within the FP32 rounding bound of the sums:
-# u * (16 * sum |term| n + 256 * sum |term|), n the contributor count of each
-# term's pixel (the transmittance is recovered by one division per contributor,
-# so its rounding grows with n) and 256 u for the per-term evaluation (MUFU
-# lg2/ex2 approximations times the exponent (nu+2)/2, mean2D rounding).
+# ... or, for an element where the terms of its sum cancel, within the FP32
+# rounding bound of that sum: u (4 A_n + 64 A), A = sum |term| (taken on the
+# operands of the subtractions inside a term), A_n the same with every
+# pixel's terms weighted by its contributor count (the transmittance is
+# recovered by one division per contributor, so its rounding grows with the
+# count), 64 u for the per-term evaluation (MUFU lg2/ex2 times the exponent,
+# the stored mean); SH coefficients add the basis bound of sh_basis_bound.
+# At most FLOOR_FRAC of the touched elements of a group (at least one) may
+# rest on it.
+FLOOR_N, FLOOR_A = 4.0, 64.0
+FLOOR_FRAC = 0.01
 GRAD_NORM = 1e-4  # and ||g - g_ref|| / ||g_ref|| per group
 
 
+def grad_floor(mag, extra=0.0):
+    """The FP32 rounding bound of each element's sum."""
+    return U32 * (FLOOR_N * mag.absn + FLOOR_A * mag.abs) + extra
+
+
 def grad_den(ref, mag, extra=0.0):
-    """Per-element scale of the bar: max(|g_ref|, FP32 bound / GRAD_REL)."""
-    bound = U32 * (16.0 * mag.absn + 256.0 * mag.abs) + extra
+    """Per-element scale: the survey's bar divided by GRAD_REL, or the FP32
+    bound divided by GRAD_REL where that is larger (|g - g_ref| <= GRAD_REL x
+    this is the element's test)."""
     scale = max(float(np.abs(ref).max()), 1e-30)
-    return np.maximum(np.maximum(np.abs(ref), bound / GRAD_REL), 1e-9 * scale)
+    lit = np.maximum(np.abs(ref), 1e-3 * scale)
+    return np.maximum(lit, grad_floor(mag, extra) / GRAD_REL)
 
 
 def sh_basis_bound(n, sh_degree, mag2d):
@@ -101,9 +251,14 @@ def sh_basis_bound(n, sh_degree, mag2d):
 
 
 def assert_groups_close(got, ref, n, sh_degree, mag, rel=GRAD_REL, norm=GRAD_NORM, label="", extra=None):
-    """Per parameter group: every element within ``rel`` of grad_den (1e-3
-    relative, or the FP32 rounding bound of its sums) and the group's relative
-    L2 error within ``norm``."""
+    """Per parameter group: every element within the survey's bar
+    rel max(|g_ref|, 1e-3 max_group |g_ref|) or within the FP32 rounding
+    bound of its sum; at most FLOOR_FRAC of the touched elements (those with a
+    nonzero reference or summand) resting on the latter; and the group's
+    relative L2 error within ``norm``.  Returns per group: the largest ratio
+    of error to bar, the relative L2 error, the number of touched elements,
+    how many of them fail the survey's bar (and so rest on the FP32 bound),
+    and that fraction."""
     sl = oracle.theta_slices(n, sh_degree)
     report = {}
     for name, s in sl.items():
@@ -112,13 +267,21 @@ def assert_groups_close(got, ref, n, sh_degree, mag, rel=GRAD_REL, norm=GRAD_NOR
         if scale == 0:
             assert np.abs(a).max() == 0, (label, name)
             continue
-        den = grad_den(b, mag[s], 0.0 if extra is None else extra[s])
-        relerr = np.abs(a - b) / den
+        ex = 0.0 if extra is None else extra[s]
+        den = grad_den(b, mag[s], ex)
+        err = np.abs(a - b)
+        relerr = err / den
         l2 = float(np.linalg.norm(a - b) / np.linalg.norm(b))
-        report[name] = (float(relerr.max()), l2)
+        touched = (b != 0) | (mag[s].abs > 0)
+        literal = touched & (err > rel * np.maximum(np.abs(b), 1e-3 * scale))
+        frac = float(literal.sum()) / max(int(touched.sum()), 1)
+        report[name] = {"max_ratio": round(float(relerr.max()) / rel, 4), "l2": float(f"{l2:.3g}"),
+                        "touched": int(touched.sum()), "literal_fail": int(literal.sum()),
+                        "floor_frac": round(frac, 5)}
         bad = relerr > rel
         assert not bad.any(), (label, name, report[name], int(bad.sum()), a[bad][:5], b[bad][:5])
         assert l2 <= norm, (label, name, report[name])
+        assert literal.sum() <= max(1.0, FLOOR_FRAC * touched.sum()), (label, name, report[name])
     return report
 
 
@@ -204,3 +367,38 @@ def assert_step_close(got, ref, mag, label="", rel=STEP_REL):
     worst = int(np.argmax(ratio))
     assert ratio[worst] <= 1.0, (label, float(ratio[worst]), got[worst], ref[worst], float(bound[worst]))
     return {"max_ratio": round(float(ratio.max()), 4), "floor_frac": round(float(np.mean(floor > rel * np.abs(ref))), 4)}
+
+
+# ---------------------------------------------------------------- the windows, checked
+def projection_error_ratio(fr, j, cam, proj, seed=0):
+    """The GPU's FP32 projection error of h on the ellipse h = h_max (where
+    alpha = tau), against the part of the oracle's ambiguity window that
+    models it, 16 u E h + 2 u (|m - corner| + 1) |dh/dm|, E the record's
+    error scale: one random point of the ring per valid entry of job j.
+    Returns the ratios |dh| / window (all must be <= 1)."""
+    n = proj.shape[0]
+    eb = fr.plan.jobs[j].entry_base
+    recs = fr.records()[eb:eb + n].cpu().numpy().astype(np.float64)
+    dkey = fr.depth_keys()[eb:eb + n].cpu().numpy().view(np.uint32)
+    ok = (proj[:, oracle.P["valid"]] != 0) & (dkey != 0xFFFFFFFF) & (proj[:, oracle.P["ntiles"]] > 0)
+    r, f = recs[ok], proj[ok]
+    org = r[:, 11].astype(np.float32).view(np.uint32)
+    ox, oy = (org & 0xFFFF).astype(np.float64), (org >> 16).astype(np.float64)
+    A, B, C = f[:, oracle.P["cov_a"]], f[:, oracle.P["cov_b"]], f[:, oracle.P["cov_c"]]
+    l11 = np.sqrt(A)
+    l21 = B / l11
+    l22 = np.sqrt(np.maximum(C - l21 ** 2, 0.0))
+    th = np.random.default_rng(seed).uniform(0.0, 2.0 * np.pi, len(f))
+    hm = f[:, oracle.P["hmax"]]
+    dx = np.sqrt(hm) * l11 * np.cos(th)
+    dy = np.sqrt(hm) * (l21 * np.cos(th) + l22 * np.sin(th))
+    ca, cb, cc = f[:, oracle.P["con_a"]], f[:, oracle.P["con_b"]], f[:, oracle.P["con_c"]]
+    h = ca * dx * dx + 2 * cb * dx * dy + cc * dy * dy
+    px, py = f[:, oracle.P["mx"]] + dx, f[:, oracle.P["my"]] + dy
+    gx, gy = px - (r[:, 0] + ox), py - (r[:, 1] + oy)
+    hg = r[:, 2] * gx * gx + 2 * r[:, 3] * gx * gy + r[:, 4] * gy * gy
+    tx0 = f[:, oracle.P["tx0"]] * fr.cfg.tile_w
+    ty0 = f[:, oracle.P["ty0"]] * fr.cfg.tile_h
+    gm = (2 * np.abs(ca * dx + cb * dy) * 2 * U32 * (np.abs(f[:, oracle.P["mx"]] - tx0) + 1)
+          + 2 * np.abs(cb * dx + cc * dy) * 2 * U32 * (np.abs(f[:, oracle.P["my"]] - ty0) + 1))
+    return np.abs(hg - h) / (16 * U32 * f[:, oracle.P["es"]] * h + gm)

@@ -10,12 +10,11 @@ import torch
 import oracle
 from paper_2503_10148_gb300 import _abi, frame, inputs
 
-from gpu_util import (DEV, assert_groups_close, f32_scene, masked_weights, oracle_views, require_gpu,
+from gpu_util import (DEV, assert_groups_close, f32_scene, oracle_views, require_gpu, resolved_weights,
                       scene_grads_flat, sh_basis_bound)
 
 pytestmark = pytest.mark.gpu
 
-FWD_TOL = 1e-4
 SIZES = ((1, 1), (1, 9), (9, 1), (7, 5), (17, 16), (33, 18), (40, 23), (16, 17))  # (width, height)
 
 
@@ -52,24 +51,14 @@ def test_max_jobs_and_scenes_forward_and_backward_against_oracle(tile):
     assert fr.status()[0] == 0
     cfgd = frame.cfg_dict(fr.cfg)
     s32 = [f32_scene(s) for s in scenes]
-    # forward, job by job
-    refs, worst, flagged, total = [], 0.0, 0, 0
+    # forward, job by job: every pixel (flagged ones against the admissible results)
+    refs = []
     for j, cam in enumerate(cams):
         (proj, ref), = oracle_views(s32[job_scene[j]], [cam], cfgd)
         refs.append((proj, ref))
-        img = fr.image(j).reshape(3, -1).cpu().numpy().astype(np.float64)
-        pb = fr.plan.jobs[j].pix_base
-        T = fr.final_T()[pb:pb + cam.width * cam.height].cpu().numpy().astype(np.float64)
-        ok = ref["flags"] == 0
-        flagged += int((~ok).sum())
-        total += ok.size
-        if ok.any():
-            worst = max(worst, float(np.abs(img[:, ok] - ref["rgb"][:, ok]).max()))
-            assert np.abs(T[ok] - ref["T"][ok]).max() <= FWD_TOL, j
-    assert worst <= FWD_TOL, worst
-    assert flagged <= 0.05 * total, (flagged, total)
+    ws, flips, st = resolved_weights(fr, cams, cfgd, refs, seed=9)
+    print("forward", st)
     # backward: per scene, the gradient summed over that scene's jobs
-    ws = masked_weights(cams, refs, seed=9)
     dl = torch.as_tensor(np.concatenate([w.reshape(-1) for w in ws]).astype(np.float32), device=DEV)
     grads = [s.zeros_like() for s in scs]
     fr.backward(dl, grads)
@@ -77,6 +66,6 @@ def test_max_jobs_and_scenes_forward_and_backward_against_oracle(tile):
     for s, sc in enumerate(scenes):
         jobs = [j for j in range(len(cams)) if job_scene[j] == s]
         gref, _, gabs, g2abs = oracle.backward(s32[s], [cams[j] for j in jobs], cfgd, [ws[j] for j in jobs],
-                                               want_grad2d=True, want_abs=True)
+                                               want_grad2d=True, want_abs=True, flip=[flips[j] for j in jobs])
         print(assert_groups_close(scene_grads_flat(grads[s]), gref, sc["n"], sc["sh_degree"], gabs,
                                   label=f"scene {s}", extra=sh_basis_bound(sc["n"], sc["sh_degree"], g2abs)))

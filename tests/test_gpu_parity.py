@@ -1,12 +1,14 @@
 """GPU parity of every hot-path step against the FP64 oracle, through the C ABI.
 
 Bars: tile lists and sorted keys bit-exact; forward <= 1e-4 max-abs per pixel
-channel (pixels the oracle flags as within rounding distance of a discrete
-decision are excluded and counted); gradients: every element within 1e-3
-relative or within the FP32 rounding bound of its sums (derived from the
-magnitudes of its summands and the contributor counts of their pixels), and
-<= 1e-4 relative L2 per group; sampler noise and updates within FP32
-rounding.
+channel and in T on every pixel (where the oracle met a decision within the
+FP32 rounding window of tau or t_min, against the admissible result -- those
+decisions taken either way -- that the GPU matched; the flagged fraction is
+reported); gradients, through the same admissible forward: every element
+within 1e-3 relative or within the FP32 rounding bound of its sums (derived
+from the magnitudes of its summands and the contributor counts of their
+pixels), and <= 1e-4 relative L2 per group; sampler: Philox words bit for
+bit, updates within 1e-6 relative or the FP32 rounding of the increment.
 """
 import math
 
@@ -17,14 +19,15 @@ import torch
 import oracle
 from paper_2503_10148_gb300 import _abi, frame, inputs
 
-from gpu_util import (DEV, GRAD_NORM, GRAD_REL, U32, adam_increment_mag, assert_groups_close, assert_step_close,
-                      f32, f32_scene, gpu_forward, grad_den, step_mags,
-                      masked_weights, oracle_views, require_gpu, scene_grads_flat, sh_basis_bound)
+from gpu_util import (DEV, FWD_TOL, GRAD_NORM, GRAD_REL, U32, adam_increment_mag, assert_groups_close,
+                      assert_step_close, check_forward_frame, check_forward_view, f32, f32_scene, gpu_forward,
+                      gpu_last_component, gpu_view, grad_den, oracle_views, projection_error_ratio, require_gpu,
+                      resolved_weights, scene_grads_flat,
+                      sh_basis_bound, step_mags)
 from oracle import Magnitudes
 
 pytestmark = pytest.mark.gpu
 
-FWD_TOL = 1e-4
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -150,6 +153,19 @@ def test_bin_sort_bit_exact_multiview(tile):
     _check_bin_sort(fr)
 
 
+def test_projection_error_within_the_ambiguity_window():
+    """The FP32 projection's error in h, on the ellipse where alpha = tau,
+    stays inside the part of the oracle's ambiguity window that models it
+    (shell workload, every valid entry of every view)."""
+    scene, cams = inputs.shell_100k_8views()
+    fr, _, cams = gpu_forward(scene, cams)
+    cfgd = frame.cfg_dict(fr.cfg)
+    ratios = np.concatenate([projection_error_ratio(fr, j, cam, oracle.project(f32_scene(scene), cam, cfgd), seed=j)
+                             for j, cam in enumerate(cams)])
+    print("projection error / window:", {q: float(np.quantile(ratios, q)) for q in (0.5, 0.99, 0.9999, 1.0)})
+    assert ratios.max() <= 1.0
+
+
 def test_depth_ties_break_by_component_index():
     """Identical components (same depth key) must keep index order."""
     base = inputs.scene_uniform_cube(64, seed=7)
@@ -161,33 +177,13 @@ def test_depth_ties_break_by_component_index():
 
 # ---------------------------------------------------------------- a4 forward
 
-def _check_forward(fr, scene, cams, cfgd, pix=None):
+def _check_forward(fr, scene, cams, cfgd, pix=None, max_flagged=None):
     refs = oracle_views(scene, cams, cfgd, pix)
-    worst = 0.0
-    flagged = 0
-    total = 0
-    kinds = np.zeros(4, np.int64)
-    for j, (cam, (_, ref)) in enumerate(zip(cams, refs)):
-        img = fr.image(j).reshape(3, -1).cpu().numpy().astype(np.float64)
-        Tg = fr.final_T()[fr.plan.jobs[j].pix_base:fr.plan.jobs[j].pix_base + cam.width * cam.height]
-        Tg = Tg.cpu().numpy().astype(np.float64)
-        if pix is not None:
-            img = img[:, pix[j]]
-            Tg = Tg[pix[j]]
-        ok = ref["flags"] == 0
-        flagged += int((~ok).sum())
-        kinds += np.bincount(ref["flags"], minlength=4)[:4]
-        total += ok.size
-        err = np.abs(img[:, ok] - ref["rgb"][:, ok])
-        worst = max(worst, float(err.max()) if err.size else 0.0)
-        assert np.abs(Tg[ok] - ref["T"][ok]).max() <= FWD_TOL
-    assert worst <= FWD_TOL, worst
-    # flagged: pixels with an |alpha| within 1e-4 relative of tau (bit 1) or a
-    # transmittance within 1e-3 relative of t_min at the termination test (bit 2)
-    print(f"forward max-abs {worst:.3e}; flagged {flagged}/{total} (near tau {kinds[1] + kinds[3]}, "
-          f"near t_min {kinds[2] + kinds[3]})")
-    assert flagged <= 0.05 * total, (flagged, total, kinds)
-    return worst, flagged
+    flips, st, _ = check_forward_frame(fr, cams, cfgd, refs, pix)
+    print("forward", st)
+    if max_flagged is not None:
+        assert st["flagged_frac"] <= max_flagged, st
+    return st
 
 
 @pytest.mark.parametrize("tile,batch", [((16, 16), 32), ((32, 16), 32), ((16, 32), 32), ((32, 32), 32),
@@ -202,40 +198,39 @@ def test_forward_tiny_all_tile_configs(tile, batch):
 
 
 def test_forward_last_contributor_matches_oracle():
+    """Every pixel's last contributor equals the oracle's (flagged pixels:
+    that of the admissible result they match)."""
     scene, cams = inputs.tiny_cube_2k()
     fr, _, cams = gpu_forward(scene, cams)
     cfgd = frame.cfg_dict(fr.cfg)
-    ref = oracle.render(oracle.project(f32_scene(scene), cams[0], cfgd), cams[0], cfgd)
-    last = fr.last_contrib().cpu().numpy().astype(np.int64)
-    rng = fr.ranges().cpu().numpy().astype(np.int64)
-    k, v = fr.sorted_pairs(fr.status()[1])
-    v = v.cpu().numpy().astype(np.int64)
-    W = cams[0].width
-    ys, xs = np.divmod(np.arange(W * cams[0].height), W)
-    tile = (ys // fr.cfg.tile_h) * fr.plan.jobs[0].tiles_x + xs // fr.cfg.tile_w
-    comp = np.where(last > 0, v[np.maximum(rng[tile, 0] + last - 1, 0)], -1)
-    ok = ref["flags"] == 0
-    assert np.array_equal(comp[ok], ref["last"][ok])
+    proj = oracle.project(f32_scene(scene), cams[0], cfgd)
+    ref = oracle.render(proj, cams[0], cfgd)
+    img, T = gpu_view(fr, 0, cams[0])
+    comp = gpu_last_component(fr, 0, cams[0])
+    chk = check_forward_view(proj, cams[0], cfgd, ref, img, T, last=comp)
+    alt = oracle.render(proj, cams[0], cfgd, flip=chk.flip)  # the admissible result the GPU matched
+    assert np.array_equal(comp, alt["last"]) and (comp >= 0).sum() > 1000
 
 
 def test_pair_counters_match_oracle():
     """cfg.count_pairs: the forward counts contributing (splat, pixel) pairs
-    (the oracle's n_contrib summed over pixels; flagged pixels, whose FP32
-    decisions may differ near tau or t_min, get a slack) and evaluated pairs
-    (at least the contributing ones); a forward without counting adds
-    nothing."""
+    (the oracle's n_contrib summed over pixels, each pixel through the
+    admissible forward the GPU matched) and evaluated pairs (at least the
+    contributing ones); a forward without counting adds nothing."""
     scene, cams = inputs.tiny_cube_2k()
     fr, _, cams = gpu_forward(scene, cams)
     cfgd = frame.cfg_dict(fr.cfg)
     nc, ne = fr.count_pairs()
-    want, slack = 0, 0
-    for cam in cams:
-        ref = oracle.render(oracle.project(f32_scene(scene), cam, cfgd), cam, cfgd)
-        want += int(ref["n_contrib"].sum())
-        fl = ref["flags"] != 0
-        slack += int(ref["n_contrib"][fl].sum()) + 4 * int(fl.sum())
-    assert abs(nc - want) <= slack, (nc, want, slack)
-    assert want > 0 and ne >= nc
+    lo = hi = 0
+    for j, cam in enumerate(cams):
+        proj = oracle.project(f32_scene(scene), cam, cfgd)
+        ref = oracle.render(proj, cam, cfgd)
+        img, T = gpu_view(fr, j, cam)
+        chk = check_forward_view(proj, cam, cfgd, ref, img, T, last=gpu_last_component(fr, j, cam))
+        lo += int(chk.nc_lo.sum())
+        hi += int(chk.nc_hi.sum())
+    assert lo <= nc <= hi and hi - lo <= 20, (nc, lo, hi)
+    assert lo > 0 and ne >= nc
     fr.forward(grow=False)
     torch.cuda.synchronize()
     ctrl = fr.ws_view(fr.plan.ws_off_ctrl, torch.int64, 4).cpu()
@@ -249,7 +244,7 @@ def test_forward_shell_8views_800_sampled():
     fr, _, cams = gpu_forward(scene, cams)
     rng = np.random.default_rng(0)
     pix = [rng.choice(c.width * c.height, 2000, replace=False) for c in cams]
-    _check_forward(fr, f32_scene(scene), cams, frame.cfg_dict(fr.cfg), pix)
+    _check_forward(fr, f32_scene(scene), cams, frame.cfg_dict(fr.cfg), pix, max_flagged=0.012)
 
 
 @pytest.mark.parametrize("case", ["ragged", "no_termination", "lowpass", "background", "large_nu", "clamped_alpha",
@@ -332,11 +327,11 @@ def test_backward_tiny_against_oracle_analytic(nu_mode, tile):
     cfgd = frame.cfg_dict(cfg)
     s32 = f32_scene(scene)
     refs = oracle_views(s32, cams, cfgd)
-    ws = masked_weights(cams, refs, seed=5)
+    ws, flips, fst = resolved_weights(fr, cams, cfgd, refs, seed=5)
     g = _gpu_backward(fr, sc, ws)
-    gref, g2d, gabs, g2abs = oracle.backward(s32, cams, cfgd, ws, want_grad2d=True, want_abs=True)
+    gref, g2d, gabs, g2abs = oracle.backward(s32, cams, cfgd, ws, want_grad2d=True, want_abs=True, flip=flips)
     _grad2d_report(fr, g2d, g2abs, cams, scene)
-    print(assert_groups_close(scene_grads_flat(g), gref, scene["n"], 0, gabs, label="tiny",
+    print(fst, assert_groups_close(scene_grads_flat(g), gref, scene["n"], 0, gabs, label="tiny",
                               extra=sh_basis_bound(scene["n"], 0, g2abs)))
 
 
@@ -348,11 +343,11 @@ def test_backward_shell_sh3_multiview_against_oracle_analytic():
     cfgd = frame.cfg_dict(fr.cfg)
     s32 = f32_scene(scene)
     refs = oracle_views(s32, cams, cfgd)
-    ws = masked_weights(cams, refs, seed=6)
+    ws, flips, fst = resolved_weights(fr, cams, cfgd, refs, seed=6)
     g = _gpu_backward(fr, sc, ws)
-    gref, g2d, gabs, g2abs = oracle.backward(s32, cams, cfgd, ws, want_grad2d=True, want_abs=True)
+    gref, g2d, gabs, g2abs = oracle.backward(s32, cams, cfgd, ws, want_grad2d=True, want_abs=True, flip=flips)
     _grad2d_report(fr, g2d, g2abs, cams, scene)
-    print(assert_groups_close(scene_grads_flat(g), gref, scene["n"], 3, gabs, label="shell",
+    print(fst, assert_groups_close(scene_grads_flat(g), gref, scene["n"], 3, gabs, label="shell",
                               extra=sh_basis_bound(scene["n"], 3, g2abs)))
 
 
@@ -365,10 +360,14 @@ def test_backward_gradcheck_50k_against_oracle_fd_and_analytic():
     cfgd = frame.cfg_dict(fr.cfg)
     s32 = f32_scene(scene)
     refs = oracle_views(s32, cams, cfgd)
-    ws = masked_weights(cams, refs, seed=7)
+    ws, flips, fst = resolved_weights(fr, cams, cfgd, refs, seed=7)
     g = scene_grads_flat(_gpu_backward(fr, sc, ws))
-    gref, gabs = oracle.backward(s32, cams, cfgd, ws, want_abs=True)
-    print(assert_groups_close(g, gref, scene["n"], 0, gabs, label="gradcheck"))
+    gref, gabs = oracle.backward(s32, cams, cfgd, ws, want_abs=True, flip=flips)
+    print(fst, assert_groups_close(g, gref, scene["n"], 0, gabs, label="gradcheck"))
+    # central differences follow the oracle's own decisions: compare them with
+    # a GPU gradient whose flagged pixels carry no weight
+    ws = [w * (ref["flags"] == 0)[None, :] for w, (_, ref) in zip(ws, refs)]
+    g = scene_grads_flat(_gpu_backward(fr, sc, ws))
     # finite differences on parameters that influence the loss
     n = scene["n"]
     sl = oracle.theta_slices(n, 0)
@@ -406,10 +405,10 @@ def test_backward_edge_cases_large_nu_and_clamp(tile):
     cfgd = frame.cfg_dict(cfg)
     s32 = f32_scene(scene)
     refs = oracle_views(s32, cams, cfgd)
-    ws = masked_weights(cams, refs, seed=8)
+    ws, flips, fst = resolved_weights(fr, cams, cfgd, refs, seed=8)
     g = _gpu_backward(fr, sc, ws)
-    gref, gabs = oracle.backward(s32, cams, cfgd, ws, want_abs=True)
-    print(assert_groups_close(scene_grads_flat(g), gref, 1200, 0, gabs, label="edge"))
+    gref, gabs = oracle.backward(s32, cams, cfgd, ws, want_abs=True, flip=flips)
+    print(fst, assert_groups_close(scene_grads_flat(g), gref, 1200, 0, gabs, label="edge"))
 
 
 # ---------------------------------------------------------------- a7 step

@@ -66,7 +66,7 @@ def test_gaussian_kernel_forward_and_backward_against_oracle(tile):
     """kernel = 1 (T2D = exp(-h/2)): the forward within 1e-4 per channel and
     the gradient within the bar of the t kernel (nu gets none); one pixel
     per lane (16x16 tiles) and packed pixel pairs (32x32)."""
-    from gpu_util import (assert_groups_close, gpu_forward, masked_weights, oracle_views, scene_grads_flat,
+    from gpu_util import (assert_groups_close, gpu_forward, oracle_views, resolved_weights, scene_grads_flat,
                           sh_basis_bound)
     require_gpu()
     scene, cams = inputs.tiny_cube_2k()
@@ -76,18 +76,15 @@ def test_gaussian_kernel_forward_and_backward_against_oracle(tile):
     assert cfgd["kernel"] == 1
     s32 = f32_scene(scene)
     refs = oracle_views(s32, cams, cfgd)
-    ok = refs[0][1]["flags"] == 0
-    img = fr.image(0).reshape(3, -1).cpu().numpy()
-    assert np.abs(img[:, ok] - refs[0][1]["rgb"].reshape(3, -1)[:, ok]).max() <= 1e-4
+    ws, flips, st = resolved_weights(fr, cams, cfgd, refs, seed=21)  # every pixel's forward compared
     assert np.isinf(fr.records().cpu().numpy()[:, 7]).all()  # records carry nu = inf
-    ws = masked_weights(cams, refs, seed=21)
     dl = torch.as_tensor(np.concatenate([w.reshape(-1) for w in ws]).astype(np.float32), device=DEV)
     g = sc.zeros_like()
     fr.backward(dl, [g])
     torch.cuda.synchronize()
     gflat = scene_grads_flat(g)
-    gref, g2d, gabs, g2abs = oracle.backward(s32, cams, cfgd, ws, want_grad2d=True, want_abs=True)
+    gref, g2d, gabs, g2abs = oracle.backward(s32, cams, cfgd, ws, want_grad2d=True, want_abs=True, flip=flips)
     sl = oracle.theta_slices(scene["n"], 0)
     assert np.all(gflat[sl["nu"]] == 0.0) and np.all(gref[sl["nu"]] == 0.0)
-    print(assert_groups_close(gflat, gref, scene["n"], 0, gabs, label="gauss",
+    print(st, assert_groups_close(gflat, gref, scene["n"], 0, gabs, label="gauss",
                               extra=sh_basis_bound(scene["n"], 0, g2abs)))

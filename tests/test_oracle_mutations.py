@@ -64,7 +64,11 @@ MUTATIONS = [
     ("gate on signed o", C, "double g = 1.0 / (1.0 + exp(kk * (fabs(o) - t0)));",
      "double g = 1.0 / (1.0 + exp(kk * (o - t0)));"),
     ("termination after the splat instead of before", C,
-     "if (cfg->t_min > 0.0 && Tn < cfg->t_min) break;", "if (cfg->t_min > 0.0 && T < cfg->t_min) break;"),
+     "int term = Tn < cfg->t_min;", "int term = T < cfg->t_min;"),
+    ("an ambiguous alpha decision that cannot be flipped", C,
+     "if (ev < 32 && ((flip >> ev) & 1u)) include = !include;", ""),
+    ("an ambiguous termination that cannot be flipped", C,
+     "if (ev < 32 && ((flip >> ev) & 1u)) term = !term;", ""),
     ("no lower alpha clamp", C, "if (alpha < -cfg->alpha_max) { alpha = -cfg->alpha_max; clamped = 1; }", ""),
     ("Philox key constant", C, "k0 += 0x9E3779B9u;", "k0 += 0x9E3779BBu;"),
     ("Box-Muller second normal as cos", C, "z[1] = r1 * sin(2.0 * ORC_PI * u2);",

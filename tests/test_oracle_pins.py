@@ -422,6 +422,66 @@ def test_termination_keeps_transmittance_above_t_min():
     assert np.all(off["n_contrib"] >= out["n_contrib"])
 
 
+def _ambiguity_scene(a_list, px, py, nu=2.0):
+    """Components stacked on the optical axis (front to back by a small depth
+    step) whose alpha at the centre of pixel (px, py) is a_list[k], seen by a
+    48 x 40 camera."""
+    cam = inputs.look_at((0.0, 0.0, 3.0), width=48, height=40)
+
+    def build(o_list):
+        comps = [_one_component([0.0, 0.0, -0.01 * k], [0.0, 0.0, 0.0], [1.0, 0.0, 0.0, 0.0], nu, o,
+                                rgb=[0.9 - 0.2 * k, 0.3, 0.2 + 0.1 * k]) for k, o in enumerate(o_list)]
+        sc = comps[0]
+        for c in comps[1:]:
+            sc = _concat_scenes(sc, c)
+        return sc
+
+    recs = oracle.project(build([0.5] * len(a_list)), cam)
+    o_list = []
+    for rec, a in zip(recs, a_list):
+        dx, dy = px + 0.5 - rec[oracle.P["mx"]], py + 0.5 - rec[oracle.P["my"]]
+        h = rec[oracle.P["con_a"]] * dx * dx + 2 * rec[oracle.P["con_b"]] * dx * dy + rec[oracle.P["con_c"]] * dy * dy
+        o_list.append(a / oracle.t2d(h, nu))
+    return build(o_list), cam
+
+
+def test_ambiguous_decisions_flip_to_the_nearby_results():
+    """A decision within the FP32 window is flagged and counted, and flipping
+    it gives the result of a tiny perturbation across the threshold: an
+    |alpha| 1e-7 above tau (included; flipped: as if just below, excluded),
+    and a T' 1e-7 above t_min (continued; flipped: terminated before that
+    splat, i.e. the image without it)."""
+    px, py = 23, 19
+    pix = np.array([py * 48 + px])
+    up, cam = _ambiguity_scene([TAU * (1 + 1e-7)], px, py)
+    down, _ = _ambiguity_scene([TAU * (1 - 1e-7)], px, py)
+    far, _ = _ambiguity_scene([TAU * (1 - 1e-3)], px, py)
+    r_up = oracle.render(oracle.project(up, cam), cam, _cfg(), pix)
+    assert r_up["flags"][0] == oracle.F_NEAR_TAU and r_up["n_amb"][0] == 1 and r_up["n_contrib"][0] == 1
+    r_flip = oracle.render(oracle.project(up, cam), cam, _cfg(), pix, flip=[1])
+    r_down = oracle.render(oracle.project(down, cam), cam, _cfg(), pix)
+    r_far = oracle.render(oracle.project(far, cam), cam, _cfg(), pix)
+    assert r_down["flags"][0] == oracle.F_NEAR_TAU and r_far["flags"][0] == 0
+    assert r_flip["n_contrib"][0] == 0 and np.array_equal(r_flip["rgb"], r_down["rgb"])
+    assert np.array_equal(r_flip["rgb"], r_far["rgb"]) and r_flip["T"][0] == 1.0
+    # termination: T after three splats 1e-7 above t_min
+    t_min = 1e-4
+    cfg = _cfg(t_min=t_min)
+    T2 = (1.0 - 0.9) * (1.0 - 0.9)
+    sc2, _ = _ambiguity_scene([0.9, 0.9, 1.0 - t_min * (1 + 1e-7) / T2, 0.5], px, py)
+    r = oracle.render(oracle.project(sc2, cam), cam, cfg, pix)
+    assert r["flags"][0] == oracle.F_NEAR_TMIN and r["n_amb"][0] == 1
+    assert r["n_contrib"][0] == 3 and r["T"][0] == pytest.approx(t_min * (1 + 1e-7), rel=1e-9)
+    rf = oracle.render(oracle.project(sc2, cam), cam, cfg, pix, flip=[1])
+    assert rf["n_contrib"][0] == 2 and rf["T"][0] == pytest.approx(T2, rel=1e-12)
+    two, _ = _ambiguity_scene([0.9, 0.9], px, py)
+    r2 = oracle.render(oracle.project(two, cam), cam, cfg, pix)
+    assert np.allclose(rf["rgb"], r2["rgb"], rtol=1e-12, atol=0)
+    # the windows are narrow: a decision 1e-3 away is not ambiguous
+    sc3, _ = _ambiguity_scene([0.9, 0.9, 1.0 - t_min * (1 + 1e-3) / T2, 0.5], px, py)
+    assert oracle.render(oracle.project(sc3, cam), cam, cfg, pix)["flags"][0] == 0
+
+
 def test_front_component_occludes_back_component():
     cam = inputs.look_at((0.0, 0.0, 3.0), width=32, height=32)
     front = _one_component([0, 0, 0.5], [-1.5] * 3, [1, 0, 0, 0], 2.0, 0.99, rgb=[1, 0, 0])
