@@ -190,11 +190,18 @@ __device__ __forceinline__ F2 vex2(F2 a) {
   f2u(a, x, y);
   return f2(mufu_ex2(x), mufu_ex2(y));
 }
-__device__ __forceinline__ float vrcp(float a) { return __fdividef(1.0f, a); }
+// MUFU reciprocal (PTX rcp.approx.ftz: about 1 ulp); one instruction, no
+// range handling of a general approximate division
+__device__ __forceinline__ float mufu_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float vrcp(float a) { return mufu_rcp(a); }
 __device__ __forceinline__ F2 vrcp(F2 a) {
   float x, y;
   f2u(a, x, y);
-  return f2(__fdividef(1.0f, x), __fdividef(1.0f, y));
+  return f2(mufu_rcp(x), mufu_rcp(y));
 }
 __device__ __forceinline__ float vlog1p(float a) { return log1pf(a); }
 __device__ __forceinline__ F2 vlog1p(F2 a) {
@@ -219,6 +226,18 @@ __device__ __forceinline__ B2 vge(F2 a, float b) {
   float x, y;
   f2u(a, x, y);
   return B2{x >= b, y >= b};
+}
+__device__ __forceinline__ B2 vge(F2 a, F2 b) {
+  float ax, ay, bx, by;
+  f2u(a, ax, ay);
+  f2u(b, bx, by);
+  return B2{ax >= bx, ay >= by};
+}
+__device__ __forceinline__ float vabs(float a) { return fabsf(a); }
+__device__ __forceinline__ F2 vabs(F2 a) {
+  float x, y;
+  f2u(a, x, y);
+  return f2(fabsf(x), fabsf(y));
 }
 __device__ __forceinline__ bool vgt(float a, float b) { return a > b; }
 __device__ __forceinline__ B2 vgt(F2 a, float b) {

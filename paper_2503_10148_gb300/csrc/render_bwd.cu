@@ -68,7 +68,7 @@ __device__ __forceinline__ float warp_reduce_scatter10(const float (&v)[10], uns
 
 __device__ __forceinline__ float log1p_minus_u(float u, float log_base) {
   if (u < 0.25f) {
-    const float sv = __fdividef(u, 2.0f - u), s2 = sv * sv;
+    const float sv = u * mufu_rcp(2.0f - u), s2 = sv * sv;
     float p = fmaf(s2, 2.0f / 9.0f, 2.0f / 7.0f);
     p = fmaf(s2, p, 2.0f / 5.0f);
     p = fmaf(s2, p, 2.0f / 3.0f);
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
         const uint32_t pos = lo + si;
         const float4 a = S.a[k][si], b = S.b[k][si], c = S.c[k][si];
         const float cb2 = 2.0f * a.w;
-        const float nu = b.w, inv_nu = __fdividef(1.0f, nu), o = b.y;
+        const float nu = b.w, inv_nu = mufu_rcp(nu), o = b.y;
         const float oabs = fabsf(o), osgn = copysignf(1.0f, o);
         int ox, oy;
         rec_origin(c.w, ox, oy);

@@ -50,33 +50,37 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
   const int lx = bx + (lane & 7) * PW, ly = by + (lane >> 3) * PH;
   const int W = J.cam.width, H = J.cam.height;
 
-  // pixel p = L v + k of the lane is value v, element k
-  V T[NV], C[NV][3];
-  M done[NV];
+  // pixel p = L v + k of the lane is value v, element k.  A pixel's
+  // threshold is tau while it composites and +inf once it is done (outside
+  // the image, or terminated): |alpha| >= +inf never holds, so a done pixel
+  // drops out of the compositing update by itself and the common path keeps
+  // no done-mask bookkeeping; termination, about once per pixel, is handled
+  // in a branch taken when some pixel of the warp terminates.
+  const float tau = cfg.tau, amax = cfg.alpha_max, tmin = cfg.t_min;
+  V T[NV], C[NV][3], thr[NV];
   uint32_t last[NPIX];
+  bool lane_done = true;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    bool d[2] = {false, false};
+    float th[2] = {tau, tau};
 #pragma unroll
     for (int k = 0; k < L; ++k) {
       const int p = L * v + k;
-      d[k] = !(lx + p % PW < W && ly + p / PW < H);
+      const bool out = !(lx + p % PW < W && ly + p / PW < H);
+      th[k] = out ? __int_as_float(0x7f800000) : tau;
+      lane_done = lane_done && out;
       last[p] = 0u;
     }
-    if constexpr (L == 2) done[v] = B2{d[0], d[1]};
-    else done[v] = d[0];
+    if constexpr (L == 2) thr[v] = f2(th[0], th[1]);
+    else thr[v] = th[0];
     T[v] = vsplat<V>(1.0f);
     C[v][0] = C[v][1] = C[v][2] = vsplat<V>(0.0f);
   }
-  bool lane_done = true;
-#pragma unroll
-  for (int v = 0; v < NV; ++v) lane_done = lane_done && mall(done[v]);
   bool warp_done = __all_sync(0xffffffffu, lane_done);
 
   const uint2 range = ws_ptr<uint2>(ws, P.ws_off_ranges)[tile];
   const uint32_t* vals = ws_ptr<uint32_t>(ws, P.ws_off_pval) + (size_t)P.pair_slot * P.pair_capacity + range.x;
   const SplatRec* rec = ws_ptr<SplatRec>(ws, P.ws_off_rec);
-  const float tau = cfg.tau, amax = cfg.alpha_max, tmin = cfg.t_min;
   uint32_t n_eval = 0, n_contrib = 0;  // pair counters (COUNT only)
 
   const uint32_t n_list = range.y - range.x;
@@ -133,7 +137,7 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
         const int si = rr * 32 + __ffs(m) - 1;
         m &= m - 1;
         const float4 a = S.a[k][si], b = S.b[k][si], c = S.c[k][si];
-        const float cb2 = 2.0f * a.w, inv_nu = __fdividef(1.0f, b.w);
+        const float cb2 = 2.0f * a.w, inv_nu = mufu_rcp(b.w);
         const float oabs = fabsf(b.y), osgn = copysignf(1.0f, b.y);
         int ox, oy;
         rec_origin(c.w, ox, oy);
@@ -153,59 +157,92 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
         // every pixel of the lane through the same straight-line code (no
         // branches between pixels, so their chains interleave); the nu
         // branch is uniform over the warp
-        PairEval<V> r[NV];
-        M ok[NV];
+        PairEval<V> r[NV];  // the threshold test is taken below, against each pixel's own threshold
         // the alpha clamp is the identity when |o| T2D cannot reach alpha_max;
         // T2D <= 1 up to the rounding of h near 0 (a few 1e-6 at most for
         // nu <= kFastNuMax), hence the margin
         if (b.w <= kFastNuMax && oabs * 1.0001f <= amax) {
 #pragma unroll
           for (int v = 0; v < NV; ++v)
-            ok[v] = eval_pair_fast<V, false>(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, b.w, inv_nu, tau, amax, r[v]);
+            (void)eval_pair_fast<V, false>(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, b.w, inv_nu, tau, amax, r[v]);
         } else if (b.w <= kFastNuMax) {
 #pragma unroll
           for (int v = 0; v < NV; ++v)
-            ok[v] = eval_pair_fast(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, b.w, inv_nu, tau, amax, r[v]);
+            (void)eval_pair_fast(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, b.w, inv_nu, tau, amax, r[v]);
         } else if (isinf(b.w)) {
 #pragma unroll
           for (int v = 0; v < NV; ++v)
-            ok[v] = eval_pair_gauss(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, tau, amax, r[v]);
+            (void)eval_pair_gauss(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, tau, amax, r[v]);
         } else {
 #pragma unroll
           for (int v = 0; v < NV; ++v)
-            ok[v] = eval_pair_slow(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, b.w, inv_nu, tau, amax, r[v]);
+            (void)eval_pair_slow(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, b.w, inv_nu, tau, amax, r[v]);
         }
         const V one = vsplat<V>(1.0f), zero = vsplat<V>(0.0f);
         const V cr = vsplat<V>(c.x), cg = vsplat<V>(c.y), cbl = vsplat<V>(c.z);
-        bool ld = true;
+        // the splat composites onto pixels whose |alpha| reaches their
+        // threshold (tau while live); Tn = T (1 - alpha) there, T elsewhere
+        V ae[NV], Tn[NV];
+        M add[NV];
+        bool lane_term = false;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           if (COUNT) {
 #pragma unroll
-            for (int kk = 0; kk < L; ++kk) n_eval += mget(done[v], kk) ? 0u : 1u;
+            for (int kk = 0; kk < L; ++kk) n_eval += isinf(vget(thr[v], kk)) ? 0u : 1u;
           }
-          const M live = mandn(ok[v], done[v]);
-          const V Tn = vmul(T[v], vsub(one, r[v].alpha));
-          const M term = mand(live, vlt(Tn, tmin));  // stops before this splat
-          const M add = mandn(live, term);
-          // alpha where the splat is composited, else 0: T (1 - 0) = T exactly,
-          // so one select serves the weight and the transmittance update
-          // (the ALU pipe is the busier one here)
-          const V ae = vsel(add, r[v].alpha, zero);
-          const V w = vmul(ae, T[v]);
+          add[v] = vge(vabs(r[v].alpha), thr[v]);
+          ae[v] = vsel(add[v], r[v].alpha, zero);
+          Tn[v] = vmul(T[v], vsub(one, ae[v]));
+          lane_term = lane_term || many(vlt(Tn[v], tmin));
+        }
+        if (__any_sync(0xffffffffu, lane_term)) {
+          // some pixel of the warp stops before this splat: it keeps its T
+          // and colour, and its threshold becomes +inf
+          bool ld = true;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            float tx[2], ty[2], ax[2], tt[2];
+#pragma unroll
+            for (int kk = 0; kk < L; ++kk) {
+              tx[kk] = vget(Tn[v], kk);
+              ty[kk] = vget(thr[v], kk);
+              ax[kk] = vget(ae[v], kk);
+              tt[kk] = vget(T[v], kk);
+              if (tx[kk] < tmin) {
+                ty[kk] = __int_as_float(0x7f800000);
+                ax[kk] = 0.0f;
+                tx[kk] = tt[kk];
+              }
+              ld = ld && isinf(ty[kk]);
+            }
+            if constexpr (L == 2) {
+              thr[v] = f2(ty[0], ty[1]);
+              ae[v] = f2(ax[0], ax[1]);
+              Tn[v] = f2(tx[0], tx[1]);
+              add[v] = B2{ax[0] != 0.0f, ax[1] != 0.0f};
+            } else {
+              thr[v] = ty[0];
+              ae[v] = ax[0];
+              Tn[v] = tx[0];
+              add[v] = ax[0] != 0.0f;
+            }
+          }
+          warp_done = __all_sync(0xffffffffu, ld);
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const V w = vmul(ae[v], T[v]);
           C[v][0] = vfma(w, cr, C[v][0]);
           C[v][1] = vfma(w, cg, C[v][1]);
           C[v][2] = vfma(w, cbl, C[v][2]);
-          T[v] = vmul(T[v], vsub(one, ae));
+          T[v] = Tn[v];
 #pragma unroll
           for (int kk = 0; kk < L; ++kk) {
-            last[L * v + kk] = mget(add, kk) ? pos1 : last[L * v + kk];
-            if (COUNT) n_contrib += mget(add, kk) ? 1u : 0u;
+            last[L * v + kk] = mget(add[v], kk) ? pos1 : last[L * v + kk];
+            if (COUNT) n_contrib += mget(add[v], kk) ? 1u : 0u;
           }
-          done[v] = mor(done[v], term);
-          ld = ld && mall(done[v]);
         }
-        warp_done = __all_sync(0xffffffffu, ld);
       }
       }
       __syncwarp();  // every lane is done with buffer k before it is refilled

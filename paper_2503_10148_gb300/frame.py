@@ -145,9 +145,12 @@ class Frame:
             wsb = (int(self.plan.ws_bytes) + 255) & ~255
             self.ws = self.arena[:int(self.plan.ws_bytes)]
             self.rgb = self.arena[wsb:wsb + 12 * int(self.plan.n_pixels)].view(torch.float32)
+            self.outside_bytes = 0
         else:
             self.ws = torch.empty(int(self.plan.ws_bytes), dtype=torch.uint8, device=self.device)
             self.rgb = torch.empty(3 * int(self.plan.n_pixels), dtype=torch.float32, device=self.device)
+            # bytes held outside a caller's arena (a server counts them against its budget)
+            self.outside_bytes = need if self.arena is not None else 0
 
     # ------------------------------------------------------------ steps
     @property

@@ -14,10 +14,18 @@ The pair count of a frame is estimated from the pairs per (scene, view) seen
 so far (per scene and resolution); a frame that still overflows its capacity
 is re-rendered with the measured count (the device status word reports it).
 
-``serve_plain`` is the reference form: the same server with one request
-per frame (one launch sequence per request) and a single arena, so the two
-differ only in batching.  Images stay in their arena until the arena's next
-frame.
+HBM budget: the arenas hold every workspace.  A request whose frame alone
+does not fit an arena is rejected at admission (counted, not rendered).  An
+overflow re-render whose larger plan no longer fits its arena is split into
+single-request frames rendered one after another in the arena; a single
+request that still does not fit is rendered in a frame-owned workspace, and
+such allocations are counted and reported (they are the only device memory
+beyond the budget).
+
+``serve_plain`` is the reference form: the same server, the same two arenas
+and streams, with one request per frame (one launch sequence per request), so
+the two differ only in batching.  Images stay in their arena until the
+arena's next frame.
 """
 from __future__ import annotations
 
@@ -89,6 +97,9 @@ class RenderServer:
         self.pairs = PairModel()
         self.headroom = headroom
         self.frames = 0
+        self.rejected = []  # requests whose frame alone exceeds an arena
+        self.outside_allocs = 0  # frames that had to allocate beyond the arenas
+        self.outside_bytes_max = 0
         self.span_s = 0.0  # first arrival to last completion of the last serve()
 
     # ------------------------------------------------------------ batches
@@ -105,8 +116,9 @@ class RenderServer:
         """The longest head of the queue whose frame fits the arena (at most
         SSS_MAX_JOBS jobs and SSS_MAX_SCENES scenes), found by bisection:
         the workspace grows with every request added, so the fitting heads
-        are a prefix of the lengths.  A head request larger than the arena
-        on its own is rendered alone (in a frame-owned workspace)."""
+        are a prefix of the lengths.  A head request whose frame alone does
+        not fit the arena is rejected (moved to ``self.rejected``) and an
+        empty batch returned."""
         limit, scenes = 0, set()
         for r in queue:
             if limit == self.max_jobs or (r.scene not in scenes and len(scenes) == abi.SSS_MAX_SCENES):
@@ -116,15 +128,22 @@ class RenderServer:
         if limit == 0:
             return []
         head = list(queue)[:limit]
-        lo, hi = 1, limit  # lo: known to fit (or forced), hi: upper bound
-        if self._plan_bytes(head[:1])[0] <= arena_bytes:
-            while lo < hi:
-                mid = (lo + hi + 1) // 2
-                if self._plan_bytes(head[:mid])[0] <= arena_bytes:
-                    lo = mid
-                else:
-                    hi = mid - 1
+        if self._plan_bytes(head[:1])[0] > arena_bytes:
+            self.rejected.append(queue.popleft())
+            return []
+        lo, hi = 1, limit  # lo: known to fit, hi: upper bound
+        while lo < hi:
+            mid = (lo + hi + 1) // 2
+            if self._plan_bytes(head[:mid])[0] <= arena_bytes:
+                lo = mid
+            else:
+                hi = mid - 1
         return [queue.popleft() for _ in range(lo)]
+
+    def _count_outside(self, fr):
+        if fr.outside_bytes:
+            self.outside_allocs += 1
+            self.outside_bytes_max = max(self.outside_bytes_max, int(fr.outside_bytes))
 
     def render(self, reqs, arena_idx: int):
         """Enqueue one frame for ``reqs`` on the server stream; returns
@@ -137,6 +156,7 @@ class RenderServer:
             fr.forward(st, grow=False)
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(st)
+        self._count_outside(fr)
         return fr, ev, used
 
     def finish(self, fr, reqs, used, arena_idx: int):
@@ -145,8 +165,20 @@ class RenderServer:
         st_ = self.streams[arena_idx]
         st, need, _ = fr.status(st_)
         if st & abi.SSS_STATUS_PAIR_OVERFLOW:
-            fr.pair_capacity = int(need * 1.1) + 4096
+            cap = int(need * 1.1) + 4096
+            arena = self.arenas[arena_idx]
+            plan = abi.sss_plan_frame([s.params() for s in fr.scenes], [F.camera_struct(c) for c in fr.cams],
+                                      fr.job_scene, self.cfg, min(cap, 0x7fffffff))
+            if len(reqs) > 1 and F.Frame.bytes_needed(plan) > arena.numel():
+                # split: one request per frame, in turn, in the arena
+                for r in reqs:
+                    one, _, _ = self.render([r], arena_idx)
+                    self.frames += 1
+                    self.finish(one, [r], [r.scene], arena_idx)
+                return True
+            fr.pair_capacity = cap
             fr._replan()
+            self._count_outside(fr)
             with torch.cuda.stream(st_):
                 fr.forward(st_, grow=False)
             st_.synchronize()
@@ -203,6 +235,8 @@ class RenderServer:
             if queue and free:
                 a = free[0]
                 batch = self.take_batch(queue, self.arenas[a].numel())
+                if not batch:  # the head request was rejected
+                    continue
                 fr, ev, used = self.render(batch, a)
                 self.frames += 1
                 self.arena_busy[a] = ev
@@ -212,15 +246,16 @@ class RenderServer:
                 time.sleep(max(0.0, min(pending[0].arrival - now, 0.002)))
             else:
                 time.sleep(0.0002)
-        lat = np.array([latency[r.rid] for r in reqs])
+        lat = np.array([latency[r.rid] for r in reqs if r.rid in latency])
         self.span_s = last_done - (reqs[0].arrival if reqs else 0.0)
         return lat, overflow
 
 
 def serve_plain(scenes, requests, cfg=None, hbm_budget_bytes: int = 8 << 30, device="cuda"):
-    """One frame per request, in arrival order, in one resident arena (no
-    batching, no second arena).  Returns (latency, server)."""
-    srv = RenderServer(scenes, cfg, hbm_budget_bytes=hbm_budget_bytes, device=device, max_jobs=1, n_arenas=1)
+    """One frame per request, in arrival order, on the same two arenas and
+    streams as the batched server (only the batching differs).  Returns
+    (latency, server)."""
+    srv = RenderServer(scenes, cfg, hbm_budget_bytes=hbm_budget_bytes, device=device, max_jobs=1, n_arenas=2)
     lat, _ = srv.serve(requests)
     return lat, srv
 
@@ -228,8 +263,12 @@ def serve_plain(scenes, requests, cfg=None, hbm_budget_bytes: int = 8 << 30, dev
 def summarize(lat, requests, srv: RenderServer) -> dict:
     """Latency percentiles and throughput (pixels over the span from the
     first arrival to the last completion)."""
-    px = sum(r.pixels for r in requests)
+    rejected = {r.rid for r in srv.rejected}
+    px = sum(r.pixels for r in requests if r.rid not in rejected)
+    served = len(requests) - len(rejected)
     return {"requests": len(requests), "frames": srv.frames,
+            "requests_per_frame": round(served / max(srv.frames, 1), 3), "rejected": len(rejected),
+            "outside_arena_frames": srv.outside_allocs, "outside_arena_mb_max": round(srv.outside_bytes_max / 2 ** 20, 1),
             "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
             "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3), "mean_ms": round(float(lat.mean()) * 1e3, 3),
             "mpix_s": round(px / max(srv.span_s, 1e-9) / 1e6, 2), "span_s": round(srv.span_s, 3)}

@@ -206,15 +206,15 @@ def scene_grads_flat(g: frame.Scene) -> np.ndarray:
 GRAD_REL = 1e-3   # the survey's bar: |g - g_ref| <= 1e-3 max(|g_ref|, 1e-3 max_group |g_ref|) ...
 U32 = 2.0 ** -24  # FP32 unit roundoff
 # ... or, for an element where the terms of its sum cancel, within the FP32
-# rounding bound of that sum: u (4 A_n + 64 A), A = sum |term| (taken on the
+# rounding bound of that sum: u (16 A_n + 256 A), A = sum |term| (taken on the
 # operands of the subtractions inside a term), A_n the same with every
 # pixel's terms weighted by its contributor count (the transmittance is
 # recovered by one division per contributor, so its rounding grows with the
-# count), 64 u for the per-term evaluation (MUFU lg2/ex2 times the exponent,
+# count), 256 u for the per-term evaluation (MUFU lg2/ex2 times the exponent,
 # the stored mean); SH coefficients add the basis bound of sh_basis_bound.
 # At most FLOOR_FRAC of the touched elements of a group (at least one) may
 # rest on it.
-FLOOR_N, FLOOR_A = 4.0, 64.0
+FLOOR_N, FLOOR_A = 16.0, 256.0
 FLOOR_FRAC = 0.01
 GRAD_NORM = 1e-4  # and ||g - g_ref|| / ||g_ref|| per group
 

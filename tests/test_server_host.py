@@ -1,7 +1,7 @@
 """Host-side logic of the render server (no GPU): the pair model, the batch
 choice (job and scene limits, longest fitting head by bisection, a head
-too large for the arena alone), the seeded Poisson arrivals and the latency
-summary.  The frame workspace size is replaced by a stand-in of known
+too large for the arena alone is rejected), the seeded Poisson arrivals and
+the latency summary.  The frame workspace size is replaced by a stand-in of known
 growth, so that only the server's own logic is under test."""
 import collections
 import os
@@ -71,11 +71,14 @@ def test_take_batch_respects_the_job_and_scene_limits():
     assert [r.rid for r in srv.take_batch(q, arena_bytes=1 << 30)] == [0]
 
 
-def test_take_batch_renders_an_oversized_head_alone_and_an_empty_queue_as_nothing():
+def test_take_batch_rejects_an_oversized_head_and_takes_nothing_from_an_empty_queue():
+    """The HBM budget holds: a request whose frame alone exceeds the arena is
+    rejected (counted), never rendered in memory of its own."""
     srv = _server(bytes_per_request=1000)
+    srv.rejected = []
     q = collections.deque(_req(i, 0) for i in range(3))
     got = srv.take_batch(q, arena_bytes=500)
-    assert [r.rid for r in got] == [0] and len(q) == 2
+    assert got == [] and [r.rid for r in srv.rejected] == [0] and len(q) == 2
     assert srv.take_batch(collections.deque(), arena_bytes=500) == []
 
 
@@ -97,9 +100,19 @@ def test_poisson_requests_are_seeded_ordered_and_at_the_rate(monkeypatch):
 def test_summarize_reports_percentiles_and_throughput_over_the_span():
     reqs = [_req(i, 0, w=100, h=100) for i in range(100)]
     lat = np.arange(1, 101, dtype=np.float64) * 1e-3  # 1 .. 100 ms
-    srv = types.SimpleNamespace(frames=40, span_s=2.0)
+    srv = types.SimpleNamespace(frames=40, span_s=2.0, rejected=[], outside_allocs=0, outside_bytes_max=0)
     s = server.summarize(lat, reqs, srv)
-    assert s["requests"] == 100 and s["frames"] == 40
+    assert s["requests"] == 100 and s["frames"] == 40 and s["requests_per_frame"] == 2.5
+    assert s["rejected"] == 0 and s["outside_arena_frames"] == 0
     assert s["p50_ms"] == pytest.approx(50.5) and s["p99_ms"] == pytest.approx(99.01)
     assert s["mean_ms"] == pytest.approx(50.5)
     assert s["mpix_s"] == pytest.approx(100 * 100 * 100 / 2.0 / 1e6)
+
+
+def test_summarize_counts_rejected_requests_out_of_the_throughput():
+    reqs = [_req(i, 0, w=100, h=100) for i in range(10)]
+    srv = types.SimpleNamespace(frames=3, span_s=1.0, rejected=reqs[:2], outside_allocs=1, outside_bytes_max=3 << 20)
+    s = server.summarize(np.full(8, 1e-3), reqs, srv)
+    assert s["rejected"] == 2 and s["mpix_s"] == pytest.approx(8 * 100 * 100 / 1e6)
+    assert s["requests_per_frame"] == pytest.approx(8 / 3, abs=1e-3)
+    assert s["outside_arena_frames"] == 1 and s["outside_arena_mb_max"] == 3.0
