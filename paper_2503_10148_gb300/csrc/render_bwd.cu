@@ -9,7 +9,9 @@
 // T_k (rgb_k - B_k), and B follows the blend B_{k-1} = alpha_k rgb_k +
 // (1 - alpha_k) B_k from B = bg at the back: no division, and the rounding of
 // the recovered T_k scales the (often small) difference instead of its two
-// large operands.  For a contributor k:
+// large operands.  The kernel carries -alpha (the records are evaluated with
+// the opacity's sign flipped) and -g . B, which saves a subtraction per
+// pixel.  For a contributor k:
 //   dL/drgb   = alpha T_k g                               (g = dL/dC)
 //   dL/dalpha = T_k g . (rgb - B)
 //   dL/do     = dL/dalpha T2D,  dL/dT2D = dL/dalpha o   (unless alpha was clamped)
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
   const uint32_t* Lf = ws_ptr<uint32_t>(ws, P.ws_off_last);
   const float* gimg = dl_drgb + 3 * (size_t)J.pix_base;
   // pixel p = L v + k of the lane is value v, element k
-  V T[NV], Sg[NV], g[NV][3];  // Sg = dL/dC . (colour behind)
+  V T[NV], Sg[NV], g[NV][3];  // Sg = -dL/dC . (colour behind)
   uint32_t last[NPIX];
   uint32_t lane_max = 0;
 #pragma unroll
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
     float sg[2];
 #pragma unroll
     for (int kk = 0; kk < L; ++kk)
-      sg[kk] = fmaf(gg[kk][0], cfg.bg[0], fmaf(gg[kk][1], cfg.bg[1], gg[kk][2] * cfg.bg[2]));
+      sg[kk] = -fmaf(gg[kk][0], cfg.bg[0], fmaf(gg[kk][1], cfg.bg[1], gg[kk][2] * cfg.bg[2]));
     if constexpr (L == 2) {
       T[v] = f2(t[0], t[1]);
       Sg[v] = f2(sg[0], sg[1]);
@@ -266,19 +268,19 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
         if (nu <= kFastNuMax && oabs * 1.0001f <= amax) {
 #pragma unroll
           for (int v = 0; v < NV; ++v)
-            ok[v] = eval_pair_fast<V, false>(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, nu, inv_nu, tau, amax, r[v]);
+            ok[v] = eval_pair_fast<V, false>(dx[v], dy[v], a.z, cb2, b.x, oabs, -osgn, nu, inv_nu, tau, amax, r[v]);
         } else if (nu <= kFastNuMax) {
 #pragma unroll
           for (int v = 0; v < NV; ++v)
-            ok[v] = eval_pair_fast(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, nu, inv_nu, tau, amax, r[v]);
+            ok[v] = eval_pair_fast(dx[v], dy[v], a.z, cb2, b.x, oabs, -osgn, nu, inv_nu, tau, amax, r[v]);
         } else if (isinf(nu)) {
 #pragma unroll
           for (int v = 0; v < NV; ++v)
-            ok[v] = eval_pair_gauss(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, tau, amax, r[v]);
+            ok[v] = eval_pair_gauss(dx[v], dy[v], a.z, cb2, b.x, oabs, -osgn, tau, amax, r[v]);
         } else {
 #pragma unroll
           for (int v = 0; v < NV; ++v)
-            ok[v] = eval_pair_slow(dx[v], dy[v], a.z, cb2, b.x, oabs, osgn, nu, inv_nu, tau, amax, r[v]);
+            ok[v] = eval_pair_slow(dx[v], dy[v], a.z, cb2, b.x, oabs, -osgn, nu, inv_nu, tau, amax, r[v]);
         }
         // per-lane sums: rgb (v7..9), st = dL/dalpha T2D (v5 = dL/do), st
         // times the nu factor (v6 / o) and, per pixel, q = st / (1 + h/nu),
@@ -296,10 +298,10 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
           else before = pos < last[v];
           const M live = mand(ok[v], before);
           any = any || many(live);
-          const V al = vsel(live, r[v].alpha, zero);
+          const V al = vsel(live, r[v].alpha, zero);  // -alpha (the record's sign flipped)
           // T_k = T_{k+1} / (1 - alpha); with al = 0 off the live pixels the
           // MUFU reciprocal of 1 is exactly 1, so T is kept bit for bit
-          const V Tk = vmul(T[v], vrcp(vsub(one, al)));
+          const V Tk = vmul(T[v], vrcp(vadd(one, al)));
           T[v] = Tk;
           const V w = vmul(al, Tk);  // 0 unless live
           r7 = vfma(w, g[v][0], r7);
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
           // dL/dalpha = T_k dL/dC . (rgb - B) with B the colour behind; only
           // its projection on dL/dC is needed: Sg = dL/dC . B, and
           // B <- alpha rgb + (1 - alpha) B gives Sg <- Sg + alpha (g.rgb - Sg)
-          const V gdiff = vsub(vfma(g[v][0], cr, vfma(g[v][1], cg, vmul(g[v][2], cbl))), Sg[v]);
+          const V gdiff = vfma(g[v][0], cr, vfma(g[v][1], cg, vfma(g[v][2], cbl, Sg[v])));
           Sg[v] = vfma(al, gdiff, Sg[v]);
           const V dl_da = vsel(mandn(live, r[v].clamped), vmul(gdiff, Tk), zero);
           const V st = vmul(dl_da, r[v].t2d);
@@ -376,9 +378,9 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
         vv[4] = kq * m5;
         vv[5] = vsum(s5);
         vv[6] = o * vsum(s6);
-        vv[7] = vsum(r7);
-        vv[8] = vsum(r8);
-        vv[9] = vsum(r9);
+        vv[7] = -vsum(r7);
+        vv[8] = -vsum(r8);
+        vv[9] = -vsum(r9);
         if (__any_sync(0xffffffffu, any)) {
           int slot;
           const float tot = warp_reduce_scatter10(vv, lane, &slot);
