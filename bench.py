@@ -71,9 +71,11 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-serve", action="store_true", help="skip the render-server leg")
-    ap.add_argument("--serve-seconds", type=float, default=10.0, help="Poisson arrival window of the server leg")
-    ap.add_argument("--serve-tile", default="32x32",
-                    help="WxH list tile of the server leg (single views of mixed sizes: latency, not throughput)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="Poisson arrival window of the server leg at 200 req/s (the higher rates use half)")
+    ap.add_argument("--serve-tile", default="auto",
+                    help="list tile of the server leg: 'auto' (per frame, the tuned tile of its largest view) "
+                         "or WxH for every frame")
     ap.add_argument("--workload", default="clusters_1p5m_4views", choices=sorted(WORKLOADS),
                     help="smaller seeded workloads exist for profiling; the benchmark line uses the default")
     return ap.parse_args()
@@ -494,8 +496,12 @@ def run_ours(args):
     result["relocate"] = relocate_leg(scene_np, device)
     result["inference"] = inference_leg(scene_np, cams, device, cfg)
     if not args.no_serve:
-        stw, sth = (int(v) for v in args.serve_tile.split("x"))
-        result["serve"] = serve_leg(device, F.make_cfg(tile_w=stw, tile_h=sth), args.serve_seconds)
+        if args.serve_tile == "auto":
+            from paper_2503_10148_gb300 import autotune
+            result["serve"] = serve_leg(device, F.make_cfg(), args.serve_seconds, tile_of=autotune.serve_tile)
+        else:
+            stw, sth = (int(v) for v in args.serve_tile.split("x"))
+            result["serve"] = serve_leg(device, F.make_cfg(tile_w=stw, tile_h=sth), args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -572,35 +578,42 @@ def inference_leg(scene_np, cams, device, cfg, reps: int = 50) -> dict:
 # ------------------------------------------------------------------ serving
 
 SERVE_WORKLOAD = ("3 resident scenes (200k, 1M, 3M components, clusters + ground distribution), Poisson "
-                  "arrivals at 200 req/s, random camera on the radius-3 sphere, resolution uniform over "
-                  "{256x256, 800x800, 1297x840, 1920x1080}; forward render per request")
+                  "arrivals at 200 req/s (the configured rate) and at 500 and 1000 req/s, random camera on the "
+                  "radius-3 sphere, resolution uniform over {256x256, 800x800, 1297x840, 1920x1080}; forward "
+                  "render per request; then every request of the 200 req/s run arriving at once (burst)")
+SERVE_RATES = (200.0, 500.0, 1000.0)
 
 
-def serve_leg(device, cfg, seconds: float) -> dict:
-    """Render server (batched multi-scene frames, two arenas) against one
-    frame per request, on the same seeded requests: latency at 200 req/s,
-    then throughput with every request arriving at once."""
+def serve_leg(device, cfg, seconds: float, tile_of=None) -> dict:
+    """Render server (batched multi-scene frames) against one frame per
+    request, on the same two arenas, streams and tile policy and the same
+    seeded requests: latency at each arrival rate, then throughput with every
+    request arriving at once."""
     import dataclasses
     import torch
     from paper_2503_10148_gb300 import frame as F, inputs, server
     scenes = [F.Scene.from_numpy(s, device) for s in inputs.serving_scenes()]
-    reqs = server.poisson_requests(len(scenes), rate=200.0, duration=seconds, seed=21)
     budget = 16 << 30
-    out = {"workload": SERVE_WORKLOAD, "hbm_budget_gb": budget >> 30, "arrival_window_s": seconds,
-           "tile": f"{cfg.tile_w}x{cfg.tile_h}"}
-    for name, burst in (("poisson", False), ("burst", True)):
-        rs = [dataclasses.replace(r, arrival=0.0) for r in reqs] if burst else reqs
-        srv = server.RenderServer(scenes, cfg, hbm_budget_bytes=budget, device=device)
+    out = {"workload": SERVE_WORKLOAD, "hbm_budget_gb": budget >> 30,
+           "tile": "per frame: the tuned tile of its largest view" if tile_of else f"{cfg.tile_w}x{cfg.tile_h}"}
+    runs = []
+    for rate in SERVE_RATES:
+        window = seconds if rate == SERVE_RATES[0] else seconds / 2
+        reqs = server.poisson_requests(len(scenes), rate=rate, duration=window, seed=21)
+        runs.append((f"poisson_{int(rate)}", reqs, window))
+    runs.append(("burst", [dataclasses.replace(r, arrival=0.0) for r in runs[0][1]], 0.0))
+    for name, rs, window in runs:
+        srv = server.RenderServer(scenes, cfg, hbm_budget_bytes=budget, device=device, tile_of=tile_of)
         lat, ov = srv.serve(rs)
         b = server.summarize(lat, rs, srv)
         b["overflow_rerenders"] = ov
         del srv
         torch.cuda.empty_cache()
-        lat_p, psrv = server.serve_plain(scenes, rs, cfg, hbm_budget_bytes=budget, device=device)
+        lat_p, psrv = server.serve_plain(scenes, rs, cfg, hbm_budget_bytes=budget, device=device, tile_of=tile_of)
         p = server.summarize(lat_p, rs, psrv)
         del psrv
         torch.cuda.empty_cache()
-        out[name] = {"batched": b, "plain": p}
+        out[name] = {"arrival_window_s": window, "batched": b, "plain": p}
     return out
 
 

@@ -207,7 +207,10 @@ typedef struct sss_frame_plan {
                             [2] status bits, [3] entries, [4..5] uint64
                             contributing (splat, pixel) pairs and [6..7]
                             uint64 evaluated pairs of the forwards run with
-                            cfg.count_pairs = 1; reset by sss_bin          */
+                            cfg.count_pairs = 1, [8..9] the work-item
+                            counter and finished-warp count of the
+                            persistent render kernels (back to 0 after each
+                            render launch); reset by sss_bin                 */
   int32_t sort_blocks;   /* persistent CTAs used by the sorts and scans     */
   uint32_t pair_slot;    /* which half of pkey/pval holds the sorted pairs  */
 } sss_frame_plan;
@@ -254,7 +257,10 @@ int sss_sort(const sss_frame_plan* plan, void* ws, sss_stream_t stream);
  *   skipped when |o T2D| < tau; C += rgb alpha T; T *= (1 - alpha); stop
  *   before a splat that would make T < t_min; finally C += T bg.
  * out_rgb: device float[3 * n_pixels], [3][H][W] per job at 3*pix_base[j].
- * Also writes the final T and last-contributor positions into ws. */
+ * Also writes the final T and last-contributor positions into ws.  Runs as
+ * a persistent grid (as many CTAs as are resident at once) whose warps take
+ * (sub-tile, warp box) items from a counter in the workspace; two render
+ * launches on one workspace must therefore not overlap on the GPU. */
 int sss_render_fwd(const sss_frame_plan* plan, void* ws, float* out_rgb, sss_stream_t stream);
 
 /* a5. Given dL/dC (device float[3 * n_pixels], same layout as out_rgb),

@@ -89,3 +89,63 @@ def tune(name: str, scene, cams, targets, candidates=None, steps: int = 5, devic
               "candidates": {f"{a}x{c}/{d}": round(m, 3) for m, a, c, d in results}}
     store(name, choice, path)
     return choice
+
+
+# ---------------------------------------------------------------- serving
+SERVE_TILES = (16, 32, 64, 128)
+SERVE_KEY = "serving"
+
+
+def tune_serve(scenes, resolutions, cams_per_res: int = 3, reps: int = 5, device="cuda", log=print,
+               path: str = CACHE, seed: int = 5) -> dict:
+    """For each serving resolution, the square list tile whose single-view
+    frame (project -> bin -> sort -> render_fwd) is fastest, averaged over the
+    resident scenes and a few seeded cameras on the radius-3 sphere.  A small
+    view wants small tiles (more warps in flight, shorter lists per warp), a
+    large one large tiles (fewer pairs to sort).  Stored under "serving"."""
+    import numpy as np
+    import torch
+
+    from . import frame as F
+    from . import inputs
+
+    rng = np.random.default_rng(seed)
+    table = {}
+    for (w, h) in resolutions:
+        cams = [F.f32_camera(inputs.random_sphere_camera(rng, width=w, height=h)) for _ in range(cams_per_res)]
+        ms = {}
+        for t in SERVE_TILES:
+            cfg = F.make_cfg(tile_w=t, tile_h=t, batch=32)
+            acc = []
+            for sc in scenes:
+                for cam in cams:
+                    fr = F.Frame([sc], [cam], cfg=cfg, device=device)
+                    fr.forward(grow=True)
+                    torch.cuda.synchronize(device)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for _ in range(reps):
+                        fr.forward(grow=False)
+                    e1.record()
+                    torch.cuda.synchronize(device)
+                    acc.append(e0.elapsed_time(e1) / reps)
+                    del fr
+            ms[t] = float(np.mean(acc))
+            log(f"autotune serving {w}x{h}: tile {t}x{t}: {ms[t]:.3f} ms per view")
+        best = min(ms, key=ms.get)
+        table[f"{w}x{h}"] = {"tile": best, "ms": {str(k): round(v, 4) for k, v in ms.items()}}
+    choice = {"tiles": table}
+    store(SERVE_KEY, choice, path)
+    return choice
+
+
+def serve_tile(width: int, height: int, default: int = 32) -> int:
+    """The tuned list tile (square side) for a view of width x height: that
+    of the tuned resolution nearest in pixel count, or `default` when nothing
+    is tuned."""
+    c = cached(SERVE_KEY)
+    if not c or not c.get("tiles"):
+        return default
+    px = width * height
+    best = min(c["tiles"].items(), key=lambda kv: abs(int(kv[0].split("x")[0]) * int(kv[0].split("x")[1]) - px))
+    return int(best[1]["tile"])

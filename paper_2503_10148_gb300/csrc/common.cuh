@@ -39,7 +39,36 @@ __host__ __device__ inline const T* ws_ptr(const void* ws, size_t off) {
   return reinterpret_cast<const T*>(static_cast<const char*>(ws) + off);
 }
 
-enum CtrlWord : int { kCtrlPairsNeeded = 0, kCtrlPairsSorted = 1, kCtrlStatus = 2, kCtrlEntries = 3 };
+enum CtrlWord : int { kCtrlPairsNeeded = 0, kCtrlPairsSorted = 1, kCtrlStatus = 2, kCtrlEntries = 3, kCtrlQueue = 8 };
+
+// End of a persistent render launch for the calling warp: counts the warp as
+// finished (queue[1]); the last of the grid's warps resets the item counter
+// and the finished count, so the next launch starts from item 0.  Every warp
+// has taken its last item before it counts itself, so nothing reads the
+// counter after the reset.
+__device__ __forceinline__ void queue_retire(uint32_t* queue, unsigned lane) {
+  if (lane == 0) {
+    const uint32_t total = gridDim.x * (blockDim.x >> 5);
+    if (atomicAdd(queue + 1, 1u) == total - 1) {
+      queue[0] = 0u;
+      queue[1] = 0u;
+    }
+  }
+}
+
+// CTAs of a persistent launch: as many as are resident at once on the
+// device (occupancy of `kernel` at `threads` threads per CTA), at most
+// `max_ctas`.
+template <class K>
+inline unsigned persistent_grid(K kernel, int threads, uint32_t max_ctas) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1) {
+    (void)cudaGetLastError();
+    per_sm = 1;
+  }
+  const uint32_t g = (uint32_t)per_sm * (uint32_t)device_sm_count();
+  return g < max_ctas ? g : (max_ctas ? max_ctas : 1u);
+}
 
 // ------------------------------------------------------------ job lookup
 // Largest j in [0, n) with base(j) <= x; bases are non-decreasing.

@@ -88,28 +88,28 @@ __device__ __forceinline__ F2 log1p_minus_u(F2 u, F2 log_base) {
   return vsel(vlt(u, 0.25f), series, vsub(log_base, u));
 }
 
+// One work item: warp (item & 1) of CTA (item >> 1) of the grid form, i.e.
+// one warp box of one sub-tile.  S is the calling warp's staging buffer.
 template <int PW, int PH, int R, bool PAPER_NU>
-__global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const sss_frame_plan P, void* ws,
-                                                                           const float* __restrict__ dl_drgb) {
+__device__ __forceinline__ void bwd_item(const sss_frame_plan& P, void* ws, const float* __restrict__ dl_drgb,
+                                         uint32_t item, WarpBuf<R>& S) {
   constexpr int NPIX = PW * PH;
   constexpr uint32_t B = 32 * R;  // records per warp and round
   constexpr int TW = 16 * PW, TH = 16 * PH;
   constexpr int L = LaneVec<NPIX>::L, NV = LaneVec<NPIX>::NV;
   using V = typename std::conditional<L == 2, F2, float>::type;
   using M = MaskT<V>;
-  __shared__ WarpBuf<R> s_wb[2];
-
   // sub-tiles of the list tile as in the forward; warp w of a sub-tile's
   // 2 x 4 layout
   const sss_raster_cfg& cfg = P.cfg;
   const uint32_t SX = (uint32_t)cfg.tile_w / TW, SY = (uint32_t)cfg.tile_h / TH;
-  const uint32_t cta = blockIdx.x >> 2, tile = cta / (SX * SY), sub = cta - tile * (SX * SY);
-  WarpBuf<R>& S = s_wb[threadIdx.x >> 5];
+  const uint32_t blk = item >> 1;
+  const uint32_t cta = blk >> 2, tile = cta / (SX * SY), sub = cta - tile * (SX * SY);
   const int j = job_of_tile(P, tile);
   const sss_job_desc& J = P.jobs[j];
   const uint32_t lt = tile - J.tile_base;
   const int tx = (int)(lt % (uint32_t)J.tiles_x), ty = (int)(lt / (uint32_t)J.tiles_x);
-  const int warp = (int)((blockIdx.x & 3u) << 1) | (int)(threadIdx.x >> 5);
+  const int warp = (int)((blk & 3u) << 1) | (int)(item & 1u);
   const unsigned lane = threadIdx.x & 31;
   const int bx = tx * cfg.tile_w + (int)(sub % SX) * TW + (warp & 1) * 8 * PW;
   const int by = ty * cfg.tile_h + (int)(sub / SX) * TH + (warp >> 1) * 4 * PH;
@@ -394,10 +394,33 @@ __global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const
   }
 }
 
+// Persistent, as the forward: warps take work items from the workspace's
+// counter until none is left; the last one resets it.
+template <int PW, int PH, int R, bool PAPER_NU>
+__global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const sss_frame_plan P, void* ws,
+                                                                           const float* __restrict__ dl_drgb,
+                                                                           uint32_t n_items) {
+  __shared__ WarpBuf<R> s_wb[2];
+  WarpBuf<R>& S = s_wb[threadIdx.x >> 5];
+  uint32_t* queue = ws_ptr<uint32_t>(ws, P.ws_off_ctrl) + kCtrlQueue;
+  const unsigned lane = threadIdx.x & 31;
+  for (;;) {
+    uint32_t item = 0;
+    if (lane == 0) item = atomicAdd(queue, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= n_items) break;
+    bwd_item<PW, PH, R, PAPER_NU>(P, ws, dl_drgb, item, S);
+  }
+  queue_retire(queue, lane);
+}
+
 template <int PW, int PH, int R, bool PAPER_NU>
 int launch_batch(const sss_frame_plan& P, void* ws, const float* g, cudaStream_t st) {
   const unsigned subs = (unsigned)(P.cfg.tile_w / (16 * PW)) * (unsigned)(P.cfg.tile_h / (16 * PH));
-  k_render_bwd<PW, PH, R, PAPER_NU><<<4 * subs * P.n_tiles, 64, 0, st>>>(P, ws, g);
+  const uint32_t n_items = 8u * subs * P.n_tiles;  // warps of the grid form
+  if (n_items == 0) return SSS_OK;
+  const unsigned grid = persistent_grid(k_render_bwd<PW, PH, R, PAPER_NU>, 64, n_items / 2);
+  k_render_bwd<PW, PH, R, PAPER_NU><<<grid, 64, 0, st>>>(P, ws, g, n_items);
   SSS_LAUNCH_CHECK();
   return SSS_OK;
 }

@@ -2,9 +2,11 @@
 // (Sec. 3.4 Eq. SSS_color; signed opacity Sec. 3.3).
 //
 // A render sub-tile of (16 PW) x (16 PH) pixels (at most 32 x 32; a list
-// tile of the binning may hold several) is covered by eight warps laid out
-// 2 x 4, run as four CTAs of two warps; warp w owns an (8 PW) x (4 PH) box
-// and lane l a PW x PH block of pixels inside it.  Warps are
+// tile of the binning may hold several) is covered by eight warp boxes laid
+// out 2 x 4; warp box w is (8 PW) x (4 PH) pixels and lane l owns a PW x PH
+// block of pixels inside it.  The kernel is persistent: a grid of as many
+// two-warp CTAs as fit on the device, whose warps take warp boxes from a
+// work counter in index order until none is left.  Warps are
 // independent (no CTA barrier): each walks the tile's list in rounds of 32
 // or 64 records (cfg.batch; one or two 48-byte records per lane) gathered
 // by entry index with cp.async into the warp's own double buffer (the next
@@ -22,25 +24,26 @@
 namespace sss {
 namespace {
 
+// One work item: warp (item & 1) of CTA (item >> 1) of the grid form, i.e.
+// one warp box of one sub-tile.  S is the calling warp's staging buffer.
 template <int PW, int PH, int R, bool COUNT>
-__global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, void* ws, float* __restrict__ out_rgb) {
+__device__ __forceinline__ void fwd_item(const sss_frame_plan& P, void* ws, float* __restrict__ out_rgb, uint32_t item,
+                                         WarpBuf<R>& S) {
   constexpr int NPIX = PW * PH;
   constexpr uint32_t B = 32 * R;  // records per warp and round
   constexpr int TW = 16 * PW, TH = 16 * PH;
   constexpr int L = LaneVec<NPIX>::L, NV = LaneVec<NPIX>::NV;
   using V = typename std::conditional<L == 2, F2, float>::type;
   using M = MaskT<V>;
-  __shared__ WarpBuf<R> s_wb[2];
-
   // a list tile of cfg.tile_w x cfg.tile_h pixels is rendered as SX x SY
   // sub-tiles of TW x TH, each by four CTAs of two warps; warp w of the
   // sub-tile's 2 x 4 layout.  Every sub-tile walks the whole list of its
   // tile (the per-warp cull drops what misses its box).
   const sss_raster_cfg& cfg = P.cfg;
   const uint32_t SX = (uint32_t)cfg.tile_w / TW, SY = (uint32_t)cfg.tile_h / TH;
-  const uint32_t cta = blockIdx.x >> 2, tile = cta / (SX * SY), sub = cta - tile * (SX * SY);
-  const int warp = (int)((blockIdx.x & 3u) << 1) | (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
-  WarpBuf<R>& S = s_wb[threadIdx.x >> 5];
+  const uint32_t blk = item >> 1;
+  const uint32_t cta = blk >> 2, tile = cta / (SX * SY), sub = cta - tile * (SX * SY);
+  const int warp = (int)((blk & 3u) << 1) | (int)(item & 1u), lane = threadIdx.x & 31;
   const int j = job_of_tile(P, tile);
   const sss_job_desc& J = P.jobs[j];
   const uint32_t lt = tile - J.tile_base;
@@ -278,13 +281,41 @@ __global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, v
   }
 }
 
+// Persistent: a grid of as many CTAs as fit on the device at once, whose
+// warps take work items from a counter in the workspace (control word 8) in
+// index order -- the order of the grid form, which keeps neighbouring tiles'
+// records in L2 together -- until none is left.  No warp waits on another.
+// The last warp to finish (control word 9 counts them) resets both words, so
+// the next render launch on the workspace starts from item 0.
+template <int PW, int PH, int R, bool COUNT>
+__global__ void __launch_bounds__(64, 16) k_render_fwd(const sss_frame_plan P, void* ws, float* __restrict__ out_rgb,
+                                                       uint32_t n_items) {
+  __shared__ WarpBuf<R> s_wb[2];
+  WarpBuf<R>& S = s_wb[threadIdx.x >> 5];
+  uint32_t* queue = ws_ptr<uint32_t>(ws, P.ws_off_ctrl) + kCtrlQueue;
+  const unsigned lane = threadIdx.x & 31;
+  for (;;) {
+    uint32_t item = 0;
+    if (lane == 0) item = atomicAdd(queue, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= n_items) break;
+    fwd_item<PW, PH, R, COUNT>(P, ws, out_rgb, item, S);
+  }
+  queue_retire(queue, lane);
+}
+
 template <int PW, int PH, int R>
 int launch_depth(const sss_frame_plan& P, void* ws, float* out, cudaStream_t st) {
   const unsigned subs = (unsigned)(P.cfg.tile_w / (16 * PW)) * (unsigned)(P.cfg.tile_h / (16 * PH));
-  if (P.cfg.count_pairs)
-    k_render_fwd<PW, PH, R, true><<<4 * subs * P.n_tiles, 64, 0, st>>>(P, ws, out);
-  else
-    k_render_fwd<PW, PH, R, false><<<4 * subs * P.n_tiles, 64, 0, st>>>(P, ws, out);
+  const uint32_t n_items = 8u * subs * P.n_tiles;  // warps of the grid form
+  if (n_items == 0) return SSS_OK;
+  if (P.cfg.count_pairs) {
+    const unsigned grid = persistent_grid(k_render_fwd<PW, PH, R, true>, 64, n_items / 2);
+    k_render_fwd<PW, PH, R, true><<<grid, 64, 0, st>>>(P, ws, out, n_items);
+  } else {
+    const unsigned grid = persistent_grid(k_render_fwd<PW, PH, R, false>, 64, n_items / 2);
+    k_render_fwd<PW, PH, R, false><<<grid, 64, 0, st>>>(P, ws, out, n_items);
+  }
   SSS_LAUNCH_CHECK();
   return SSS_OK;
 }

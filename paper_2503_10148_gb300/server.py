@@ -66,18 +66,19 @@ def poisson_requests(n_scenes: int, rate: float, duration: float, seed: int, res
 
 
 class PairModel:
-    """Pairs per (scene, view) seen so far, by scene and resolution."""
+    """Pairs per (scene, view) seen so far, by scene, resolution and list
+    tile."""
 
     def __init__(self, default_per_entry: float = 8.0):
         self.rate = {}
         self.default = default_per_entry
 
-    def estimate(self, scene_idx: int, n: int, w: int, h: int) -> int:
-        r = self.rate.get((scene_idx, w, h), self.default)
+    def estimate(self, scene_idx: int, n: int, w: int, h: int, tile: int = 0) -> int:
+        r = self.rate.get((scene_idx, w, h, tile), self.default)
         return int(r * n)
 
-    def observe(self, scene_idx: int, n: int, w: int, h: int, pairs: int):
-        key = (scene_idx, w, h)
+    def observe(self, scene_idx: int, n: int, w: int, h: int, pairs: int, tile: int = 0):
+        key = (scene_idx, w, h, tile)
         old = self.rate.get(key)
         val = pairs / max(n, 1)
         self.rate[key] = val if old is None else max(val, 0.8 * old + 0.2 * val)
@@ -85,9 +86,13 @@ class PairModel:
 
 class RenderServer:
     def __init__(self, scenes, cfg=None, hbm_budget_bytes: int = 8 << 30, headroom: float = 1.3, device="cuda",
-                 max_jobs: int = abi.SSS_MAX_JOBS, n_arenas: int = 2):
+                 max_jobs: int = abi.SSS_MAX_JOBS, n_arenas: int = 2, tile_of=None):
+        """``tile_of``: optional (width, height) -> square list tile side; a
+        frame then takes the tile of its largest view (small views render
+        faster on small tiles, large ones on large tiles), else ``cfg``'s."""
         self.scenes = list(scenes)
         self.cfg = cfg if cfg is not None else F.make_cfg()
+        self.tile_of = tile_of
         self.device = torch.device(device)
         self.max_jobs = max(1, min(int(max_jobs), abi.SSS_MAX_JOBS))
         per = hbm_budget_bytes // n_arenas
@@ -103,13 +108,24 @@ class RenderServer:
         self.span_s = 0.0  # first arrival to last completion of the last serve()
 
     # ------------------------------------------------------------ batches
+    def frame_cfg(self, reqs):
+        """The raster options of a frame of ``reqs``."""
+        if self.tile_of is None:
+            return self.cfg
+        big = max(reqs, key=lambda r: r.cam.width * r.cam.height)
+        t = int(self.tile_of(big.cam.width, big.cam.height))
+        c = type(self.cfg).from_buffer_copy(self.cfg)
+        c.tile_w = c.tile_h = t
+        return c
+
     def _plan_bytes(self, reqs):
         used = sorted({r.scene for r in reqs})
         remap = {s: i for i, s in enumerate(used)}
+        cfg = self.frame_cfg(reqs)
         cap = 4096 + int(self.headroom * sum(
-            self.pairs.estimate(r.scene, self.scenes[r.scene].n, r.cam.width, r.cam.height) for r in reqs))
+            self.pairs.estimate(r.scene, self.scenes[r.scene].n, r.cam.width, r.cam.height, cfg.tile_w) for r in reqs))
         plan = abi.sss_plan_frame([self.scenes[s].params() for s in used], [F.camera_struct(r.cam) for r in reqs],
-                                  [remap[r.scene] for r in reqs], self.cfg, min(cap, 0x7fffffff))
+                                  [remap[r.scene] for r in reqs], cfg, min(cap, 0x7fffffff))
         return F.Frame.bytes_needed(plan), used, remap, cap
 
     def take_batch(self, queue: collections.deque, arena_bytes: int):
@@ -152,7 +168,8 @@ class RenderServer:
         st = self.streams[arena_idx]
         with torch.cuda.stream(st):
             fr = F.Frame([self.scenes[s] for s in used], [r.cam for r in reqs], [remap[r.scene] for r in reqs],
-                         cfg=self.cfg, pair_capacity=cap, device=self.device, arena=self.arenas[arena_idx])
+                         cfg=self.frame_cfg(reqs), pair_capacity=cap, device=self.device,
+                         arena=self.arenas[arena_idx])
             fr.forward(st, grow=False)
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(st)
@@ -168,7 +185,7 @@ class RenderServer:
             cap = int(need * 1.1) + 4096
             arena = self.arenas[arena_idx]
             plan = abi.sss_plan_frame([s.params() for s in fr.scenes], [F.camera_struct(c) for c in fr.cams],
-                                      fr.job_scene, self.cfg, min(cap, 0x7fffffff))
+                                      fr.job_scene, fr.cfg, min(cap, 0x7fffffff))
             if len(reqs) > 1 and F.Frame.bytes_needed(plan) > arena.numel():
                 # split: one request per frame, in turn, in the arena
                 for r in reqs:
@@ -189,7 +206,7 @@ class RenderServer:
         ends_np = cum[ends].cpu().numpy()
         counts = np.diff(np.concatenate([[0], ends_np]))
         for r, c in zip(reqs, counts):
-            self.pairs.observe(r.scene, self.scenes[r.scene].n, r.cam.width, r.cam.height, int(c))
+            self.pairs.observe(r.scene, self.scenes[r.scene].n, r.cam.width, r.cam.height, int(c), fr.cfg.tile_w)
         return bool(st & abi.SSS_STATUS_PAIR_OVERFLOW)
 
     # ------------------------------------------------------------ serving loop
@@ -251,11 +268,12 @@ class RenderServer:
         return lat, overflow
 
 
-def serve_plain(scenes, requests, cfg=None, hbm_budget_bytes: int = 8 << 30, device="cuda"):
-    """One frame per request, in arrival order, on the same two arenas and
-    streams as the batched server (only the batching differs).  Returns
-    (latency, server)."""
-    srv = RenderServer(scenes, cfg, hbm_budget_bytes=hbm_budget_bytes, device=device, max_jobs=1, n_arenas=2)
+def serve_plain(scenes, requests, cfg=None, hbm_budget_bytes: int = 8 << 30, device="cuda", tile_of=None):
+    """One frame per request, in arrival order, on the same two arenas,
+    streams and tile policy as the batched server (only the batching
+    differs).  Returns (latency, server)."""
+    srv = RenderServer(scenes, cfg, hbm_budget_bytes=hbm_budget_bytes, device=device, max_jobs=1, n_arenas=2,
+                       tile_of=tile_of)
     lat, _ = srv.serve(requests)
     return lat, srv
 

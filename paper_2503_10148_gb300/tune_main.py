@@ -1,6 +1,7 @@
 """Runs the autotuner on a named workload and stores the choice.
 
     python -m paper_2503_10148_gb300.tune_main [workload] [--steps K]
+    python -m paper_2503_10148_gb300.tune_main --serve   (list tile per serving resolution)
 """
 from __future__ import annotations
 
@@ -17,8 +18,14 @@ def main():
     ap.add_argument("workload", nargs="?", default="clusters_1p5m_4views")
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--out", default=autotune.CACHE)
+    ap.add_argument("--serve", action="store_true", help="tune the serving list tile per resolution instead")
     args = ap.parse_args()
     build.build()
+    if args.serve:
+        dev = torch.device("cuda", 0)
+        scenes = [F.Scene.from_numpy(s, dev) for s in inputs.serving_scenes()]
+        print(autotune.tune_serve(scenes, inputs.SERVE_RESOLUTIONS, device=dev, path=args.out))
+        return
     scene_np, cams = getattr(inputs, args.workload)()
     cams = [F.f32_camera(c) for c in cams]
     dev = torch.device("cuda", 0)

@@ -558,3 +558,73 @@ def test_pair_capacity_overflow_is_reported_and_recovered():
     fr2.forward(grow=True)
     st2, need2, done2 = fr2.status()
     assert st2 == 0 and need2 == need == done2
+
+
+# ---------------------------------------------------------------- persistent launches, captured frames
+
+def test_persistent_render_queue_resets_between_launches():
+    """The render kernels take their work items from a counter in the
+    workspace: after every launch it is back at 0 (control words 8 and 9), and
+    repeated renders of a frame are bit for bit the first one."""
+    scene, cams = inputs.tiny_cube_2k()
+    fr, sc, cams = gpu_forward(scene, cams)
+    ctrl = lambda: fr.ws_view(fr.plan.ws_off_ctrl, torch.int32, 16)[8:10].cpu().tolist()
+    assert ctrl() == [0, 0]
+    first = fr.rgb.clone()
+    w = torch.as_tensor(np.concatenate([x.reshape(-1) for x in inputs.linear_loss_weights(cams, 3)]).astype(np.float32),
+                        device=DEV)
+    grads = []
+    for _ in range(3):
+        fr.render_fwd()
+        g = sc.zeros_like()
+        fr.backward(w, [g])
+        torch.cuda.synchronize()
+        assert ctrl() == [0, 0]
+        assert torch.equal(fr.rgb, first)
+        grads.append(g)
+    for f in frame.FIELDS:  # the backward's float atomics may add in another order
+        a, b = grads[0].t[f], grads[2].t[f]
+        assert float((a - b).norm()) <= 1e-5 * float(b.norm()) + 1e-30, f
+
+
+def test_multi_scene_frame_captured_in_a_cuda_graph():
+    """A frame of two scenes and mixed resolutions -- projection, binning,
+    sorting, forward and backward -- captured once into a CUDA graph and
+    replayed: the replays equal the eager frame (images bit for bit)."""
+    a = inputs.scene_uniform_cube(3000, seed=31)
+    b = inputs.subset_scene(inputs.scene_sphere_shell(100_000, seed=32), np.arange(0, 100_000, 20))
+    scs = [frame.Scene.from_numpy(x, DEV) for x in (a, b)]
+    cams = [frame.f32_camera(inputs.look_at((0.2, 0.1, 3.0), width=160, height=120)),
+            frame.f32_camera(inputs.look_at((2.0, 1.0, 2.0), width=97, height=203)),
+            frame.f32_camera(inputs.look_at((-1.0, 2.5, 1.2), width=256, height=256))]
+    job_scene = [0, 1, 1]
+    fr = frame.Frame(scs, cams, job_scene=job_scene, device=DEV)
+    fr.forward(grow=True)
+    torch.cuda.synchronize()
+    eager = fr.rgb.clone()
+    dl = torch.as_tensor(np.random.default_rng(4).uniform(-1, 1, fr.rgb.numel()).astype(np.float32), device=DEV)
+    ge = [s.zeros_like() for s in scs]
+    fr.backward(dl, ge)
+    torch.cuda.synchronize()
+    gg = [s.zeros_like() for s in scs]
+    side = torch.cuda.Stream(DEV)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):  # warm-up off the capture
+        fr.forward(side, grow=False)
+        fr.backward(dl, gg, side)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        st = torch.cuda.current_stream()
+        fr.forward(st, grow=False)
+        fr.backward(dl, gg, st)
+    for _ in range(2):
+        fr.rgb.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(fr.rgb, eager)
+        for x, y in zip(gg, ge):
+            for f in frame.FIELDS:  # float atomics: the order of the additions may differ
+                assert float((x.t[f] - y.t[f]).norm()) <= 1e-5 * float(y.t[f].norm()) + 1e-30, f
+    assert fr.status()[0] == 0

@@ -71,3 +71,59 @@ def test_server_batches_a_burst_within_its_budget(scenes):
     assert np.all(np.isfinite(lat)) and len(lat) == len(reqs)
     assert srv.frames < len(reqs)
     assert all(b <= budget // 2 for b in sizes[1:]), sizes
+
+
+def test_served_mixed_frame_against_the_oracle(scenes):
+    """A served frame holding 256x256, 800x800, 1297x840 and 1920x1080 jobs of
+    two scenes, rendered by the server with the per-frame tile of its largest
+    view: 300 seeded pixels per job compared with the FP64 oracle (flagged
+    pixels against the admissible results)."""
+    import oracle
+    from gpu_util import check_forward_view, f32_scene, gpu_last_component, gpu_view, merge_stats
+    rng = np.random.default_rng(3)
+    res = ((256, 256), (800, 800), (1297, 840), (1920, 1080))
+    reqs = [server.Request(i, 0.0, i % 2, frame.f32_camera(inputs.random_sphere_camera(rng, width=w, height=h)), w * h)
+            for i, (w, h) in enumerate(res)]
+    srv = server.RenderServer(scenes[:2], frame.make_cfg(), hbm_budget_bytes=2 << 30, device=DEV,
+                              tile_of=lambda w, h: 16 if w * h < 100_000 else 64)
+    fr, ev, used = srv.render(reqs, 0)
+    ev.synchronize()
+    srv.finish(fr, reqs, used, 0)
+    assert fr.cfg.tile_w == 64
+    cfgd = frame.cfg_dict(fr.cfg)
+    stats = []
+    for j, r in enumerate(reqs):
+        s32 = f32_scene(scenes[r.scene].to_numpy())
+        pix = rng.choice(r.pixels, 300, replace=False).astype(np.int64)
+        proj = oracle.project(s32, r.cam, cfgd)
+        ref = oracle.render(proj, r.cam, cfgd, pix)
+        img, T = gpu_view(fr, j, r.cam, pix)
+        stats.append(check_forward_view(proj, r.cam, cfgd, ref, img, T, pix,
+                                        last=gpu_last_component(fr, j, r.cam, pix)).stats)
+    print("served frame", merge_stats(stats))
+
+
+def test_server_with_per_frame_tiles_matches_single_frames(scenes):
+    """With a tile per frame (that of its largest view), every served image
+    equals the same request rendered alone with its frame's tile."""
+    import dataclasses
+    reqs = server.poisson_requests(3, rate=200.0, duration=0.3, seed=12,
+                                   resolutions=((128, 128), (320, 240), (640, 360)))
+    burst = [dataclasses.replace(r, arrival=0.0) for r in reqs][:24]
+    tile_of = lambda w, h: 16 if w * h <= 128 * 128 else 32
+    srv = server.RenderServer(scenes, frame.make_cfg(), hbm_budget_bytes=1 << 30, device=DEV, tile_of=tile_of)
+    seen = []
+    orig = srv.finish
+
+    def spy(fr, breqs, used, a):
+        out = orig(fr, breqs, used, a)
+        for j, r in enumerate(breqs):
+            one = frame.Frame([scenes[r.scene]], [r.cam], cfg=fr.cfg, device=DEV)
+            one.forward(grow=True)
+            torch.cuda.synchronize()
+            seen.append(torch.equal(fr.image(j), one.image(0)))
+        return out
+
+    srv.finish = spy
+    lat, _ = srv.serve(burst, warm=False)
+    assert len(seen) >= len(burst) and all(seen)

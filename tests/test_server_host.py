@@ -116,3 +116,26 @@ def test_summarize_counts_rejected_requests_out_of_the_throughput():
     assert s["rejected"] == 2 and s["mpix_s"] == pytest.approx(8 * 100 * 100 / 1e6)
     assert s["requests_per_frame"] == pytest.approx(8 / 3, abs=1e-3)
     assert s["outside_arena_frames"] == 1 and s["outside_arena_mb_max"] == 3.0
+
+
+def test_frame_tile_follows_the_largest_view():
+    srv = object.__new__(server.RenderServer)
+    srv.cfg = _abi.sss_default_cfg()
+    srv.tile_of = lambda w, h: 16 if w * h < 100_000 else 64
+    small, big = _req(0, 0, w=256, h=256), _req(1, 0, w=1920, h=1080)
+    assert srv.frame_cfg([small]).tile_w == 16 and srv.frame_cfg([small]).tile_h == 16
+    assert srv.frame_cfg([small, big]).tile_w == 64
+    assert srv.frame_cfg([small]).batch == srv.cfg.batch  # the rest of the options kept
+    srv.tile_of = None
+    assert srv.frame_cfg([small]) is srv.cfg
+
+
+def test_serve_tile_reads_the_tuned_table(tmp_path, monkeypatch):
+    from paper_2503_10148_gb300 import autotune
+    path = str(tmp_path / "tuned.json")
+    monkeypatch.setattr(autotune, "CACHE", path)
+    assert autotune.serve_tile(800, 800) == 32  # nothing tuned: the default
+    autotune.store(autotune.SERVE_KEY, {"tiles": {"256x256": {"tile": 16}, "800x800": {"tile": 32},
+                                                   "1920x1080": {"tile": 64}}}, path)
+    assert autotune.serve_tile(256, 256) == 16 and autotune.serve_tile(300, 300) == 16
+    assert autotune.serve_tile(1297, 840) == 32 and autotune.serve_tile(1920, 1080) == 64
