@@ -85,7 +85,7 @@ class PairModel:
 
 
 class RenderServer:
-    def __init__(self, scenes, cfg=None, hbm_budget_bytes: int = 8 << 30, headroom: float = 1.3, device="cuda",
+    def __init__(self, scenes, cfg=None, hbm_budget_bytes: int = 8 << 30, headroom: float = 1.6, device="cuda",
                  max_jobs: int = abi.SSS_MAX_JOBS, n_arenas: int = 2, tile_of=None):
         """``tile_of``: optional (width, height) -> square list tile side; a
         frame then takes the tile of its largest view (small views render
@@ -128,33 +128,47 @@ class RenderServer:
                                   [remap[r.scene] for r in reqs], cfg, min(cap, 0x7fffffff))
         return F.Frame.bytes_needed(plan), used, remap, cap
 
-    def take_batch(self, queue: collections.deque, arena_bytes: int):
-        """The longest head of the queue whose frame fits the arena (at most
-        SSS_MAX_JOBS jobs and SSS_MAX_SCENES scenes), found by bisection:
-        the workspace grows with every request added, so the fitting heads
-        are a prefix of the lengths.  A head request whose frame alone does
-        not fit the arena is rejected (moved to ``self.rejected``) and an
-        empty batch returned."""
-        limit, scenes = 0, set()
-        for r in queue:
-            if limit == self.max_jobs or (r.scene not in scenes and len(scenes) == abi.SSS_MAX_SCENES):
-                break
-            scenes.add(r.scene)
-            limit += 1
-        if limit == 0:
+    def tile_class(self, r) -> int:
+        """The list tile a request renders best on (0 without a tile policy)."""
+        return int(self.tile_of(r.cam.width, r.cam.height)) if self.tile_of is not None else 0
+
+    def take_batch(self, queue: collections.deque, arena_bytes: int, lookahead: int = 2 * abi.SSS_MAX_JOBS):
+        """The longest run of queued requests whose frame fits the arena (at
+        most SSS_MAX_JOBS jobs and SSS_MAX_SCENES scenes), found by
+        bisection: the workspace grows with every request added, so the
+        fitting runs are a prefix of the lengths.  With a tile policy the
+        run holds only requests of the head's tile class (no view renders on
+        a tile chosen for another size), taken in arrival order from the
+        first ``lookahead`` queued requests; the others keep their places.
+        A head request whose frame alone does not fit the arena is rejected
+        (moved to ``self.rejected``) and an empty batch returned."""
+        if not queue:
             return []
-        head = list(queue)[:limit]
+        cls = self.tile_class(queue[0])
+        picked, scenes = [], set()
+        for i, r in enumerate(queue):
+            if i == lookahead or len(picked) == self.max_jobs:
+                break
+            if self.tile_class(r) != cls or (r.scene not in scenes and len(scenes) == abi.SSS_MAX_SCENES):
+                continue
+            scenes.add(r.scene)
+            picked.append(i)
+        head = [queue[i] for i in picked]
         if self._plan_bytes(head[:1])[0] > arena_bytes:
             self.rejected.append(queue.popleft())
             return []
-        lo, hi = 1, limit  # lo: known to fit, hi: upper bound
+        lo, hi = 1, len(head)  # lo: known to fit, hi: upper bound
         while lo < hi:
             mid = (lo + hi + 1) // 2
             if self._plan_bytes(head[:mid])[0] <= arena_bytes:
                 lo = mid
             else:
                 hi = mid - 1
-        return [queue.popleft() for _ in range(lo)]
+        take = set(picked[:lo])
+        rest = [r for i, r in enumerate(queue) if i not in take]
+        queue.clear()
+        queue.extend(rest)
+        return head[:lo]
 
     def _count_outside(self, fr):
         if fr.outside_bytes:
@@ -211,12 +225,19 @@ class RenderServer:
 
     # ------------------------------------------------------------ serving loop
     def serve(self, requests, warm=True):
-        """Replay ``requests`` in real time.  Returns per-request latency (s)."""
-        if warm:  # every launch and host path once per arena, outside the timed run
-            for a in range(len(self.arenas)):
-                fr, ev, used = self.render(requests[:1], a)
+        """Replay ``requests`` in real time.  Returns per-request latency (s).
+        The warm-up, outside the timed run, renders one request of every
+        (scene, resolution) alone -- every launch and host path, and the pair
+        model's first count of each -- alternating the arenas."""
+        if warm:
+            first = {}
+            for r in requests:
+                first.setdefault((r.scene, r.cam.width, r.cam.height), r)
+            for i, r in enumerate(first.values()):
+                a = i % len(self.arenas)
+                fr, ev, used = self.render([r], a)
                 ev.synchronize()
-                self.finish(fr, requests[:1], used, a)
+                self.finish(fr, [r], used, a)
             torch.cuda.synchronize(self.device)
         reqs = sorted(requests, key=lambda r: r.arrival)
         start_ev = torch.cuda.Event(enable_timing=True)

@@ -26,6 +26,7 @@ def _server(bytes_per_request=100, max_jobs=_abi.SSS_MAX_JOBS):
     bytes_per_request per request of the head."""
     srv = object.__new__(server.RenderServer)
     srv.max_jobs = max_jobs
+    srv.tile_of = None
     srv.calls = []
 
     def plan_bytes(reqs):
@@ -139,3 +140,18 @@ def test_serve_tile_reads_the_tuned_table(tmp_path, monkeypatch):
                                                    "1920x1080": {"tile": 64}}}, path)
     assert autotune.serve_tile(256, 256) == 16 and autotune.serve_tile(300, 300) == 16
     assert autotune.serve_tile(1297, 840) == 32 and autotune.serve_tile(1920, 1080) == 64
+
+
+def test_take_batch_keeps_to_the_head_tile_class():
+    """With a tile policy a frame holds only requests of its head's tile
+    class, in arrival order, from the first `lookahead` queued requests; the
+    others keep their places."""
+    srv = _server(bytes_per_request=1)
+    srv.tile_of = lambda w, h: 16 if w * h < 100_000 else 64
+    q = collections.deque([_req(0, 0, w=256, h=256), _req(1, 1, w=256, h=256), _req(2, 0, w=1920, h=1080),
+                           _req(3, 0, w=256, h=256), _req(4, 0, w=1920, h=1080)])
+    assert [r.rid for r in srv.take_batch(q, arena_bytes=1 << 30)] == [0, 1, 3]
+    assert [r.rid for r in q] == [2, 4]
+    assert [r.rid for r in srv.take_batch(q, arena_bytes=1 << 30)] == [2, 4]
+    q = collections.deque([_req(0, 0, w=256, h=256), _req(1, 0, w=1920, h=1080), _req(2, 0, w=256, h=256)])
+    assert [r.rid for r in srv.take_batch(q, arena_bytes=1 << 30, lookahead=2)] == [0]
