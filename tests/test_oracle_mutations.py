@@ -36,8 +36,8 @@ MUTATIONS = [
     ("h without the 2 of 2 b dx dy", C,
      "double h = r[P_CON_A] * dx * dx + 2.0 * r[P_CON_B] * dx * dy", "double h = r[P_CON_A] * dx * dx + r[P_CON_B] * dx * dy"),
     ("J W^T instead of J W", C,
-     "J[r * 3 + 0] * V[0 * 4 + c] + J[r * 3 + 1] * V[1 * 4 + c] + J[r * 3 + 2] * V[2 * 4 + c]",
-     "J[r * 3 + 0] * V[c * 4 + 0] + J[r * 3 + 1] * V[c * 4 + 1] + J[r * 3 + 2] * V[c * 4 + 2]"),
+     "A[r * 3 + c] = J[r * 3 + 0] * V[0 * 4 + c] + J[r * 3 + 1] * V[1 * 4 + c] + J[r * 3 + 2] * V[2 * 4 + c]",
+     "A[r * 3 + c] = J[r * 3 + 0] * V[c * 4 + 0] + J[r * 3 + 1] * V[c * 4 + 1] + J[r * 3 + 2] * V[c * 4 + 2]"),
     ("dT/dh sign", C, "return -(nu + 2.0) / (2.0 * nu) * pow(1.0 + h / nu, -(nu + 4.0) / 2.0); }",
      "return (nu + 2.0) / (2.0 * nu) * pow(1.0 + h / nu, -(nu + 4.0) / 2.0); }"),
     ("dC/dalpha without the (1 - alpha) division", C,
