@@ -44,10 +44,11 @@ enum CtrlWord : int { kCtrlPairsNeeded = 0, kCtrlPairsSorted = 1, kCtrlStatus = 
 // End of a persistent render launch for the calling warp: counts the warp as
 // finished (queue[1]); the last of the grid's warps resets the item counter
 // and the finished count, so the next launch starts from item 0.  Every warp
-// has taken its last item before it counts itself, so nothing reads the
-// counter after the reset.
+// has taken its last item before it counts itself (the fence orders its last
+// take before its count), so nothing touches the counter after the reset.
 __device__ __forceinline__ void queue_retire(uint32_t* queue, unsigned lane) {
   if (lane == 0) {
+    __threadfence();
     const uint32_t total = gridDim.x * (blockDim.x >> 5);
     if (atomicAdd(queue + 1, 1u) == total - 1) {
       queue[0] = 0u;
