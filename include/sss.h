@@ -186,7 +186,8 @@ typedef struct sss_frame_plan {
   size_t ws_off_rec;     /* float4[3][n_entries]: 2D splat records:
                             {mean2D - origin, conic a, conic b},
                             {conic c, o, h_max, nu}, {rgb, origin bits}
-                            with origin = the entry's first tile corner
+                            with origin = the integer pixel nearest to
+                            mean2D, limited to [0, 16384]
                             (x | y << 16)                                   */
   size_t ws_off_dkey;    /* uint32[n_entries]: FP32 depth-key bits          */
   size_t ws_off_ntiles;  /* uint32[n_entries]: tiles touched                */

@@ -324,10 +324,10 @@ static double kernel_limit(double o_abs, double nu, double a, const ocfg* cfg) {
   return cfg->kernel == 1 ? 2.0 * log(o_abs / a) : h_limit(o_abs, nu, a);
 }
 
-/* Scale of the rounding error of a Sigma2D computed in FP32, relative to its
- * smallest eigenvalue: |J W|_F^2 s_max^2 / lambda_min(Sigma2D).  An FP32
- * evaluation of Sigma2D = (J W R S)(J W R S)^T perturbs it by a few u times
- * |J W|_F^2 s_max^2 (rotation and products rounded on the scale of the
+/* Scale of the rounding error of an evaluation of Sigma2D, relative to its
+ * smallest eigenvalue: |J W|_F^2 s_max^2 / lambda_min(Sigma2D).  Evaluating
+ * Sigma2D = (J W R S)(J W R S)^T with unit roundoff e perturbs it by a few e
+ * times |J W|_F^2 s_max^2 (rotation and products rounded on the scale of the
  * largest axis), and a perturbation dS of Sigma2D moves h = d^T Sigma2D^-1 d
  * by at most |dS| h / lambda_min.  Used only for the ambiguity windows. */
 static double error_scale(int n, const double* th, size_t i, const ocam* cam, const double* rec) {
@@ -464,16 +464,21 @@ static void cvec_push(cvec* c, contrib x) {
  * decision lies within the rounding error of an FP32 evaluation (the
  * precision of the paper's rasterizer), both outcomes are correct results.
  * The window bounds, to first order, the relative error of alpha evaluated
- * in FP32, as the sum of:
- *   - the 2D covariance of an FP32 projection: |dh| <= 16 u E h, E the
- *     error scale of the record (error_scale above; 16 u is 1.6 times the
- *     largest |dh| / (u E h) measured for GB300's FP32 projection at the
- *     alpha threshold over the shell and cluster workloads);
- *   - the screen mean stored relative to its first tile's corner:
- *     2 u (|m - corner| + 1) per coordinate (twice the largest measured
- *     error), times |dh/dm|;
- *   - evaluating h in FP32 from the offsets: 6 u q, q the sum of the
- *     magnitudes of the three terms of h;
+ * in FP32 from a projection whose conic is evaluated in double-float
+ * arithmetic (pairs of FP32, unit roundoff about 4 u^2) and rounded once to
+ * FP32, as the sum of:
+ *   - the scales exp(log_scale) in FP32 (at most 2 ulp, 4 u, each; squared in
+ *     Sigma2D, a relative perturbation of each axis' share): 8 u h;
+ *   - the double-float evaluation of the conic: 64 u^2 E h, E the error scale
+ *     of the record (error_scale above; the FP32 evaluation of the same
+ *     expressions measured at most 10.2 u E h, and 64 u^2 is 16 times the
+ *     double-float unit roundoff);
+ *   - the conic rounded to FP32: u q, q the sum of the magnitudes of the three
+ *     terms of h;
+ *   - the screen mean stored relative to the integer pixel nearest to it
+ *     (limited to [0, 16384]): 2 u (|m - origin| + 1) per coordinate, times
+ *     |dh/dm|;
+ *   - evaluating h in FP32 from the offsets: 6 u q;
  * times |dlnT2D/dh| = (nu+2) / (2 nu (1 + h/nu)) (1/2 for the Gaussian); plus
  * T2D = 2^(-(nu+2)/2 log2(1 + h/nu)) with hardware log2 / exp2 of 2^-22
  * error (absolute for log2, times the exponent; relative for exp2),
@@ -486,10 +491,10 @@ static double alpha_window(const double* r, double h, double dx, double dy, cons
   const double u = ORC_U;
   const double ca = r[P_CON_A], cb = r[P_CON_B], cc = r[P_CON_C];
   const double q = fabs(ca) * dx * dx + 2.0 * fabs(cb * dx * dy) + fabs(cc) * dy * dy;
-  const double ox = r[P_TX0] * cfg->tile_w, oy = r[P_TY0] * cfg->tile_h;
+  const double ox = fmin(fmax(rint(r[P_MX]), 0.0), 16384.0), oy = fmin(fmax(rint(r[P_MY]), 0.0), 16384.0);
   const double gm = 2.0 * fabs(ca * dx + cb * dy) * 2.0 * u * (fabs(r[P_MX] - ox) + 1.0) +
                     2.0 * fabs(cb * dx + cc * dy) * 2.0 * u * (fabs(r[P_MY] - oy) + 1.0);
-  const double dh = 16.0 * u * r[P_ES] * h + gm + 6.0 * u * q;
+  const double dh = 8.0 * u * h + 64.0 * u * u * r[P_ES] * h + gm + 7.0 * u * q;
   double w;
   if (cfg->kernel == 1) {
     w = 0.5 * dh + ORC_MUFU + u * 0.5 * h;

@@ -111,9 +111,9 @@ inline unsigned ceil_div(size_t a, size_t b) { return (unsigned)((a + b - 1) / b
 //   a = {mean2D x - ox, mean2D y - oy, conic a, conic b}
 //   b = {conic c, o, h_max, nu}
 //   c = {r, g, b, origin}   origin = bits of (ox | oy << 16)
-// (ox, oy) is the pixel corner of the entry's first tile: every pixel that
-// can see the splat has x >= ox, y >= oy, so (x - ox) is an exact small
-// integer and the stored, tile-relative mean keeps FP32's fine spacing near 0
+// (ox, oy) is the integer pixel nearest to the mean (limited to [0, 16384]):
+// (x - ox) is an exact small integer for every pixel x, and the stored
+// mean - origin keeps FP32's fine spacing near 0 (within u/2 px of the mean)
 // instead of its ~1e-4 px spacing at 1000 px.
 // h = a dx^2 + 2 b dx dy + c dy^2 with (dx, dy) = pixel centre - mean2D.
 struct SplatRec {

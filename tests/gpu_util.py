@@ -371,11 +371,13 @@ def assert_step_close(got, ref, mag, label="", rel=STEP_REL):
 
 # ---------------------------------------------------------------- the windows, checked
 def projection_error_ratio(fr, j, cam, proj, seed=0):
-    """The GPU's FP32 projection error of h on the ellipse h = h_max (where
+    """The GPU projection's error of h on the ellipse h = h_max (where
     alpha = tau), against the part of the oracle's ambiguity window that
-    models it, 16 u E h + 2 u (|m - corner| + 1) |dh/dm|, E the record's
-    error scale: one random point of the ring per valid entry of job j.
-    Returns the ratios |dh| / window (all must be <= 1)."""
+    models it, 8 u h + 64 u^2 E h + u q + 2 u (|m - origin| + 1) |dh/dm|
+    (scales, double-float conic, its FP32 rounding, the stored mean; E the
+    record's error scale, q the sum of the magnitudes of h's terms): one
+    random point of the ring per valid entry of job j.  Returns the ratios
+    |dh| / window (all must be <= 1)."""
     n = proj.shape[0]
     eb = fr.plan.jobs[j].entry_base
     recs = fr.records()[eb:eb + n].cpu().numpy().astype(np.float64)
@@ -397,8 +399,7 @@ def projection_error_ratio(fr, j, cam, proj, seed=0):
     px, py = f[:, oracle.P["mx"]] + dx, f[:, oracle.P["my"]] + dy
     gx, gy = px - (r[:, 0] + ox), py - (r[:, 1] + oy)
     hg = r[:, 2] * gx * gx + 2 * r[:, 3] * gx * gy + r[:, 4] * gy * gy
-    tx0 = f[:, oracle.P["tx0"]] * fr.cfg.tile_w
-    ty0 = f[:, oracle.P["ty0"]] * fr.cfg.tile_h
-    gm = (2 * np.abs(ca * dx + cb * dy) * 2 * U32 * (np.abs(f[:, oracle.P["mx"]] - tx0) + 1)
-          + 2 * np.abs(cb * dx + cc * dy) * 2 * U32 * (np.abs(f[:, oracle.P["my"]] - ty0) + 1))
-    return np.abs(hg - h) / (16 * U32 * f[:, oracle.P["es"]] * h + gm)
+    gm = (2 * np.abs(ca * dx + cb * dy) * 2 * U32 * (np.abs(f[:, oracle.P["mx"]] - ox) + 1)
+          + 2 * np.abs(cb * dx + cc * dy) * 2 * U32 * (np.abs(f[:, oracle.P["my"]] - oy) + 1))
+    q = np.abs(ca) * dx * dx + 2 * np.abs(cb * dx * dy) + np.abs(cc) * dy * dy
+    return np.abs(hg - h) / (8 * U32 * h + 64 * U32 * U32 * f[:, oracle.P["es"]] * h + U32 * q + gm)

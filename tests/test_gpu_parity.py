@@ -61,11 +61,30 @@ def _check_projection(fr, scene, cams, cfgd):
         rf = ref[valid_ref]
         org = recs[sl][valid_ref][:, 11].astype(np.float32).view(np.uint32)
         ox, oy = (org & 0xFFFF).astype(np.float64), (org >> 16).astype(np.float64)
-        assert np.allclose(r[:, 0] + ox, rf[:, oracle.P["mx"]], rtol=0, atol=2e-4)
-        assert np.allclose(r[:, 1] + oy, rf[:, oracle.P["my"]], rtol=0, atol=2e-4)
-        scale = np.maximum(np.abs(rf[:, oracle.P["con_a"]]), np.abs(rf[:, oracle.P["con_c"]]))
-        for col, key in ((2, "con_a"), (3, "con_b"), (4, "con_c")):
-            assert np.all(np.abs(r[:, col] - rf[:, oracle.P[key]]) <= 2e-4 * scale), key
+        # the origin is the integer pixel nearest to the mean's FP32 high part
+        # (either one within that part's spacing of a half-integer), limited
+        # to [0, 16384]; the stored offset is the ~46-bit mean rounded once
+        for col, key, o in ((0, "mx", ox), (1, "my", oy)):
+            m = rf[:, oracle.P[key]]
+            near = np.clip(np.rint(m), 0, 16384)
+            half = np.abs(np.abs(m - np.floor(m)) - 0.5) <= 2.0 ** -23 * np.maximum(np.abs(m), 1.0)
+            okn = (o == near) | half
+            assert okn.all(), (key, int((~okn).sum()), m[~okn][:4].tolist(), o[~okn][:4].tolist())
+            dm = np.abs(r[:, col] + o - m) / (U32 * np.abs(m - o) + 1e-9)
+            assert dm.max() <= 1.0, (key, float(dm.max()))
+        # the conic: double-float, rounded once to FP32 (u relative); the FP32
+        # scales exp(log_scale) (2 ulp each) perturb Sigma2D by at most 8 u of
+        # itself, so entry (i, j) of its inverse by 8 u sqrt(con_ii con_jj);
+        # the double-float chain's own error, 64 u^2 E on Sigma2D relative to
+        # lambda_min, is at most 128 u^2 E times the conic's largest diagonal
+        # entry (E the record's error scale)
+        ca_r, cc_r = rf[:, oracle.P["con_a"]], rf[:, oracle.P["con_c"]]
+        scale = np.maximum(np.abs(ca_r), np.abs(cc_r))
+        es = rf[:, oracle.P["es"]]
+        for col, key, geo in ((2, "con_a", ca_r), (3, "con_b", np.sqrt(ca_r * cc_r)), (4, "con_c", cc_r)):
+            ref_c = rf[:, oracle.P[key]]
+            bound = 1.01 * U32 * np.abs(ref_c) + 8.1 * U32 * geo + 128 * U32 * U32 * es * scale
+            assert np.all(np.abs(r[:, col] - ref_c) <= bound), (key, float(np.max(np.abs(r[:, col] - ref_c) / bound)))
         assert np.allclose(r[:, 5], rf[:, oracle.P["o"]], rtol=0, atol=2e-6)
         assert np.allclose(r[:, 6], rf[:, oracle.P["hmax"]], rtol=2e-5, atol=1e-5)
         assert np.allclose(r[:, 7], rf[:, oracle.P["nu"]], rtol=1e-6)
@@ -83,9 +102,6 @@ def _check_projection(fr, scene, cams, cfgd):
         ty0, ty1 = rg[:, 1] & 0xFFFF, rg[:, 1] >> 16
         ntr = rf[:, oracle.P["ntiles"]]
         has = ntr > 0
-        # the origin is the first tile's pixel corner
-        assert np.all((ox == tx0 * cfgd["tile_w"]) | (nt[sl][valid_ref] == 0))
-        assert np.all((oy == ty0 * cfgd["tile_h"]) | (nt[sl][valid_ref] == 0))
         same = (nt[sl][valid_ref] == ntr) & (~has | ((tx0 == rf[:, oracle.P["tx0"]]) & (tx1 == rf[:, oracle.P["tx1"]])
                                                       & (ty0 == rf[:, oracle.P["ty0"]]) & (ty1 == rf[:, oracle.P["ty1"]])))
         assert np.all(same | fragile), int((~same & ~fragile).sum())
@@ -244,7 +260,7 @@ def test_forward_shell_8views_800_sampled():
     fr, _, cams = gpu_forward(scene, cams)
     rng = np.random.default_rng(0)
     pix = [rng.choice(c.width * c.height, 2000, replace=False) for c in cams]
-    _check_forward(fr, f32_scene(scene), cams, frame.cfg_dict(fr.cfg), pix, max_flagged=0.012)
+    _check_forward(fr, f32_scene(scene), cams, frame.cfg_dict(fr.cfg), pix, max_flagged=0.005)
 
 
 @pytest.mark.parametrize("case", ["ragged", "no_termination", "lowpass", "background", "large_nu", "clamped_alpha",
