@@ -65,8 +65,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--tile", default=None, help="WxH tile, e.g. 16x16 (default: autotuned cache or 16x16)")
+    ap.add_argument("--tile", default=None, help="WxH tile, e.g. 16x16 (default: autotuned cache or 64x64)")
     ap.add_argument("--batch", type=int, default=None, help="records per warp and staging round with --tile: 32 or 64")
+    ap.add_argument("--bwd-box-h", type=int, default=None,
+                    help="height of the backward's warp box with --tile: 8 or 16 (16 needs tiles of at least 32x64)")
     ap.add_argument("--no-plain", action="store_true", help="skip the one-frame-per-view comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -186,10 +188,12 @@ def _cfg(args):
     from paper_2503_10148_gb300 import autotune, frame
     if getattr(args, "tile", None):
         tw, th = (int(v) for v in args.tile.split("x"))
-        return frame.make_cfg(tile_w=tw, tile_h=th, batch=getattr(args, "batch", None) or 32), "cli"
+        return frame.make_cfg(tile_w=tw, tile_h=th, batch=getattr(args, "batch", None) or 32,
+                              bwd_box_h=getattr(args, "bwd_box_h", None) or 8), "cli"
     best = autotune.cached(getattr(args, "workload", "clusters_1p5m_4views"))
     if best:
-        return frame.make_cfg(tile_w=best["tile_w"], tile_h=best["tile_h"], batch=best.get("batch", 32)), "autotuned"
+        return frame.make_cfg(tile_w=best["tile_w"], tile_h=best["tile_h"], batch=best.get("batch", 32),
+                              bwd_box_h=best.get("bwd_box_h", 8)), "autotuned"
     return frame.make_cfg(), "default"
 
 
@@ -477,7 +481,7 @@ def run_ours(args):
         "data": "synthetic (seeded scene, cameras and target images)",
         "config": {"workload": WORKLOAD if args.workload == "clusters_1p5m_4views" else args.workload,
                    "views": len(cams), "width": cams[0].width, "height": cams[0].height,
-                   "components": scene.n, "tile": f"{cfg.tile_w}x{cfg.tile_h}", "batch": cfg.batch,
+                   "components": scene.n, "tile": f"{cfg.tile_w}x{cfg.tile_h}", "batch": cfg.batch, "bwd_box_h": cfg.bwd_box_h,
                    "cfg_source": cfg_src, "form": "batched frame through torch.autograd.Function (render, image loss), whole step in one CUDA graph, every step from the configured scene",
                    "pairs_per_step": pairs, "pair_capacity": ts.frame.pair_capacity,
                    "l2": "inputs larger than L2 (params 360 MB, pair lists > 1 GB, images 52 MB)",

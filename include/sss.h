@@ -109,8 +109,9 @@ typedef struct sss_raster_cfg {
   int32_t tile_w, tile_h; /* 16, 32, 64 (default) or 128 pixels each: the
                              tiles of the pair lists; the render runs
                              sub-tiles of at most 32 x 32 (eight warps,
-                             lanes of up to 2 x 2 pixels), each walking its
-                             tile's whole list                             */
+                             lanes of up to 2 x 2 pixels; 32 x 64 and 2 x 4
+                             in the backward with bwd_box_h = 16), each
+                             walking its tile's whole list                 */
   int32_t batch;          /* records each warp stages in shared memory per
                              round (double buffered, cp.async): 32 or 64,
                              one or two per lane                          */
@@ -138,6 +139,13 @@ typedef struct sss_raster_cfg {
                              counts evaluated and contributing (splat,
                              pixel) pairs into ctrl[4..7] (a diagnostic for
                              work figures; costs a few % of the forward)     */
+  int32_t bwd_box_h;      /* height in pixels of a warp's box in the backward
+                             render: 8 (default; 16 x 8 boxes, 2 x 2 pixels
+                             per lane) or 16 (16 x 16 boxes, 2 x 4 pixels per
+                             lane; needs tile_w >= 32 and tile_h >= 64).  A
+                             box twice as high halves the per-splat work of
+                             large splats at a lower occupancy: a choice per
+                             workload, not a change of any result's value   */
 } sss_raster_cfg;
 
 /* Fills *cfg with the defaults quoted above. */

@@ -38,7 +38,8 @@ class sss_camera(Structure):
 class sss_raster_cfg(Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("batch", c_int32), ("nu_grad_mode", c_int32),
                 ("tau", c_float), ("t_min", c_float), ("alpha_max", c_float), ("znear", c_float),
-                ("lowpass", c_float), ("bg", c_float * 3), ("kernel", c_int32), ("count_pairs", c_int32)]
+                ("lowpass", c_float), ("bg", c_float * 3), ("kernel", c_int32), ("count_pairs", c_int32),
+                ("bwd_box_h", c_int32)]
 
 
 class sss_job_desc(Structure):

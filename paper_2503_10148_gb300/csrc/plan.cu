@@ -31,6 +31,7 @@ void sss_default_cfg(sss_raster_cfg* cfg) {
   cfg->alpha_max = 0.99f;
   cfg->znear = 0.2f;
   cfg->lowpass = 0.0f;
+  cfg->bwd_box_h = 8;
 }
 
 const char* sss_status_string(int status) {
@@ -53,6 +54,8 @@ int sss_plan_frame(const sss_params* scenes, int n_scenes, const sss_camera* cam
   if (cfg->nu_grad_mode != 0 && cfg->nu_grad_mode != 1) return SSS_ERR_INVALID_ARG;
   if (cfg->kernel != 0 && cfg->kernel != 1) return SSS_ERR_INVALID_ARG;
   if (cfg->count_pairs != 0 && cfg->count_pairs != 1) return SSS_ERR_INVALID_ARG;
+  if (cfg->bwd_box_h != 8 && cfg->bwd_box_h != 16) return SSS_ERR_INVALID_ARG;
+  if (cfg->bwd_box_h == 16 && (cfg->tile_w < 32 || cfg->tile_h < 64)) return SSS_ERR_UNSUPPORTED;
   if (!(cfg->tau > 0.0f && cfg->tau < cfg->alpha_max && cfg->alpha_max < 1.0f && cfg->t_min >= 0.0f &&
         cfg->t_min < 1.0f && cfg->lowpass >= 0.0f))
     return SSS_ERR_INVALID_ARG;

@@ -259,46 +259,24 @@ __device__ __forceinline__ void bwd_item(const sss_frame_plan& P, void* ws, cons
             dy[v] = dys[v / PW];
           }
         }
-        // all pixels of the lane in straight-line code, masked; nu branch
-        // uniform over the warp
-        PairEval<V> r[NV];
-        M ok[NV];
-        // the alpha clamp is the identity when |o| T2D cannot reach alpha_max
-        // (the forward makes the same choice, so both take identical decisions)
-        if (nu <= kFastNuMax && oabs * 1.0001f <= amax) {
-#pragma unroll
-          for (int v = 0; v < NV; ++v)
-            ok[v] = eval_pair_fast<V, false>(dx[v], dy[v], a.z, cb2, b.x, oabs, -osgn, nu, inv_nu, tau, amax, r[v]);
-        } else if (nu <= kFastNuMax) {
-#pragma unroll
-          for (int v = 0; v < NV; ++v)
-            ok[v] = eval_pair_fast(dx[v], dy[v], a.z, cb2, b.x, oabs, -osgn, nu, inv_nu, tau, amax, r[v]);
-        } else if (isinf(nu)) {
-#pragma unroll
-          for (int v = 0; v < NV; ++v)
-            ok[v] = eval_pair_gauss(dx[v], dy[v], a.z, cb2, b.x, oabs, -osgn, tau, amax, r[v]);
-        } else {
-#pragma unroll
-          for (int v = 0; v < NV; ++v)
-            ok[v] = eval_pair_slow(dx[v], dy[v], a.z, cb2, b.x, oabs, -osgn, nu, inv_nu, tau, amax, r[v]);
-        }
         // per-lane sums: rgb (v7..9), st = dL/dalpha T2D (v5 = dL/do), st
         // times the nu factor (v6 / o) and, per pixel, q = st / (1 + h/nu),
         // with dL/dh = o (dT2D/dh / T2D) (1 + h/nu) q; dL/dmean and dL/dconic
         // follow from q-weighted moments of the pixel offsets (h is quadratic
-        // in the offsets, so its gradients are linear in these moments)
+        // in the offsets, so its gradients are linear in these moments).
+        // Each value is accumulated right after its evaluation, so only one
+        // value's evaluation is live at a time.
         const V one = vsplat<V>(1.0f), zero = vsplat<V>(0.0f), ivn = vsplat<V>(inv_nu);
         const V cr = vsplat<V>(c.x), cg = vsplat<V>(c.y), cbl = vsplat<V>(c.z);
         V s5 = zero, s6 = zero, r7 = zero, r8 = zero, r9 = zero, q[NV];
         bool any = false;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
+        auto accumulate = [&](int v, const PairEval<V>& rv, M okv) {
           M before;  // the splat is in front of the pixel's last contributor
           if constexpr (L == 2) before = B2{pos < last[L * v], pos < last[L * v + 1]};
           else before = pos < last[v];
-          const M live = mand(ok[v], before);
+          const M live = mand(okv, before);
           any = any || many(live);
-          const V al = vsel(live, r[v].alpha, zero);  // -alpha (the record's sign flipped)
+          const V al = vsel(live, rv.alpha, zero);  // -alpha (the record's sign flipped)
           // T_k = T_{k+1} / (1 - alpha); with al = 0 off the live pixels the
           // MUFU reciprocal of 1 is exactly 1, so T is kept bit for bit
           const V Tk = vmul(T[v], vrcp(vadd(one, al)));
@@ -312,31 +290,71 @@ __device__ __forceinline__ void bwd_item(const sss_frame_plan& P, void* ws, cons
           // B <- alpha rgb + (1 - alpha) B gives Sg <- Sg + alpha (g.rgb - Sg)
           const V gdiff = vfma(g[v][0], cr, vfma(g[v][1], cg, vfma(g[v][2], cbl, Sg[v])));
           Sg[v] = vfma(al, gdiff, Sg[v]);
-          const V dl_da = vsel(mandn(live, r[v].clamped), vmul(gdiff, Tk), zero);
-          const V st = vmul(dl_da, r[v].t2d);
+          const V dl_da = vsel(mandn(live, rv.clamped), vmul(gdiff, Tk), zero);
+          const V st = vmul(dl_da, rv.t2d);
           s5 = vadd(s5, st);
-          const V inv_base = vrcp(vfma(r[v].h, ivn, one));
+          const V inv_base = vrcp(vfma(rv.h, ivn, one));
           q[v] = vmul(st, inv_base);
-          const V u = vmul(vmul(r[v].h, ivn), inv_base);  // x / (1 + x)
+          const V u = vmul(vmul(rv.h, ivn), inv_base);  // x / (1 + x)
           // paper form: (nu+2) x / (2 nu (1+x)) = u/2 + u/nu; exact: u/nu - g/2
           const V dnu = PAPER_NU ? vfma(vsplat<V>(0.5f), u, vmul(u, ivn))
-                                 : vfma(vsplat<V>(-0.5f), log1p_minus_u(u, r[v].log_base), vmul(u, ivn));
+                                 : vfma(vsplat<V>(-0.5f), log1p_minus_u(u, rv.log_base), vmul(u, ivn));
           s6 = vfma(st, dnu, s6);
+        };
+        // all pixels of the lane in straight-line code, masked; nu branch
+        // uniform over the warp.  The alpha clamp is the identity when
+        // |o| T2D cannot reach alpha_max (the forward makes the same choice,
+        // so both take identical decisions).
+        if (nu <= kFastNuMax && oabs * 1.0001f <= amax) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            PairEval<V> rv;
+            const M okv = eval_pair_fast<V, false>(dx[v], dy[v], a.z, cb2, b.x, oabs, -osgn, nu, inv_nu, tau, amax, rv);
+            accumulate(v, rv, okv);
+          }
+        } else if (nu <= kFastNuMax) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            PairEval<V> rv;
+            const M okv = eval_pair_fast(dx[v], dy[v], a.z, cb2, b.x, oabs, -osgn, nu, inv_nu, tau, amax, rv);
+            accumulate(v, rv, okv);
+          }
+        } else if (isinf(nu)) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            PairEval<V> rv;
+            const M okv = eval_pair_gauss(dx[v], dy[v], a.z, cb2, b.x, oabs, -osgn, tau, amax, rv);
+            accumulate(v, rv, okv);
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            PairEval<V> rv;
+            const M okv = eval_pair_slow(dx[v], dy[v], a.z, cb2, b.x, oabs, -osgn, nu, inv_nu, tau, amax, rv);
+            accumulate(v, rv, okv);
+          }
         }
         // moments of q over the lane's PW x PH pixels from column and row sums
         float m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f, m5 = 0.0f;
-        if constexpr (PW == 2 && PH == 2) {
+        if constexpr (PW == 2 && PH % 2 == 0) {
           // value v is row v: columns packed as (col 0, col 1)
-          const F2 cq = vadd(q[0], q[1]);                    // per-column sums
-          const F2 cqy = vfma(q[1], dy[1], vmul(q[0], dy[0]));  // per-column sums of q dy
+          F2 cq = q[0], cqy = vmul(q[0], dy[0]);  // per-column sums of q and q dy
+#pragma unroll
+          for (int v = 1; v < NV; ++v) {
+            cq = vadd(cq, q[v]);
+            cqy = vfma(q[v], dy[v], cqy);
+          }
           const F2 dq = vmul(dx[0], cq);
           m1 = vsum(dq);
           m3 = vsum(vmul(dq, dx[0]));
           m4 = vsum(vmul(dx[0], cqy));
-          const F2 dyr = f2(dys[0], dys[1]), rq = f2(vsum(q[0]), vsum(q[1]));  // per-row sums
-          const F2 dr = vmul(dyr, rq);
-          m2 = vsum(dr);
-          m5 = vsum(vmul(dr, dyr));
+#pragma unroll
+          for (int jj = 0; jj < PH; jj += 2) {  // per-row sums, two rows at a time
+            const F2 dyr = f2(dys[jj], dys[jj + 1]), rq = f2(vsum(q[jj]), vsum(q[jj + 1]));
+            const F2 dr = vmul(dyr, rq);
+            m2 += vsum(dr);
+            m5 += vsum(vmul(dr, dyr));
+          }
         } else {
         float cq[PW], cqy[PW], rq[PH];
 #pragma unroll
@@ -397,7 +415,7 @@ __device__ __forceinline__ void bwd_item(const sss_frame_plan& P, void* ws, cons
 // Persistent, as the forward: warps take work items from the workspace's
 // counter until none is left; the last one resets it.
 template <int PW, int PH, int R, bool PAPER_NU>
-__global__ void __launch_bounds__(64, PW * PH >= 4 ? 12 : 16) k_render_bwd(const sss_frame_plan P, void* ws,
+__global__ void __launch_bounds__(64, PW * PH >= 8 ? 8 : (PW * PH >= 4 ? 12 : 16)) k_render_bwd(const sss_frame_plan P, void* ws,
                                                                            const float* __restrict__ dl_drgb,
                                                                            uint32_t n_items) {
   __shared__ WarpBuf<R> s_wb[2];
@@ -446,7 +464,11 @@ extern "C" int sss_render_bwd(const sss_frame_plan* plan, void* ws, const float*
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemsetAsync(sss::ws_ptr<float>(ws, P.ws_off_grad2d), 0, 48 * (size_t)P.n_entries, st) != cudaSuccess)
     return SSS_ERR_CUDA;
-  const int pw = (P.cfg.tile_w >= 32 ? 32 : P.cfg.tile_w) / 16, ph = (P.cfg.tile_h >= 32 ? 32 : P.cfg.tile_h) / 16;
+  // sub-tiles of at most 32 x 32 (lanes of up to 2 x 2 pixels), or 32 x 64
+  // (lanes of 2 x 4) with 16-pixel-high warp boxes
+  const int pw = (P.cfg.tile_w >= 32 ? 32 : P.cfg.tile_w) / 16;
+  const int ph = P.cfg.bwd_box_h == 16 ? 4 : (P.cfg.tile_h >= 32 ? 32 : P.cfg.tile_h) / 16;
+  if (pw == 2 && ph == 4) return sss::launch_tile<2, 4>(P, ws, dL_drgb, st);
   if (pw == 1 && ph == 1) return sss::launch_tile<1, 1>(P, ws, dL_drgb, st);
   if (pw == 2 && ph == 1) return sss::launch_tile<2, 1>(P, ws, dL_drgb, st);
   if (pw == 1 && ph == 2) return sss::launch_tile<1, 2>(P, ws, dL_drgb, st);

@@ -73,6 +73,7 @@ def test_status_strings_and_defaults(lib):
     assert (c.tile_w, c.tile_h, c.batch) == (64, 64, 32)
     assert abs(c.tau - 1 / 255) < 1e-9 and abs(c.t_min - 1e-4) < 1e-10 and abs(c.alpha_max - 0.99) < 1e-7
     assert c.lowpass == 0.0 and c.znear == pytest.approx(0.2)
+    assert c.bwd_box_h == 8 and c.count_pairs == 0 and c.kernel == 0
     assert _abi.sss_version() >= 100
 
 
@@ -115,7 +116,7 @@ def test_plan_layout_and_offsets(lib):
     assert plan.ws_off_pval - plan.ws_off_pkey >= 8 * 5000
 
 
-@pytest.mark.parametrize("bad", ["n_jobs", "scene_idx", "tile", "batch", "deg", "size", "cap", "tau"])
+@pytest.mark.parametrize("bad", ["n_jobs", "scene_idx", "tile", "batch", "deg", "size", "cap", "tau", "box", "box_tile"])
 def test_plan_rejects_bad_arguments(lib, bad):
     scenes = [_dummy_scene(10)]
     cams = [_cam(64, 64)]
@@ -141,6 +142,11 @@ def test_plan_rejects_bad_arguments(lib, bad):
         cap = 0
     elif bad == "tau":
         cfg.tau = 0.0
+    elif bad == "box":
+        cfg.bwd_box_h = 12  # 8 or 16
+    elif bad == "box_tile":
+        cfg.tile_w, cfg.tile_h, cfg.bwd_box_h = 64, 32, 16  # 16-pixel boxes need 64-pixel-high tiles
+        expect = _abi.SSS_ERR_UNSUPPORTED
     with pytest.raises(_abi.SSSError) as ei:
         _abi.sss_plan_frame(scenes, cams, js, cfg, cap)
     assert ei.value.status == expect

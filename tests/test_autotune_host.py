@@ -58,10 +58,21 @@ def test_store_keeps_one_choice_per_workload_and_cached_reads_it(tmp_path, monke
     assert autotune.cached("c")["tile_w"] == 16
 
 
+def test_candidates_pair_the_tall_backward_box_with_tall_tiles():
+    cands = autotune.default_candidates()
+    assert len(cands) == len(autotune.TILES) * len(autotune.BATCHES) + 10
+    assert all(box == 8 or (tw >= 32 and th >= 64) for tw, th, _, box in cands)
+    assert len({autotune.candidate_key(*c) for c in cands}) == len(cands)
+
+
 def test_the_shipped_choice_is_a_candidate():
     choice = autotune.cached("clusters_1p5m_4views")
     assert choice is not None
     assert (choice["tile_w"], choice["tile_h"]) in autotune.TILES and choice["batch"] in autotune.BATCHES
-    assert len(choice["candidates"]) == 20
-    best = min(choice["candidates"].values())
-    assert choice["ms_per_step"] == best
+    key = autotune.candidate_key(choice["tile_w"], choice["tile_h"], choice["batch"], choice.get("bwd_box_h", 8))
+    assert set(choice["candidates"]) == {autotune.candidate_key(*c) for c in autotune.default_candidates()}
+    # the finalists are the fastest candidates of the first stage, re-timed
+    fin = choice["finalists"]
+    first = sorted(choice["candidates"], key=choice["candidates"].get)[:len(fin)]
+    assert set(fin) == set(first) and key in fin
+    assert choice["ms_per_step"] == min(fin.values()) == fin[key]

@@ -334,11 +334,15 @@ def _grad2d_report(fr, g2d_ref, g2d_abs, cams, scene):
 
 @pytest.mark.parametrize("nu_mode,tile", [(0, (16, 16)), (1, (16, 16)), (0, (32, 16)), (0, (16, 32)), (1, (32, 32)),
                                           (0, (64, 32)), (1, (32, 64)), (0, (64, 64)), (1, (128, 128)),
-                                          (0, (16, 16, 64)), (1, (64, 128, 64))])
+                                          (0, (16, 16, 64)), (1, (64, 128, 64)),
+                                          (0, (32, 64, 32, 16)), (1, (64, 64, 64, 16)), (0, (128, 128, 32, 16))])
 def test_backward_tiny_against_oracle_analytic(nu_mode, tile):
+    """tile = (tile_w, tile_h[, records per warp and staging round[, height
+    of the backward's warp box]])."""
     scene, cams = inputs.tiny_cube_2k()
-    batch = tile[2] if len(tile) > 2 else 32  # records per warp and staging round
-    cfg = frame.make_cfg(nu_grad_mode=nu_mode, tile_w=tile[0], tile_h=tile[1], batch=batch)
+    batch = tile[2] if len(tile) > 2 else 32
+    box = tile[3] if len(tile) > 3 else 8
+    cfg = frame.make_cfg(nu_grad_mode=nu_mode, tile_w=tile[0], tile_h=tile[1], batch=batch, bwd_box_h=box)
     fr, sc, cams = gpu_forward(scene, cams, cfg)
     cfgd = frame.cfg_dict(cfg)
     s32 = f32_scene(scene)
@@ -407,16 +411,18 @@ def test_backward_gradcheck_50k_against_oracle_fd_and_analytic():
     assert checked >= 180
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (32, 32)])
+@pytest.mark.parametrize("tile", [(16, 16), (32, 32), (64, 64, 16)])
 def test_backward_edge_cases_large_nu_and_clamp(tile):
     """Large nu (the log1pf/expf path) and clamped alpha, one pixel per lane
-    (16x16 tiles) and packed pixel pairs (32x32)."""
+    (16x16 tiles), two packed pixel pairs per lane (32x32) and four (64x64
+    with 16-pixel-high backward boxes)."""
     scene = inputs.scene_uniform_cube(1200, seed=13)
     rng = np.random.default_rng(4)
     scene["nu"] = np.exp(rng.uniform(0, math.log(2e4), 1200)).astype(np.float32)  # some beyond the 1e4 limit
     scene["opacity_raw"][:100] = np.float32(3.5)  # |o| > alpha_max: clamped alpha
     cam = inputs.look_at((0.1, 0.2, 3.0), width=96, height=72)
-    cfg = frame.make_cfg(bg=(0.3, 0.1, 0.6), lowpass=0.3, tile_w=tile[0], tile_h=tile[1])
+    cfg = frame.make_cfg(bg=(0.3, 0.1, 0.6), lowpass=0.3, tile_w=tile[0], tile_h=tile[1],
+                         bwd_box_h=tile[2] if len(tile) > 2 else 8)
     fr, sc, cams = gpu_forward(scene, [cam], cfg)
     cfgd = frame.cfg_dict(cfg)
     s32 = f32_scene(scene)
