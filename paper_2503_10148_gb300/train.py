@@ -130,21 +130,23 @@ class TrainStep:
         e0, e1 = self.frame.timing[name]
         return e0.elapsed_time(e1)
 
-    def capture(self):
+    def capture(self, pool=None, warmup: int = 2):
         """Warm-up steps on a side stream (the autograd engine must not have
         run this backward on the legacy stream before a capture: it would
-        touch that stream during the capture), then one captured step."""
+        touch that stream during the capture), then one captured step.
+        ``pool``: the memory pool of an earlier capture of this step (copies
+        of the step, replayed one after another, share its temporaries)."""
         cur = torch.cuda.current_stream(self.device)
         side = torch.cuda.Stream(self.device)
         side.wait_stream(cur)
         with torch.cuda.stream(side):
-            for _ in range(2):
+            for _ in range(warmup):
                 self.run()
         cur.wait_stream(side)
         torch.cuda.synchronize(self.device)
         g = torch.cuda.CUDAGraph()
         try:
-            with torch.cuda.graph(g):
+            with torch.cuda.graph(g, pool=pool):
                 self.run()
         except BaseException:
             torch.cuda.set_stream(cur)  # a failed capture_end leaves the capture stream current
