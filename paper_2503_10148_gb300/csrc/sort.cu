@@ -438,20 +438,29 @@ __global__ void __launch_bounds__(kThreads) k_emit(const sss_frame_plan P, const
   slice(P.n_entries, gridDim.x, blockIdx.x, begin, end);
   uint32_t carry = block_off[blockIdx.x];
   const uint32_t cap = P.pair_capacity;
-  for (uint32_t base = begin; base < end; base += kThreads) {
+  // software pipeline over the 256-entry chunks: the entry id of chunk k + 2
+  // and the count and rectangle of chunk k + 1 are loaded while chunk k's
+  // pairs are written, so the dependent gathers (depth order -> entry ->
+  // count, rectangle) overlap the scan and the stores
+  auto entry_at = [&](uint32_t base) -> uint32_t {
     const uint32_t i = base + threadIdx.x;
-    uint32_t e = 0, c = 0, t0 = 0, wx = 1, stride = 0;
-    if (i < end) {
-      e = order[i];
-      c = ntiles[e];
-      if (c) {
-        const sss_job_desc& J = P.jobs[job_of_entry(P, e)];
-        const uint2 r = rect[e];
-        const uint32_t tx0 = r.x & 0xffffu, tx1 = r.x >> 16, ty0 = r.y & 0xffffu;
-        stride = (uint32_t)J.tiles_x;
-        t0 = J.tile_base + ty0 * stride + tx0;
-        wx = tx1 - tx0 + 1;
-      }
+    return i < end ? order[i] : 0xffffffffu;
+  };
+  uint32_t e_cur = entry_at(begin), e_nxt = entry_at(begin + kThreads);
+  uint32_t c_cur = e_cur != 0xffffffffu ? ntiles[e_cur] : 0u;
+  uint2 r_cur = c_cur ? rect[e_cur] : make_uint2(0u, 0u);
+  for (uint32_t base = begin; base < end; base += kThreads) {
+    const uint32_t c_nxt = e_nxt != 0xffffffffu ? ntiles[e_nxt] : 0u;
+    const uint2 r_nxt = c_nxt ? rect[e_nxt] : make_uint2(0u, 0u);
+    const uint32_t e_nn = entry_at(base + 2 * kThreads);
+    const uint32_t c = c_cur;
+    uint32_t t0 = 0, wx = 1, stride = 0;
+    if (c) {
+      const sss_job_desc& J = P.jobs[job_of_entry(P, e_cur)];
+      const uint32_t tx0 = r_cur.x & 0xffffu, tx1 = r_cur.x >> 16, ty0 = r_cur.y & 0xffffu;
+      stride = (uint32_t)J.tiles_x;
+      t0 = J.tile_base + ty0 * stride + tx0;
+      wx = tx1 - tx0 + 1;
     }
     uint32_t total;
     const uint32_t incl = block_scan_incl(c, s_w, total);
@@ -459,7 +468,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(const sss_frame_plan P, const
     s_t0[threadIdx.x] = t0;
     s_wx[threadIdx.x] = wx;
     s_stride[threadIdx.x] = stride;
-    s_e[threadIdx.x] = e;
+    s_e[threadIdx.x] = e_cur;
     __syncthreads();
     for (uint32_t k = threadIdx.x; k < total; k += kThreads) {
       uint32_t j = 0;
@@ -475,6 +484,10 @@ __global__ void __launch_bounds__(kThreads) k_emit(const sss_frame_plan P, const
       }
     }
     carry += total;
+    e_cur = e_nxt;
+    c_cur = c_nxt;
+    r_cur = r_nxt;
+    e_nxt = e_nn;
     __syncthreads();
   }
 }
