@@ -5,7 +5,8 @@ For a workload it times the whole captured train step (``train.TrainStep``)
 for every (tile_w, tile_h, batch, bwd_box_h) candidate and keeps the
 fastest.  Tile size
 trades pair count (bigger tiles: fewer pairs to sort) against the render's
-work per tile: a tile is rendered as sub-tiles of at most 32 x 32 pixels,
+work per tile: a tile is rendered as sub-tiles of at most 32 x 32 pixels (32 x 64
+in the backward with the taller box),
 each walking the tile's whole list (its warps skip the records whose
 ellipse misses their block).
 The staging batch is the number of records a warp gathers per round, 32 or

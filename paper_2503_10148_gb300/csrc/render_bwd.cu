@@ -1,6 +1,7 @@
 // a5: closed-form backward of the compositing (SM "Backward Pass").
 //
-// Same CTA/warp/lane layout as the forward.  Each pixel walks its tile's list
+// The forward's CTA/warp/lane layout, or (cfg.bwd_box_h = 16) warp boxes twice
+// as high: 2 x 4 pixels a lane, 32 x 64 sub-tiles.  Each pixel walks its tile's list
 // from its last contributor back to the front, recomputing the transmittance
 // before every contributor as T_k = T_{k+1} / (1 - alpha_k) (no per-pixel
 // lists are stored).  With S_k the colour composited behind contributor k
