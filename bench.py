@@ -288,26 +288,40 @@ def roofline(stage: str, ms: float, ts, pairs: tuple, peaks: dict, peak_src: str
             "work": f"{nbytes} algorithmic bytes"}
 
 
+PROFILED_SOURCES = {"render_bwd": ("render_bwd.cu", "common.cuh"), "render_fwd": ("render_fwd.cu", "common.cuh")}
+
+
+def code_hash(files) -> str:
+    """First 16 hex digits of the sha256 of the C/CUDA sources `files` (under
+    csrc/) with comments removed and whitespace runs collapsed: an edit of a
+    comment leaves it unchanged, a change of the code does not."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2503_10148_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(kernel: str, workload: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary
     profiles/<kernel>_<workload>.md, or None when there is none or the kernel
-    sources no longer hash to the value recorded with the counters."""
-    import hashlib
+    sources' code no longer hashes to the value recorded with the counters."""
     import re
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
-    srcs = {"render_bwd": ("render_bwd.cu", "common.cuh"), "render_fwd": ("render_fwd.cu", "common.cuh")}.get(kernel)
+    srcs = PROFILED_SOURCES.get(kernel)
     if not srcs or not os.path.exists(path):
         return None
     text = open(path).read()
-    m_sha = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", text)
+    m_sha = re.search(r"code_sha256_16:\s*([0-9a-f]{16})", text)
     m_b = re.search(r"dram_bytes_per_launch:\s*(\d+)", text)
     if not (m_sha and m_b):
         return None
-    h = hashlib.sha256()
-    for f in srcs:
-        with open(os.path.join(ROOT, "paper_2503_10148_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return int(m_b.group(1)) if h.hexdigest()[:16] == m_sha.group(1) else None
+    return int(m_b.group(1)) if code_hash(srcs) == m_sha.group(1) else None
 
 
 def algorithmic_bytes(stage: str, ts) -> int:

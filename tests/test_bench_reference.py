@@ -108,3 +108,17 @@ def test_alu_roofline_follows_the_per_pair_work_and_device_ceiling():
     f = bench.roofline("render_fwd", 2.0, None, (1_000_000_000, 2_000_000_000), {}, "measured", 152, 2070.0)
     # 8 x 2e9 + 12 x 1e9 = 28e9 flops (0.348 ms of FP32) vs 2e9 MUFU (0.397 ms): the MUFU pipe binds
     assert f["frac"] == pytest.approx(2e9 / (152 * 16 * 2.07e9) / 2e-3, rel=1e-3)
+
+
+def test_profile_code_hash_ignores_comments_not_code(tmp_path, monkeypatch):
+    """The DRAM traffic recorded with an ncu capture stays valid through an
+    edit of a comment, and not through a change of the code."""
+    csrc = tmp_path / "paper_2503_10148_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (csrc / "k.cu").write_text("// header\nint f(int a) {\n  return a + 1;  /* one */\n}\n")
+    h0 = bench.code_hash(["k.cu"])
+    (csrc / "k.cu").write_text("// a longer header\n// over two lines\nint f(int a) {\n    return a + 1;\n}\n")
+    assert bench.code_hash(["k.cu"]) == h0
+    (csrc / "k.cu").write_text("// header\nint f(int a) {\n  return a + 2;\n}\n")
+    assert bench.code_hash(["k.cu"]) != h0
