@@ -479,12 +479,19 @@ static void cvec_push(cvec* c, contrib x) {
  *     (limited to [0, 16384]): 2 u (|m - origin| + 1) per coordinate, times
  *     |dh/dm|;
  *   - evaluating h in FP32 from the offsets: 6 u q;
- * times |dlnT2D/dh| = (nu+2) / (2 nu (1 + h/nu)) (1/2 for the Gaussian); plus
- * T2D = 2^(-(nu+2)/2 log2(1 + h/nu)) with hardware log2 / exp2 of 2^-22
- * error (absolute for log2, times the exponent; relative for exp2),
- * 2 u (nu+2)/2 for rounding the argument 1 + h/nu, and 4 u for the rest
- * (tanh of the opacity, products).  Capped at 1e-2 (the prefilter evaluates
- * every pair with |alpha| >= tau (1 - 1e-2)). */
+ * times |dlnT2D/dh| = (nu+2) / (2 nu (1 + h/nu)) (1/2 for the Gaussian); plus,
+ * with e = (nu+2)/2 and T2D = 2^(-e log2(1 + h/nu)) evaluated as the kernel
+ * does:
+ *   - hardware log2 / exp2 of 2^-22 error (absolute for log2, times the
+ *     exponent e; relative for exp2);
+ *   - the argument 1 + h/nu from a 1-ulp hardware reciprocal of nu and one
+ *     FMA: 3 u relative, times e;
+ *   - the exponent -e log2(1 + h/nu), e and the product each rounded once:
+ *     2 u of |ln T2D| = 2 u e ln(1 + h/nu) (for the Gaussian, the product
+ *     -h log2(e) / 2: u h / 2);
+ *   - 4 u for the rest (tanh of the opacity, products).
+ * Capped at 1e-2 (the prefilter evaluates every pair with
+ * |alpha| >= tau (1 - 1e-2)). */
 #define ORC_U (1.0 / 16777216.0)
 #define ORC_MUFU (1.0 / 4194304.0)
 static double alpha_window(const double* r, double h, double dx, double dy, const ocfg* cfg) {
@@ -500,7 +507,8 @@ static double alpha_window(const double* r, double h, double dx, double dy, cons
     w = 0.5 * dh + ORC_MUFU + u * 0.5 * h;
   } else {
     const double nu = r[P_NU], e = 0.5 * (nu + 2.0);
-    w = e / nu / (1.0 + h / nu) * dh + log(2.0) * e * ORC_MUFU + 2.0 * u * e + ORC_MUFU;
+    w = e / nu / (1.0 + h / nu) * dh + log(2.0) * e * ORC_MUFU + 3.0 * u * e + 2.0 * u * e * log1p(h / nu) +
+        ORC_MUFU;
   }
   w += 4.0 * u;
   return w < 1e-2 ? w : 1e-2;

@@ -73,7 +73,7 @@ def test_fullsize_forward_sampled_pixels(full):
     print(f"full-size forward: {st}, flagged fraction uniform {fu:.4f} / deepest-list tail {ft:.4f}, "
           f"deepest-list tail max-abs {tail_err:.3e}")
     # ~370 evaluated pairs per pixel, each near tau with a probability set by
-    # its window, and long contributor lists for the T window: 0.43 % of
+    # its window, and long contributor lists for the T window: 0.49 % of
     # 120,000 uniform pixels of the four views (the oracle alone); the bars
     # leave room for the sampling noise of 7,600 pixels
     assert fu <= 0.008 and st["flagged_frac"] <= 0.012, (fu, st)
