@@ -489,7 +489,8 @@ static void cvec_push(cvec* c, contrib x) {
  *   - the exponent -e log2(1 + h/nu), e and the product each rounded once:
  *     2 u of |ln T2D| = 2 u e ln(1 + h/nu) (for the Gaussian, the product
  *     -h log2(e) / 2: u h / 2);
- *   - 4 u for the rest (tanh of the opacity, products).
+ *   - the opacity, FP32 tanh of at most 2 ulp (4 u), and its product with
+ *     T2D: 5 u.
  * Capped at 1e-2 (the prefilter evaluates every pair with
  * |alpha| >= tau (1 - 1e-2)). */
 #define ORC_U (1.0 / 16777216.0)
@@ -510,7 +511,7 @@ static double alpha_window(const double* r, double h, double dx, double dy, cons
     w = e / nu / (1.0 + h / nu) * dh + log(2.0) * e * ORC_MUFU + 3.0 * u * e + 2.0 * u * e * log1p(h / nu) +
         ORC_MUFU;
   }
-  w += 4.0 * u;
+  w += 5.0 * u;
   return w < 1e-2 ? w : 1e-2;
 }
 
