@@ -63,10 +63,13 @@ class ForwardCheck:
     match the GPU's pixel within tol, so its image does not determine which
     decisions it took (a gradient through it cannot be attributed);
     [nc_lo, nc_hi] bounds the contributor count over the admissible results
-    within tol; stats summarises the view."""
+    within tol; alts[k] (unresolved pixels only) lists one decision mask per
+    distinct admissible result the GPU's pixel matched; stats summarises the
+    view."""
 
-    def __init__(self, flip, unresolved, nc_lo, nc_hi, stats):
+    def __init__(self, flip, unresolved, nc_lo, nc_hi, stats, alts=None):
         self.flip, self.unresolved, self.nc_lo, self.nc_hi, self.stats = flip, unresolved, nc_lo, nc_hi, stats
+        self.alts = alts or {}
 
 
 def check_forward_view(proj, cam, cfgd, ref, img, T, pix=None, tol=FWD_TOL, last=None) -> ForwardCheck:
@@ -93,6 +96,7 @@ def check_forward_view(proj, cam, cfgd, ref, img, T, pix=None, tol=FWD_TOL, last
     nc_hi = nc_lo.copy()
     idx = np.flatnonzero(fl)
     worst_fl, primary = 0.0, 0
+    alts = {}
     if idx.size:
         k = ref["n_amb"][idx]
         assert int(k.max()) < FLIP_BITS, ("ambiguous decisions per pixel", int(k.max()))
@@ -113,7 +117,10 @@ def check_forward_view(proj, cam, cfgd, ref, img, T, pix=None, tol=FWD_TOL, last
             flip[idx[i]] = masks[pick]
             good = np.flatnonzero(err[s0:s0 + r] <= tol) + s0
             res = np.concatenate([alt["rgb"][:, good], alt["T"][None, good], alt["n_contrib"][None, good]])
-            unresolved[idx[i]] = np.unique(res, axis=1).shape[1] > 1
+            _, first = np.unique(res, axis=1, return_index=True)
+            unresolved[idx[i]] = first.size > 1
+            if first.size > 1:
+                alts[int(idx[i])] = [int(masks[good[f]]) for f in sorted(first)]
             nc_lo[idx[i]] = alt["n_contrib"][good].min()
             nc_hi[idx[i]] = alt["n_contrib"][good].max()
         worst_fl = float(best.max())
@@ -123,7 +130,7 @@ def check_forward_view(proj, cam, cfgd, ref, img, T, pix=None, tol=FWD_TOL, last
              "near_tmin": int(np.sum((ref["flags"] & oracle.F_NEAR_TMIN) != 0)),
              "flagged_as_primary": primary, "unresolved": int(unresolved.sum()), "max_err_unflagged": worst,
              "max_err_flagged": worst_fl}
-    return ForwardCheck(flip, unresolved, nc_lo, nc_hi, stats)
+    return ForwardCheck(flip, unresolved, nc_lo, nc_hi, stats, alts)
 
 
 def merge_stats(stats):
@@ -163,9 +170,10 @@ def gpu_last_component(fr, j, cam, pix=None):
     return comp if pix is None else comp[pix]
 
 
-def check_forward_frame(fr, cams, cfgd, refs, pix=None, tol=FWD_TOL):
+def check_forward_frame(fr, cams, cfgd, refs, pix=None, tol=FWD_TOL, alts_out=None):
     """check_forward_view for every job of a frame; returns (flips per view,
-    merged stats, unresolved masks per view)."""
+    merged stats, unresolved masks per view).  With alts_out (a list), every
+    unresolved pixel is appended as (view, linear pixel, admissible masks)."""
     flips, stats, unres = [], [], []
     for j, (cam, (proj, ref)) in enumerate(zip(cams, refs)):
         pj = None if pix is None else pix[j]
@@ -174,17 +182,21 @@ def check_forward_frame(fr, cams, cfgd, refs, pix=None, tol=FWD_TOL):
         flips.append(c.flip)
         stats.append(c.stats)
         unres.append(c.unresolved)
+        if alts_out is not None:
+            lin = np.arange(cam.width * cam.height) if pj is None else np.asarray(pj, np.int64)
+            alts_out.extend((j, int(lin[k]), m) for k, m in sorted(c.alts.items()))
     return flips, merge_stats(stats), unres
 
 
-def resolved_weights(fr, cams, cfgd, refs, seed, pix=None):
+def resolved_weights(fr, cams, cfgd, refs, seed, pix=None, alts_out=None):
     """Seeded dL/dC weights and, per view, the oracle's choice of ambiguous
     decisions that the GPU's forward matched, so that the oracle
     differentiates the same admissible forward.  Only the pixels whose image
     matches two different admissible results (its decisions are then not
     determined; counted in stats["unresolved"]) carry no weight.  With pix
-    given, only those pixels carry weight."""
-    flips, stats, unres = check_forward_frame(fr, cams, cfgd, refs, pix)
+    given, only those pixels carry weight.  alts_out as in
+    check_forward_frame."""
+    flips, stats, unres = check_forward_frame(fr, cams, cfgd, refs, pix, alts_out=alts_out)
     ws = inputs.linear_loss_weights(cams, seed)
     out = []
     for v, w in enumerate(ws):
@@ -201,6 +213,45 @@ def resolved_weights(fr, cams, cfgd, refs, seed, pix=None):
 
 def scene_grads_flat(g: frame.Scene) -> np.ndarray:
     return np.concatenate([g.t[f].detach().cpu().numpy().reshape(-1).astype(np.float64) for f in frame.FIELDS])
+
+
+def check_unresolved_gradients(fr, sc, s32, cams, cfgd, unresolved, seed, sh_degree, max_pixels=48):
+    """Pixels whose image matches two different admissible results carry no
+    weight in the frame-wide gradient tests; here each is differentiated on
+    its own.  unresolved: list of (view j, linear pixel p, masks), the masks
+    the admissible results the GPU's pixel matched (ForwardCheck.alts).  For
+    each (at most max_pixels, in order) the GPU runs its full backward with a
+    seeded dL/dC on that pixel alone, and its gradient must pass the gradient
+    bar against the oracle's differentiated through one of the admissible
+    results.  Returns (pixels checked, how many matched their first mask)."""
+    rng = np.random.default_rng(seed)
+    n = s32["n"]
+    checked = first = 0
+    for j, p, masks in unresolved[:max_pixels]:
+        w = rng.uniform(-1, 1, size=3).astype(np.float32).astype(np.float64)
+        dl = [np.zeros((3, c.width * c.height), np.float32) for c in cams]
+        dl[j][:, p] = w
+        g = sc.zeros_like()
+        fr.backward(torch.as_tensor(np.concatenate([d.reshape(-1) for d in dl]), device=DEV), [g])
+        torch.cuda.synchronize()
+        got = scene_grads_flat(g)
+        errors = []
+        for k, m in enumerate(masks):
+            gref, _, gabs, g2abs = oracle.backward(s32, [cams[j]], cfgd, [w[:, None]], [np.array([p], np.int64)],
+                                                   want_grad2d=True, want_abs=True, flip=[np.array([m], np.uint32)])
+            try:
+                assert_groups_close(got, gref, n, sh_degree, gabs, label=f"unresolved pixel {j}:{p}",
+                                    extra=sh_basis_bound(n, sh_degree, g2abs))
+            except AssertionError as e:
+                errors.append(e)
+                continue
+            first += k == 0
+            break
+        else:
+            raise AssertionError(("unresolved pixel matches none of its admissible gradients", j, p, errors[:2]))
+        checked += 1
+    return checked, first
+
 
 
 GRAD_REL = 1e-3   # the survey's bar: |g - g_ref| <= 1e-3 max(|g_ref|, 1e-3 max_group |g_ref|) ...

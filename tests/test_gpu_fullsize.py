@@ -14,7 +14,8 @@ import bench
 import oracle
 from paper_2503_10148_gb300 import frame, inputs
 
-from gpu_util import (DEV, assert_groups_close, check_forward_view, f32_scene, gpu_last_component, gpu_view,
+from gpu_util import (DEV, assert_groups_close, check_forward_view, check_unresolved_gradients, f32_scene,
+                      gpu_last_component, gpu_view,
                       merge_stats, projection_error_ratio, require_gpu, scene_grads_flat, sh_basis_bound)
 
 pytestmark = pytest.mark.gpu
@@ -125,7 +126,7 @@ def test_fullsize_backward_on_pixel_subset(full):
     elsewhere.  The deepest-list pixels are then checked on their own."""
     fr, sc, cams = full["fr"], full["sc"], full["cams"]
     rng = np.random.default_rng(13)
-    pix, tails, dl_sub, flips = [], [], [], []
+    pix, tails, dl_sub, flips, unresolved = [], [], [], [], []
     for j, cam in enumerate(cams):
         p, tail = _sample_pixels(fr, j, cam, 450, 50, seed=30 + j)
         proj = oracle.project(full["s32"], cam, full["cfgd"])
@@ -136,7 +137,8 @@ def test_fullsize_backward_on_pixel_subset(full):
         tails.append(tail)
         flips.append(chk.flip)
         w = rng.uniform(-1, 1, size=(3, p.size)).astype(np.float32).astype(np.float64)
-        w[:, chk.unresolved] = 0.0  # their images do not determine their decisions
+        w[:, chk.unresolved] = 0.0  # their images do not determine their decisions: checked one by one below
+        unresolved.extend((j, int(p[k]), m) for k, m in sorted(chk.alts.items()))
         dl_sub.append(w)
     n = full["scene"]["n"]
 
@@ -160,3 +162,9 @@ def test_fullsize_backward_on_pixel_subset(full):
     got, gref, gabs, g2abs = run([w * t[None, :] for w, t in zip(dl_sub, tails)])
     print("deepest-list tail", assert_groups_close(got, gref, n, 3, gabs, label="full-size tail",
                                                    extra=sh_basis_bound(n, 3, g2abs)))
+    # the pixels left out above, each differentiated on its own
+    checked, first = check_unresolved_gradients(fr, sc, full["s32"], cams, full["cfgd"], unresolved, seed=14,
+                                                sh_degree=3)
+    print(f"unresolved pixels: {len(unresolved)}, checked one by one {checked}, matching the first admissible "
+          f"result {first}")
+    assert checked == min(len(unresolved), 48)

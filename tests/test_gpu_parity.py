@@ -20,7 +20,8 @@ import oracle
 from paper_2503_10148_gb300 import _abi, frame, inputs
 
 from gpu_util import (DEV, FWD_TOL, GRAD_NORM, GRAD_REL, U32, adam_increment_mag, assert_groups_close,
-                      assert_step_close, check_forward_frame, check_forward_view, f32, f32_scene, gpu_forward,
+                      assert_step_close, check_forward_frame, check_forward_view, check_unresolved_gradients, f32,
+                      f32_scene, gpu_forward,
                       gpu_last_component, gpu_view, grad_den, oracle_views, projection_error_ratio, require_gpu,
                       resolved_weights, scene_grads_flat,
                       sh_basis_bound, step_mags)
@@ -363,12 +364,17 @@ def test_backward_shell_sh3_multiview_against_oracle_analytic():
     cfgd = frame.cfg_dict(fr.cfg)
     s32 = f32_scene(scene)
     refs = oracle_views(s32, cams, cfgd)
-    ws, flips, fst = resolved_weights(fr, cams, cfgd, refs, seed=6)
+    unresolved = []
+    ws, flips, fst = resolved_weights(fr, cams, cfgd, refs, seed=6, alts_out=unresolved)
     g = _gpu_backward(fr, sc, ws)
     gref, g2d, gabs, g2abs = oracle.backward(s32, cams, cfgd, ws, want_grad2d=True, want_abs=True, flip=flips)
     _grad2d_report(fr, g2d, g2abs, cams, scene)
     print(fst, assert_groups_close(scene_grads_flat(g), gref, scene["n"], 3, gabs, label="shell",
                               extra=sh_basis_bound(scene["n"], 3, g2abs)))
+    checked, first = check_unresolved_gradients(fr, sc, s32, cams, cfgd, unresolved, seed=9, sh_degree=3)
+    print(f"unresolved pixels: {len(unresolved)}, checked one by one {checked}, matching the first admissible "
+          f"result {first}")
+    assert checked == min(len(unresolved), 48)
 
 
 def test_backward_gradcheck_50k_against_oracle_fd_and_analytic():
@@ -380,10 +386,16 @@ def test_backward_gradcheck_50k_against_oracle_fd_and_analytic():
     cfgd = frame.cfg_dict(fr.cfg)
     s32 = f32_scene(scene)
     refs = oracle_views(s32, cams, cfgd)
-    ws, flips, fst = resolved_weights(fr, cams, cfgd, refs, seed=7)
+    unresolved = []
+    ws, flips, fst = resolved_weights(fr, cams, cfgd, refs, seed=7, alts_out=unresolved)
     g = scene_grads_flat(_gpu_backward(fr, sc, ws))
     gref, gabs = oracle.backward(s32, cams, cfgd, ws, want_abs=True, flip=flips)
     print(fst, assert_groups_close(g, gref, scene["n"], 0, gabs, label="gradcheck"))
+    # the pixels whose image leaves their decisions open, each on its own
+    checked, first = check_unresolved_gradients(fr, sc, s32, cams, cfgd, unresolved, seed=8, sh_degree=0)
+    print(f"unresolved pixels: {len(unresolved)}, checked one by one {checked}, matching the first admissible "
+          f"result {first}")
+    assert checked == min(len(unresolved), 48)
     # central differences follow the oracle's own decisions: compare them with
     # a GPU gradient whose flagged pixels carry no weight
     ws = [w * (ref["flags"] == 0)[None, :] for w, (_, ref) in zip(ws, refs)]
