@@ -306,6 +306,32 @@ def test_forward_empty_and_culled_scenes():
         assert fr.status()[1] == 0
 
 
+@pytest.mark.parametrize("shape,tile", [((16384, 24), (16, 16)), ((24, 16384), (32, 32))])
+def test_forward_and_backward_at_the_largest_image_extent(shape, tile):
+    """Images 16,384 pixels wide or high, the plan's limit: 1,024 tiles along
+    a row (16-pixel tiles), record origins up to the 16,384 limit and pixel
+    offsets from them at the largest magnitudes; every pixel's forward and the
+    gradient of a seeded linear loss over all of them against the oracle."""
+    w, h = shape
+    scene = inputs.scene_uniform_cube(3000, seed=17)
+    fx = 17567.0 if w > h else 14000.0  # a strip of the cube seen at a usual pixel scale
+    cam = inputs.look_at((0.2, -0.1, 3.0), width=w, height=h, fov_x_deg=math.degrees(2 * math.atan(w / 2 / fx)))
+    cfg = frame.make_cfg(tile_w=tile[0], tile_h=tile[1])
+    fr, sc, cams = gpu_forward(scene, [cam], cfg)
+    cfgd = frame.cfg_dict(cfg)
+    s32 = f32_scene(scene)
+    assert fr.status()[1] > 10000  # the strip holds many splats
+    st = _check_forward(fr, s32, cams, cfgd, max_flagged=0.01)
+    refs = oracle_views(s32, cams, cfgd)
+    unresolved = []
+    ws, flips, fst = resolved_weights(fr, cams, cfgd, refs, seed=18, alts_out=unresolved)
+    g = _gpu_backward(fr, sc, ws)
+    gref, gabs = oracle.backward(s32, cams, cfgd, ws, want_abs=True, flip=flips)
+    print(st, assert_groups_close(scene_grads_flat(g), gref, scene["n"], 0, gabs, label=f"{w}x{h}"))
+    checked, _ = check_unresolved_gradients(fr, sc, s32, cams, cfgd, unresolved, seed=19, sh_degree=0)
+    assert checked == min(len(unresolved), 48)
+
+
 # ---------------------------------------------------------------- a5 + a6 backward
 
 def _gpu_backward(fr, sc, ws):
