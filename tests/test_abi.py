@@ -156,6 +156,7 @@ def test_device_entry_points_reject_null_arguments(lib):
     # argument checks happen before any CUDA call, so these run without a GPU
     assert lib.sss_project(None, None, None) == _abi.SSS_ERR_INVALID_ARG
     assert lib.sss_render_fwd(None, None, None, None) == _abi.SSS_ERR_INVALID_ARG
+    assert lib.sss_render_bwd(None, None, None, None) == _abi.SSS_ERR_INVALID_ARG
     assert lib.sss_sghmc_step(None, None, None, None, None, None, None, None) == _abi.SSS_ERR_INVALID_ARG
     assert lib.sss_loss_l1(None, None, 0, None, None, None) == _abi.SSS_ERR_INVALID_ARG
     assert lib.sss_loss_l1_grad(None, None, 0, None, None, None) == _abi.SSS_ERR_INVALID_ARG
