@@ -76,6 +76,8 @@ def lib():
         L.orc_sh_basis.argtypes = [ctypes.c_int, _dp, _dp]
         L.orc_sh_basis.restype = None
         L.orc_max_threads.restype = ctypes.c_int
+        L.orc_pair_windows.argtypes = [_dp, _dp, _ip, ctypes.c_long, _lp, _dp, _dp, _dp, _dp, _dp]
+        L.orc_pair_windows.restype = None
         _lib = L
     return _lib
 
@@ -283,6 +285,18 @@ def normals3(seed: int, step: int, i: int) -> np.ndarray:
     z = np.zeros(3, np.float64)
     lib().orc_normals3(int(seed), int(step), int(i), z)
     return z
+
+
+def pair_windows(proj: np.ndarray, cfg, idx, px, py):
+    """(h, alpha, window) of (component, pixel-centre) pairs: the FP64
+    values and the ambiguity window of the alpha threshold decision."""
+    fd, fi = cfg_arrays(cfg)
+    idx = np.ascontiguousarray(idx, np.int64)
+    px = np.ascontiguousarray(px, np.float64)
+    py = np.ascontiguousarray(py, np.float64)
+    h, a, w = (np.zeros(idx.size) for _ in range(3))
+    lib().orc_pair_windows(np.ascontiguousarray(proj), fd, fi, idx.size, idx, px, py, h, a, w)
+    return h, a, w
 
 
 def t2d(h: float, nu: float) -> float:

@@ -487,8 +487,8 @@ static void cvec_push(cvec* c, contrib x) {
  *   - the argument 1 + h/nu from a 1-ulp hardware reciprocal of nu and one
  *     FMA: 3 u relative, times e;
  *   - the exponent -e log2(1 + h/nu), e and the product each rounded once:
- *     2 u of |ln T2D| = 2 u e ln(1 + h/nu) (for the Gaussian, the product
- *     -h log2(e) / 2: u h / 2);
+ *     2 u of |ln T2D| = 2 u e ln(1 + h/nu) (for the Gaussian, the FP32
+ *     constant log2(e) / 2 and its product with h: 2 u of h / 2);
  *   - the opacity, FP32 tanh of at most 2 ulp (4 u), and its product with
  *     T2D: 5 u.
  * Capped at 1e-2 (the prefilter evaluates every pair with
@@ -505,7 +505,7 @@ static double alpha_window(const double* r, double h, double dx, double dy, cons
   const double dh = 8.0 * u * h + 64.0 * u * u * r[P_ES] * h + gm + 7.0 * u * q;
   double w;
   if (cfg->kernel == 1) {
-    w = 0.5 * dh + ORC_MUFU + u * 0.5 * h;
+    w = 0.5 * dh + ORC_MUFU + u * h;
   } else {
     const double nu = r[P_NU], e = 0.5 * (nu + 2.0);
     w = e / nu / (1.0 + h / nu) * dh + log(2.0) * e * ORC_MUFU + 3.0 * u * e + 2.0 * u * e * log1p(h / nu) +
@@ -513,6 +513,12 @@ static double alpha_window(const double* r, double h, double dx, double dy, cons
   }
   w += 5.0 * u;
   return w < 1e-2 ? w : 1e-2;
+}
+
+/* h = d^T Sigma2D^-1 d of a projection record at the offset d = (dx, dy)
+ * from its mean (Sec. 3.2 Eq. t_2D). */
+static double record_h(const double* r, double dx, double dy) {
+  return r[P_CON_A] * dx * dx + 2.0 * r[P_CON_B] * dx * dy + r[P_CON_C] * dy * dy;
 }
 
 /* Composite pixel (px, py) (integer indices; sample point at the centre).
@@ -537,7 +543,7 @@ static void composite_pixel(const double* proj, const long* order, long m, const
     long i = order[k];
     const double* r = proj + (size_t)i * P_STRIDE;
     double dx = u - r[P_MX], dy = v - r[P_MY];
-    double h = r[P_CON_A] * dx * dx + 2.0 * r[P_CON_B] * dx * dy + r[P_CON_C] * dy * dy;
+    double h = record_h(r, dx, dy);
     if (h > hpre[i]) continue; /* |alpha| < tau (1 - 1e-2) for sure */
     double t2d = kernel_value(h, r[P_NU], cfg);
     double alpha = r[P_O] * t2d;
@@ -579,6 +585,23 @@ static void composite_pixel(const double* proj, const long* order, long m, const
   *last = lst;
   *flags = fl;
   if (n_amb) *n_amb = ev;
+}
+
+/* The ambiguity window (alpha_window above) and the FP64 alpha of npairs
+ * (component, pixel) pairs: component idx[k] of the projection records at
+ * the pixel centre (px[k], py[k]).  For the tests that check the window
+ * against an FP32 evaluation. */
+void orc_pair_windows(const double* proj, const double* cfgd, const int* cfgi, long npairs, const long* idx,
+                      const double* px, const double* py, double* out_h, double* out_alpha, double* out_w) {
+  const ocfg cfg = read_cfg(cfgd, cfgi);
+  for (long k = 0; k < npairs; ++k) {
+    const double* r = proj + (size_t)idx[k] * P_STRIDE;
+    const double dx = px[k] - r[P_MX], dy = py[k] - r[P_MY];
+    const double h = record_h(r, dx, dy);
+    out_h[k] = h;
+    out_alpha[k] = r[P_O] * kernel_value(h, r[P_NU], &cfg);
+    out_w[k] = alpha_window(r, h, dx, dy, &cfg);
+  }
 }
 
 static double* prefilter_bounds(int n, const double* proj, const ocfg* cfg) {

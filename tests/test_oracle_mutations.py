@@ -22,7 +22,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_variants.py", "tests/test_oracle_loss.py",
-        "tests/test_oracle_relocation.py"]
+        "tests/test_oracle_relocation.py", "tests/test_oracle_window.py"]
 
 C = "oracle/sss_oracle.c"
 LOSS = "oracle/image_loss.py"
@@ -34,7 +34,7 @@ MUTATIONS = [
      "return pow(1.0 + h / nu, -(nu + 2.0) / 2.0); }", "return pow(1.0 + h / nu, -(nu + 3.0) / 2.0); }"),
     ("conic off-diagonal sign", C, "out[G_CB] = -cov[1] / det;", "out[G_CB] = cov[1] / det;"),
     ("h without the 2 of 2 b dx dy", C,
-     "double h = r[P_CON_A] * dx * dx + 2.0 * r[P_CON_B] * dx * dy", "double h = r[P_CON_A] * dx * dx + r[P_CON_B] * dx * dy"),
+     "return r[P_CON_A] * dx * dx + 2.0 * r[P_CON_B] * dx * dy", "return r[P_CON_A] * dx * dx + r[P_CON_B] * dx * dy"),
     ("J W^T instead of J W", C,
      "A[r * 3 + c] = J[r * 3 + 0] * V[0 * 4 + c] + J[r * 3 + 1] * V[1 * 4 + c] + J[r * 3 + 2] * V[2 * 4 + c]",
      "A[r * 3 + c] = J[r * 3 + 0] * V[c * 4 + 0] + J[r * 3 + 1] * V[c * 4 + 1] + J[r * 3 + 2] * V[c * 4 + 2]"),
@@ -98,6 +98,13 @@ MUTATIONS = [
      "beta(0.5, ((k + 1) * (nu_new + 3.0) - 1.0) / 2.0)", "beta(0.5, ((k + 1) * (nu_new + 2.0) - 1.0) / 2.0)"),
     ("relocation draw from the prefix's left side", RELOC, "np.searchsorted(prefix, v, side=\"right\")",
      "np.searchsorted(prefix, v, side=\"left\")"),
+    # the ambiguity window must bound an FP32 evaluation of alpha
+    ("window without the FP32 evaluation of h", C, "gm + 7.0 * u * q;", "gm + 1.0 * u * q;"),
+    ("window without the argument 1 + h/nu", C, "ORC_MUFU + 3.0 * u * e + 2.0 * u * e", "ORC_MUFU + 2.0 * u * e"),
+    ("window without the opacity", C, "  w += 5.0 * u;\n", "  w += 0.0 * u;\n"),
+    ("window without the log2 error", C, "log(2.0) * e * ORC_MUFU + 3.0", "3.0"),
+    ("window without the h error", C, "w = e / nu / (1.0 + h / nu) * dh + ", "w = "),
+    ("Gaussian window without dlnT2D/dh", C, "w = 0.5 * dh + ORC_MUFU + u * h;", "w = ORC_MUFU + u * h;"),
 ]
 
 
