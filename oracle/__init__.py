@@ -78,6 +78,9 @@ def lib():
         L.orc_max_threads.restype = ctypes.c_int
         L.orc_pair_windows.argtypes = [_dp, _dp, _ip, ctypes.c_long, _lp, _dp, _dp, _dp, _dp, _dp]
         L.orc_pair_windows.restype = None
+        L.orc_pixel_paths.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _ip, ctypes.c_long, _lp, ctypes.c_int,
+                                      _ip, _lp, _dp, _dp, _dp]
+        L.orc_pixel_paths.restype = None
         _lib = L
     return _lib
 
@@ -297,6 +300,21 @@ def pair_windows(proj: np.ndarray, cfg, idx, px, py):
     h, a, w = (np.zeros(idx.size) for _ in range(3))
     lib().orc_pair_windows(np.ascontiguousarray(proj), fd, fi, idx.size, idx, px, py, h, a, w)
     return h, a, w
+
+
+def pixel_paths(proj: np.ndarray, cam, cfg, pix, max_k: int = 512):
+    """Per pixel (linear indices pix) its contributors in compositing order:
+    (count [npix], index, alpha, T in front, errT behind [npix][max_k]), errT
+    being the termination window's bound on an FP32 transmittance."""
+    fd, fi = cfg_arrays(cfg)
+    pix = np.ascontiguousarray(pix, np.int64)
+    n = proj.shape[0]
+    cnt = np.zeros(pix.size, np.int32)
+    idx = np.zeros((pix.size, max_k), np.int64)
+    a, T, e = (np.zeros((pix.size, max_k)) for _ in range(3))
+    lib().orc_pixel_paths(n, np.ascontiguousarray(proj), int(cam.width), fd, fi, pix.size, pix, int(max_k), cnt, idx,
+                          a, T, e)
+    return cnt, idx, a, T, e
 
 
 def t2d(h: float, nu: float) -> float:

@@ -447,7 +447,7 @@ static long* sorted_valid(int n, const double* proj, long* count) {
 }
 
 /* One contributor of a pixel, kept for the backward pass. */
-typedef struct { long idx; double alpha, T, t2d, h, dx, dy; int clamped; } contrib;
+typedef struct { long idx; double alpha, T, t2d, h, dx, dy; int clamped; double errT; } contrib;
 
 typedef struct { contrib* v; long n, cap; } cvec;
 
@@ -570,7 +570,7 @@ static void composite_pixel(const double* proj, const long* order, long m, const
       if (term) break;
     }
     if (keep) {
-      contrib c = {i, alpha, T, t2d, h, dx, dy, clamped};
+      contrib c = {i, alpha, T, t2d, h, dx, dy, clamped, errTn};
       cvec_push(keep, c);
     }
     for (int ch = 0; ch < 3; ++ch) C[ch] += r[P_R + ch] * alpha * T;
@@ -639,6 +639,41 @@ void orc_render(int n, const double* proj, int width, int height, const double* 
     if (out_last) out_last[k] = lst;
     if (out_flags) out_flags[k] = fl;
     if (out_namb) out_namb[k] = na;
+  }
+  free(order);
+  free(hpre);
+}
+
+/* The compositing path of npix pixels (linear indices pix[k]): up to max_k
+ * contributors each, in order, with their index, (clamped) alpha, the
+ * transmittance T in front of them and the bound on the relative error of an
+ * FP32 transmittance behind them (the termination window's errT).  For the
+ * tests that check that bound against an FP32 compositing. */
+void orc_pixel_paths(int n, const double* proj, int width, const double* cfgd, const int* cfgi, long npix,
+                     const int64_t* pix, int max_k, int32_t* out_count, int64_t* out_idx, double* out_alpha,
+                     double* out_T, double* out_errT) {
+  ocfg cfg = read_cfg(cfgd, cfgi);
+  long m;
+  long* order = sorted_valid(n, proj, &m);
+  double* hpre = prefilter_bounds(n, proj, &cfg);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (long k = 0; k < npix; ++k) {
+    const long lin = (long)pix[k];
+    double rgb[3], T;
+    int nc, fl, na;
+    long lst;
+    cvec keep = {NULL, 0, 0};
+    composite_pixel(proj, order, m, hpre, &cfg, lin % width, lin / width, 0u, rgb, &T, &nc, &lst, &fl, &na, &keep);
+    const long c = keep.n < max_k ? keep.n : max_k;
+    out_count[k] = (int32_t)c;
+    for (long j = 0; j < c; ++j) {
+      const size_t o = (size_t)k * max_k + j;
+      out_idx[o] = keep.v[j].idx;
+      out_alpha[o] = keep.v[j].alpha;
+      out_T[o] = keep.v[j].T;
+      out_errT[o] = keep.v[j].errT;
+    }
+    free(keep.v);
   }
   free(order);
   free(hpre);

@@ -105,6 +105,12 @@ MUTATIONS = [
     ("window without the log2 error", C, "log(2.0) * e * ORC_MUFU + 3.0", "3.0"),
     ("window without the h error", C, "w = e / nu / (1.0 + h / nu) * dh + ", "w = "),
     ("Gaussian window without dlnT2D/dh", C, "w = 0.5 * dh + ORC_MUFU + u * h;", "w = ORC_MUFU + u * h;"),
+    # the termination window must bound an FP32 compositing of T
+    ("T bound without the 2u roundings", C, "errT + 2.0 * ORC_U + W * fabs(alpha)", "errT + W * fabs(alpha)"),
+    ("T bound without the alpha error", C, "errT + 2.0 * ORC_U + W * fabs(alpha) / fabs(1.0 - alpha);",
+     "errT + 2.0 * ORC_U;"),
+    ("T bound with alpha / (1 + alpha)", C, "W * fabs(alpha) / fabs(1.0 - alpha);", "W * fabs(alpha) / fabs(1.0 + alpha);"),
+    ("T bound not accumulated", C, "double errTn = errT + 2.0 * ORC_U", "double errTn = 2.0 * ORC_U"),
 ]
 
 

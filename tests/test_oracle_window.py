@@ -79,9 +79,10 @@ def _pairs(proj, cam, rng, per_comp):
     return comp[keep], px[keep], py[keep]
 
 
-def _emulated_alpha_range(proj, cfgd, comp, px, py, kernel):
-    """Smallest and largest |alpha| the emulated FP32 chain gives over the
-    worst cases of the hardware approximations."""
+def _emulated_aabs(proj, comp, px, py, kernel, so, sr, sl, se):
+    """|alpha| of the pairs through the emulated FP32 chain, with tanh, the
+    reciprocal of nu, log2 and exp2 each at its worst case on the side of the
+    sign given for it (so, sr, sl, se)."""
     P = oracle.P
     r = proj[comp]
     ca, cb, cc = (r[:, P[k]].astype(F32) for k in ("con_a", "con_b", "con_c"))
@@ -93,28 +94,31 @@ def _emulated_alpha_range(proj, cfgd, comp, px, py, kernel):
     t = _fma(ca, dx, ((F32(2) * cb) * dy).astype(F32))
     h = _fma(dx, t, ((cc * dy).astype(F32) * dy).astype(F32))
     o = np.abs(r[:, P["o"]])
-    nu = r[:, P["nu"]].astype(F32)
+    o32 = _worst(o, 2 * _ulp(o), so)  # tanh: 2 ulp
+    if kernel == 1:
+        p = (h * F32(-0.72134752044448170)).astype(F32)
+    else:
+        nu = r[:, P["nu"]].astype(F32)
+        inv = _worst(1.0 / nu.astype(F64), _ulp(1.0 / nu.astype(F64)), sr)  # reciprocal: 1 ulp
+        x1 = _fma(h, inv, F32(1))
+        l2 = _worst(np.log2(x1.astype(F64)), 2.0 ** -22, sl)  # log2: 2^-22 absolute
+        e = (nu * F32(-0.5) - F32(1)).astype(F32)
+        p = (e * l2).astype(F32)
+    ex = np.exp2(p.astype(F64))
+    t2d = _worst(ex, 2.0 ** -22 * ex, se)  # exp2: 2^-22 relative
+    return np.minimum((o32 * t2d).astype(F32), F32(oracle.DEFAULT_CFG["alpha_max"]))
+
+
+def _emulated_alpha_range(proj, cfgd, comp, px, py, kernel):
+    """Smallest and largest |alpha| the emulated FP32 chain gives over the
+    worst cases of the hardware approximations."""
     lo = np.full(comp.size, np.inf)
     hi = np.full(comp.size, -np.inf)
     for so in (-1, 1):
-        o32 = _worst(o, 2 * _ulp(o), so)  # tanh: 2 ulp
-        for sl in (-1, 1):
-            for se in (-1, 1):
-                if kernel == 1:
-                    p = (h * F32(-0.72134752044448170)).astype(F32)
-                    t2d = [_worst(np.exp2(p.astype(F64)), 2.0 ** -22 * np.exp2(p.astype(F64)), se)]
-                else:
-                    t2d = []
-                    for sr in (-1, 1):
-                        inv = _worst(1.0 / nu.astype(F64), _ulp(1.0 / nu.astype(F64)), sr)  # reciprocal: 1 ulp
-                        x1 = _fma(h, inv, F32(1))
-                        l2 = _worst(np.log2(x1.astype(F64)), 2.0 ** -22, sl)  # log2: 2^-22 absolute
-                        e = (nu * F32(-0.5) - F32(1)).astype(F32)
-                        p = (e * l2).astype(F32)
-                        ex = np.exp2(p.astype(F64))
-                        t2d.append(_worst(ex, 2.0 ** -22 * ex, se))  # exp2: 2^-22 relative
-                for t in t2d:
-                    a = (o32 * t).astype(F64)
+        for sr in (-1, 1):
+            for sl in (-1, 1):
+                for se in (-1, 1):
+                    a = _emulated_aabs(proj, comp, px, py, kernel, so, sr, sl, se).astype(F64)
                     lo, hi = np.minimum(lo, a), np.maximum(hi, a)
     return lo, hi
 
@@ -137,3 +141,38 @@ def test_window_bounds_an_fp32_evaluation_of_alpha(kernel):
     print(f"kernel {kernel}: {int(live.sum())} pairs, deviation / window: median {np.median(ratio):.3f}, "
           f"max {ratio.max():.3f}")
     assert ratio.max() <= 1.0
+
+
+@pytest.mark.parametrize("side", [-1, 1])
+def test_termination_window_bounds_an_fp32_compositing(side):
+    """Along every sampled pixel's path the oracle's bound errT on the
+    relative error of an FP32 transmittance (2u per composited splat plus the
+    splat's window times |alpha| / |1 - alpha|) must hold for the emulated
+    FP32 compositing T <- T (1 - alpha), with the hardware approximations at
+    their worst case on one side for every splat."""
+    scene = inputs.scene_sphere_shell(100_000, seed=1)
+    cam = _f32_camera(inputs.sphere_cameras(8, width=800, height=800)[5])
+    cfgd = _cfg(0)
+    s32 = {k: (np.asarray(v, F32) if k in FIELDS else v) for k, v in scene.items()}
+    proj = oracle.project(s32, cam, cfgd)
+    pix = np.random.default_rng(7).choice(cam.width * cam.height, 3000, replace=False)
+    cnt, idx, alpha, T64, errT = oracle.pixel_paths(proj, cam, cfgd, pix, max_k=1024)
+    assert cnt.max() < 1024 and np.mean(cnt) > 20
+    px, py = (pix % cam.width).astype(F64), (pix // cam.width).astype(F64)
+    T32 = np.ones(pix.size, F32)
+    worst = 0.0
+    for j in range(int(cnt.max())):
+        live = j < cnt
+        if not live.any():
+            break
+        k = np.flatnonzero(live)
+        # every approximation on the side that moves |alpha| by `side` (a larger 1/nu or log2 lowers it)
+        aabs = _emulated_aabs(proj, idx[k, j], px[k], py[k], 0, side, -side, -side, side)
+        a32 = (np.sign(alpha[k, j]).astype(F32) * aabs).astype(F32)
+        T32[k] = (T32[k] * (F32(1) - a32).astype(F32)).astype(F32)
+        Tn = T64[k, j] * (1.0 - alpha[k, j])
+        ratio = np.abs(T32[k].astype(F64) - Tn) / (errT[k, j] * np.abs(Tn))
+        worst = max(worst, float(ratio.max()))
+    print(f"side {side}: {pix.size} pixels, {int(cnt.sum())} composited splats, mean path {cnt.mean():.0f}, "
+          f"T deviation / bound: max {worst:.3f}")
+    assert worst <= 1.0
