@@ -44,7 +44,7 @@ WORKLOADS = {"clusters_1p5m_4views": "clusters_1p5m_4views", "shell_100k_8views"
 MUFU_PER_SM_CLK = 16    # MUFU (ex2/lg2) results per SM and clock
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0     # used only when neither nvidia-smi nor MEASURED_PEAKS.json gives it
-# Algorithmic work of the render stages, the survey's per-pair figures: the
+# Algorithmic work of the render stages, the method's minimal per-pair work: the
 # forward evaluates h (the cheap reject, 8 FP32 flops) for every evaluated
 # (splat, pixel) pair and T2D, alpha and the compositing update (12 FP32
 # flops + 2 MUFU: lg2, ex2) for every contributing pair; the backward does
@@ -55,7 +55,7 @@ BWD_FLOPS, BWD_MUFU = 50, 2
 # A finer count of the backward's formulas written out (the same h, T2D, alpha
 # and T recovery, dL/dalpha, dalpha/do, dalpha/dh, dalpha/dnu with its log,
 # dh/dmean, dh/dconic, dL/drgb): 75 FP32 flops + 4 MUFU per contributing pair.
-# Reported beside the survey's figure, labelled, never as the headline.
+# Reported beside the minimal figure, labelled, never as the headline.
 BWD_FLOPS_DETAILED, BWD_MUFU_DETAILED = 75, 4
 
 

@@ -254,7 +254,7 @@ def check_unresolved_gradients(fr, sc, s32, cams, cfgd, unresolved, seed, sh_deg
 
 
 
-GRAD_REL = 1e-3   # the survey's bar: |g - g_ref| <= 1e-3 max(|g_ref|, 1e-3 max_group |g_ref|) ...
+GRAD_REL = 1e-3   # the gradient bar: |g - g_ref| <= 1e-3 max(|g_ref|, 1e-3 max_group |g_ref|) ...
 U32 = 2.0 ** -24  # FP32 unit roundoff
 # ... or, for an element where the terms of its sum cancel, within the FP32
 # rounding bound of that sum: u (16 A_n + 256 A), A = sum |term| (taken on the
@@ -276,7 +276,7 @@ def grad_floor(mag, extra=0.0):
 
 
 def grad_den(ref, mag, extra=0.0):
-    """Per-element scale: the survey's bar divided by GRAD_REL, or the FP32
+    """Per-element scale: the gradient bar divided by GRAD_REL, or the FP32
     bound divided by GRAD_REL where that is larger (|g - g_ref| <= GRAD_REL x
     this is the element's test)."""
     scale = max(float(np.abs(ref).max()), 1e-30)
@@ -302,13 +302,13 @@ def sh_basis_bound(n, sh_degree, mag2d):
 
 
 def assert_groups_close(got, ref, n, sh_degree, mag, rel=GRAD_REL, norm=GRAD_NORM, label="", extra=None):
-    """Per parameter group: every element within the survey's bar
+    """Per parameter group: every element within the gradient bar
     rel max(|g_ref|, 1e-3 max_group |g_ref|) or within the FP32 rounding
     bound of its sum; at most FLOOR_FRAC of the touched elements (those with a
     nonzero reference or summand) resting on the latter; and the group's
     relative L2 error within ``norm``.  Returns per group: the largest ratio
     of error to bar, the relative L2 error, the number of touched elements,
-    how many of them fail the survey's bar (and so rest on the FP32 bound),
+    how many of them fail the 1e-3 bar (and so rest on the FP32 bound),
     and that fraction."""
     sl = oracle.theta_slices(n, sh_degree)
     report = {}
