@@ -35,6 +35,10 @@ constexpr int kTile = kThreads * kItems;  // elements per CTA iteration
 constexpr int kRadix = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kWarpSpan = kItems * 32;  // elements of a tile owned by one warp
+// entries per CTA of the pair count and the emission: four 256-entry chunks,
+// so that a frame's entries spread over many CTAs (their gathers are
+// latency-bound)
+constexpr uint32_t kEmitSlice = 4 * 256;
 static_assert(kThreads == kRadix, "one thread per digit");
 
 __device__ __forceinline__ uint32_t load_count(const uint32_t* count_dev, uint32_t count_max) {
@@ -42,11 +46,12 @@ __device__ __forceinline__ uint32_t load_count(const uint32_t* count_dev, uint32
 }
 
 // Contiguous slice [begin, end) of `count` elements owned by CTA b of nb;
-// slices are multiples of kTile except the last.
+// slices are multiples of UNIT (kTile for the radix passes) except the last.
+template <uint32_t UNIT = kTile>
 __device__ __forceinline__ void slice(uint32_t count, int nb, int b, uint32_t& begin, uint32_t& end) {
-  const uint64_t tiles = ((uint64_t)count + kTile - 1) / kTile;
+  const uint64_t tiles = ((uint64_t)count + UNIT - 1) / UNIT;
   const uint64_t per = (tiles + nb - 1) / nb;
-  const uint64_t b0 = (uint64_t)b * per * kTile, b1 = (uint64_t)(b + 1) * per * kTile;
+  const uint64_t b0 = (uint64_t)b * per * UNIT, b1 = (uint64_t)(b + 1) * per * UNIT;
   begin = (uint32_t)(b0 < count ? b0 : (uint64_t)count);
   end = (uint32_t)(b1 < count ? b1 : (uint64_t)count);
 }
@@ -396,7 +401,7 @@ __global__ void __launch_bounds__(kThreads) k_count_sum(const uint32_t* __restri
                                                         uint32_t* __restrict__ block_sums) {
   __shared__ uint32_t ws[kWarps];
   uint32_t begin, end;
-  slice(n, gridDim.x, blockIdx.x, begin, end);
+  slice<kEmitSlice>(n, gridDim.x, blockIdx.x, begin, end);
   uint32_t acc = 0;
   for (uint32_t i = begin + threadIdx.x; i < end; i += kThreads) acc += ntiles[order[i]];
 #pragma unroll
@@ -435,7 +440,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(const sss_frame_plan P, const
   __shared__ uint32_t s_e[kThreads];
   __shared__ uint32_t s_w[kWarps];
   uint32_t begin, end;
-  slice(P.n_entries, gridDim.x, blockIdx.x, begin, end);
+  slice<kEmitSlice>(P.n_entries, gridDim.x, blockIdx.x, begin, end);
   uint32_t carry = block_off[blockIdx.x];
   const uint32_t cap = P.pair_capacity;
   // software pipeline over the 256-entry chunks: the entry id of chunk k + 2
@@ -536,10 +541,10 @@ extern "C" int sss_bin(const sss_frame_plan* plan, void* ws, sss_stream_t stream
                       32, nb, hist, nullptr, st);
   if (rc != SSS_OK) return rc;
   uint32_t* block_sums = hist;  // reused: nb words
-  // emission: one kTile slice of the depth order per CTA (many CTAs hide the
-  // latency of the dependent order -> count / rectangle gathers); the block
-  // sums fit in the histogram scratch (256 nb + 256 words)
-  const unsigned nbe = (unsigned)std::min<size_t>(ceil_div(n, kTile), (size_t)kRadix * nb);
+  // emission: one kEmitSlice slice of the depth order per CTA (many CTAs
+  // hide the latency of the dependent order -> count / rectangle gathers);
+  // the block sums fit in the histogram scratch (256 nb + 256 words)
+  const unsigned nbe = (unsigned)std::min<size_t>(ceil_div(n, kEmitSlice), (size_t)kRadix * nb);
   k_count_sum<<<nbe, kThreads, 0, st>>>(order, ws_ptr<uint32_t>(ws, P.ws_off_ntiles), n, block_sums);
   k_scan_rows<<<1, kThreads, 0, st>>>(block_sums, nbe, ctrl + kCtrlPairsNeeded);
   k_finish_count<<<1, 1, 0, st>>>(ctrl, P.pair_capacity);
