@@ -100,6 +100,7 @@ MUTATIONS = [
      "np.searchsorted(prefix, v, side=\"left\")"),
     # the ambiguity window must bound an FP32 evaluation of alpha
     ("window without the FP32 evaluation of h", C, "gm + 7.0 * u * q;", "gm + 1.0 * u * q;"),
+    ("window without the FP32 scales", C, "const double dh = 8.0 * u * h + ", "const double dh = "),
     ("window without the argument 1 + h/nu", C, "ORC_MUFU + 3.0 * u * e + 2.0 * u * e", "ORC_MUFU + 2.0 * u * e"),
     ("window without the opacity", C, "  w += 5.0 * u;\n", "  w += 0.0 * u;\n"),
     ("window without the log2 error", C, "log(2.0) * e * ORC_MUFU + 3.0", "3.0"),

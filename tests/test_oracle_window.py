@@ -79,13 +79,17 @@ def _pairs(proj, cam, rng, per_comp):
     return comp[keep], px[keep], py[keep]
 
 
-def _emulated_aabs(proj, comp, px, py, kernel, so, sr, sl, se):
+def _emulated_aabs(proj, comp, px, py, kernel, so, sr, sl, se, con=None):
     """|alpha| of the pairs through the emulated FP32 chain, with tanh, the
     reciprocal of nu, log2 and exp2 each at its worst case on the side of the
-    sign given for it (so, sr, sl, se)."""
+    sign given for it (so, sr, sl, se).  con: the pairs' FP32 conic (a, b, c);
+    by default the FP64 record's, rounded once."""
     P = oracle.P
     r = proj[comp]
-    ca, cb, cc = (r[:, P[k]].astype(F32) for k in ("con_a", "con_b", "con_c"))
+    if con is None:
+        ca, cb, cc = (r[:, P[k]].astype(F32) for k in ("con_a", "con_b", "con_c"))
+    else:
+        ca, cb, cc = con
     mx, my = r[:, P["mx"]], r[:, P["my"]]
     ox, oy = np.clip(np.rint(mx), 0, 16384), np.clip(np.rint(my), 0, 16384)
     mxr, myr = (mx - ox).astype(F32), (my - oy).astype(F32)
@@ -109,7 +113,7 @@ def _emulated_aabs(proj, comp, px, py, kernel, so, sr, sl, se):
     return np.minimum((o32 * t2d).astype(F32), F32(oracle.DEFAULT_CFG["alpha_max"]))
 
 
-def _emulated_alpha_range(proj, cfgd, comp, px, py, kernel):
+def _emulated_alpha_range(proj, cfgd, comp, px, py, kernel, con=None):
     """Smallest and largest |alpha| the emulated FP32 chain gives over the
     worst cases of the hardware approximations."""
     lo = np.full(comp.size, np.inf)
@@ -118,9 +122,113 @@ def _emulated_alpha_range(proj, cfgd, comp, px, py, kernel):
         for sr in (-1, 1):
             for sl in (-1, 1):
                 for se in (-1, 1):
-                    a = _emulated_aabs(proj, comp, px, py, kernel, so, sr, sl, se).astype(F64)
+                    a = _emulated_aabs(proj, comp, px, py, kernel, so, sr, sl, se, con).astype(F64)
                     lo, hi = np.minimum(lo, a), np.maximum(hi, a)
     return lo, hi
+
+
+# ---- the projection's double-float conic, emulated (pairs of float32 with
+# exact error-free transformations), as a rasterizer computes it from the
+# FP32 parameters: exact products of the raw quaternion, the rotation folded
+# with the FP32 scales, the two rows of J W M, det = |n0 x n1|^2, each result
+# rounded once
+def _two_sum(a, b):
+    s = (a + b).astype(F32)
+    bb = (s - a).astype(F32)
+    return s, ((a - (s - bb)) + (b - bb)).astype(F32)
+
+
+def _fast_two_sum(a, b):
+    s = (a + b).astype(F32)
+    return s, (b - (s - a)).astype(F32)
+
+
+def _two_prod(a, b):
+    p = (a * b).astype(F32)
+    return p, _fma(a, b, -p)
+
+
+def _dmul(A, B):
+    p = (A[0] * B[0]).astype(F32)
+    return _fast_two_sum(p, _fma(A[0], B[1], _fma(A[1], B[0], _fma(A[0], B[0], -p))))
+
+
+def _dmulf(A, b):
+    p = (A[0] * b).astype(F32)
+    return _fast_two_sum(p, _fma(A[1], b, _fma(A[0], b, -p)))
+
+
+def _dadd(A, B):
+    s, e = _two_sum(A[0], B[0])
+    return _fast_two_sum(s, (e + (A[1] + B[1]).astype(F32)).astype(F32))
+
+
+def _dneg(A):
+    return -A[0], -A[1]
+
+
+def _drcp(A):
+    r = (F32(1) / A[0]).astype(F32)
+    e = (_fma(-r, A[0], np.ones_like(r)) - (r * A[1]).astype(F32)).astype(F32)
+    return _fast_two_sum(r, (r * e).astype(F32))
+
+
+def _df(x):
+    x = np.asarray(x, F32)
+    return x, np.zeros_like(x)
+
+
+def _dot3_plus(r, m, t):
+    s, err = _two_prod(r[0], m[0])
+    for k in (1, 2):
+        q = _two_prod(r[k], m[k])
+        s, e = _two_sum(s, q[0])
+        err = (err + (e + q[1]).astype(F32)).astype(F32)
+    s, e = _two_sum(s, t)
+    return _fast_two_sum(s, (err + e).astype(F32))
+
+
+def _conic_df(mu, ls_scale, q, cam, lp):
+    """Conic (a, b, c) of every component for the camera, from FP32 means,
+    scales and quaternions."""
+    V = np.asarray(cam.viewmat, F32).reshape(3, 4)
+    full = lambda v: np.full_like(mu[0], F32(v))
+    w, x, y, z = q
+    pr = {k: _two_prod(a, b) for k, (a, b) in dict(ww=(w, w), xx=(x, x), yy=(y, y), zz=(z, z), xy=(x, y),
+                                                   wz=(w, z), xz=(x, z), wy=(w, y), yz=(y, z), wx=(w, x)).items()}
+    two = lambda A: (A[0] * F32(2), A[1] * F32(2))
+    Rn = [[_dadd(_dadd(pr["ww"], pr["xx"]), _dneg(_dadd(pr["yy"], pr["zz"]))), two(_dadd(pr["xy"], _dneg(pr["wz"]))),
+           two(_dadd(pr["xz"], pr["wy"]))],
+          [two(_dadd(pr["xy"], pr["wz"])), _dadd(_dadd(pr["ww"], pr["yy"]), _dneg(_dadd(pr["xx"], pr["zz"]))),
+           two(_dadd(pr["yz"], _dneg(pr["wx"])))],
+          [two(_dadd(pr["xz"], _dneg(pr["wy"]))), two(_dadd(pr["yz"], pr["wx"])),
+           _dadd(_dadd(pr["ww"], pr["zz"]), _dneg(_dadd(pr["xx"], pr["yy"])))]]
+    inv = _drcp(_dadd(_dadd(pr["ww"], pr["xx"]), _dadd(pr["yy"], pr["zz"])))
+    sig = [_dmulf(inv, ls_scale[k]) for k in range(3)]
+    M = [[_dmul(Rn[j][k], sig[k]) for k in range(3)] for j in range(3)]
+    p = [_dot3_plus([full(V[r, k]) for k in range(3)], mu, full(V[r, 3])) for r in range(3)]
+    iz = _drcp(p[2])
+    u = [_dmul(p[0], iz), _dmul(p[1], iz)]
+    for r, (ext, f) in enumerate(((cam.width, cam.fx), (cam.height, cam.fy))):
+        lim = _dmul((full(1.3), full(4.7683717e-08)), _dmulf(_drcp(_df(full(F32(2) * F32(f)))), F32(ext)))
+        lo = (u[r][0] < -lim[0]) | ((u[r][0] == -lim[0]) & (u[r][1] < -lim[1]))
+        hi = (u[r][0] > lim[0]) | ((u[r][0] == lim[0]) & (u[r][1] > lim[1]))
+        u[r] = (np.where(lo, -lim[0], np.where(hi, lim[0], u[r][0])),
+                np.where(lo, -lim[1], np.where(hi, lim[1], u[r][1])))
+    rowf = [_dmulf(iz, F32(cam.fx)), _dmulf(iz, F32(cam.fy))]
+    U = [[_dadd(_df(full(V[r, k])), _dneg(_dmulf(u[r], V[2, k]))) for k in range(3)] for r in range(2)]
+    N = [[_dmul(rowf[r], _dadd(_dadd(_dmul(U[r][0], M[0][k]), _dmul(U[r][1], M[1][k])), _dmul(U[r][2], M[2][k])))
+          for k in range(3)] for r in range(2)]
+    dot = lambda a, b: _dadd(_dadd(_dmul(a[0], b[0]), _dmul(a[1], b[1])), _dmul(a[2], b[2]))
+    a, c, b = dot(N[0], N[0]), dot(N[1], N[1]), dot(N[0], N[1])
+    xr = [_dadd(_dmul(N[0][1], N[1][2]), _dneg(_dmul(N[0][2], N[1][1]))),
+          _dadd(_dmul(N[0][2], N[1][0]), _dneg(_dmul(N[0][0], N[1][2]))),
+          _dadd(_dmul(N[0][0], N[1][1]), _dneg(_dmul(N[0][1], N[1][0])))]
+    lpv = full(lp)
+    A, C = _dadd(a, _df(lpv)), _dadd(c, _df(lpv))
+    det = _dadd(dot(xr, xr), _dmulf(_dadd(_dadd(a, c), _df(lpv)), F32(lp)))
+    iv = _drcp(det)
+    return _dmul(C, iv)[0], _dneg(_dmul(b, iv))[0], _dmul(A, iv)[0]
 
 
 @pytest.mark.parametrize("kernel", [0, 1])
@@ -140,6 +248,39 @@ def test_window_bounds_an_fp32_evaluation_of_alpha(kernel):
     ratio = dev / w[live]
     print(f"kernel {kernel}: {int(live.sum())} pairs, deviation / window: median {np.median(ratio):.3f}, "
           f"max {ratio.max():.3f}")
+    assert ratio.max() <= 1.0
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_window_bounds_the_fp32_projection_and_evaluation(kernel):
+    """As the test above, with each record computed as a rasterizer computes
+    it: the double-float conic from the FP32 parameters, with the scales
+    exp(log_scale) at 2 ulp to either side.  This covers the projection's part
+    of the window as well (the scales, the double-float chain, the conic's
+    rounding)."""
+    scene = inputs.subset_scene(inputs.scene_sphere_shell(100_000, seed=1), np.arange(0, 100_000, 5))
+    cam = _f32_camera(inputs.sphere_cameras(8, width=800, height=800)[3])
+    cfgd = _cfg(kernel)
+    s32 = {k: (np.asarray(v, F32) if k in FIELDS else v) for k, v in scene.items()}
+    proj = oracle.project(s32, cam, cfgd)
+    comp, px, py = _pairs(proj, cam, np.random.default_rng(4), per_comp=12)
+    h, alpha, w = oracle.pair_windows(proj, cfgd, comp, px + 0.5, py + 0.5)
+    mu = [s32["mean"][k] for k in range(3)]
+    q = [s32["quat"][k] for k in range(4)]
+    a = np.abs(alpha)
+    lo = np.full(comp.size, np.inf)
+    hi = np.full(comp.size, -np.inf)
+    for ss in (-1, 1):  # expf: 2 ulp
+        sc = [_worst(np.exp(s32["log_scale"][k].astype(F64)), 2 * _ulp(np.exp(s32["log_scale"][k].astype(F64))), ss)
+              for k in range(3)]
+        ca, cb, cc = _conic_df(mu, sc, q, cam, cfgd["lowpass"])
+        l, hh = _emulated_alpha_range(proj, cfgd, comp, px, py, kernel, con=(ca[comp], cb[comp], cc[comp]))
+        lo, hi = np.minimum(lo, l), np.maximum(hi, hh)
+    live = a >= 0.5 * cfgd["tau"]
+    assert live.sum() > 50_000
+    ratio = np.maximum(np.abs(hi - a), np.abs(lo - a))[live] / a[live] / w[live]
+    print(f"kernel {kernel}: {int(live.sum())} pairs from emulated records, deviation / window: median "
+          f"{np.median(ratio):.3f}, max {ratio.max():.3f}")
     assert ratio.max() <= 1.0
 
 
